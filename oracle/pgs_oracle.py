@@ -1,0 +1,369 @@
+"""CPU oracle for the load-balanced sample sort of "A Load-Balanced Parallel and
+Distributed Sorting Algorithm Implemented with PGX.D" (arXiv 1611.00463).
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite, the smoke check and
+the CPU-baseline leg of the benchmark may import or run this module.  It shares
+no code with the CUDA path and never takes an input or an expected value from it.
+
+Plain numpy, single threaded, written for a reader to check against the paper by
+eye.  Library sorts (``numpy.argsort(kind="stable")``) and binary searches
+(``numpy.searchsorted``) serve as steps; nothing is blocked, fused or reordered.
+
+Two things are computed:
+
+* Part 1, the sorted output.  The method reaches exactly the plain result: a
+  stable ascending sort on the key's total order, payload carried along
+  (Section IV: smaller entries end on lower-numbered processors, and each entry
+  keeps where it came from, step 6).  ``stable_sort`` is that definition.
+* Part 2, the method's own steps in the paper's order (Section IV, steps 1-6;
+  Section IV-A, Fig. 2 balanced merge; Section IV-B, sample budget and the
+  investigator), giving the bucket vector e[0..P], the per-run cut matrix, the
+  exchange offsets and, after the per-bucket merges, again the sorted output.
+
+Readings of points the paper leaves open (each is listed in the design notes):
+sample positions are the last element of s equal blocks of a sorted run; the
+Master takes every (S/P)-th sample as a splitter; bucket b receives the
+stable-rank range [e_b, e_{b+1}); the default investigator cuts every splitter
+at its ideal rank floor(b*N/P) clamped into the splitter's duplicate range, and
+it divides that range by global stable rank so the output stays stable.
+
+Parity pins: every function below is pinned by tests that do not re-run its own
+formula (brute force, closed forms, invariants and the balance bound); none is
+"parity unpinned" except the learned-CDF training, which the tests pin only by
+properties (see ``mlp_*``).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+DTYPES = {"u32": np.uint32, "u64": np.uint64, "f32": np.uint32}
+KEY_BYTES = {"u32": 4, "u64": 8, "f32": 4}
+
+INVESTIGATOR_RANK = 0      # default: cut at rank floor(bN/P) clamped into [L_b, L_b+G_b]
+INVESTIGATOR_EQUAL = 1     # a group of k equal splitters splits the value's range into k equal parts
+INVESTIGATOR_OFF = 2       # plain binary search (upper bound), the failure mode of Fig. 5(b)
+
+SAMPLE_BUFFER_BYTES = 262144   # the 256 KB read buffer of Section IV-B
+
+
+# ---------------------------------------------------------------------------
+# Key order
+# ---------------------------------------------------------------------------
+
+def ord_bits(keys: np.ndarray, dtype: str) -> np.ndarray:
+    """Unsigned integer whose natural order is the key order.
+
+    Integer keys are their own order.  float32 keys (passed as uint32 bit
+    patterns) follow IEEE-754 totalOrder: negative values have every bit
+    flipped, non-negative ones get the sign bit set, so
+    -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN.
+    The paper only sorts integers; this ordering is the reading for floats.
+    """
+    if dtype in ("u32", "u64"):
+        return keys
+    if dtype != "f32":
+        raise ValueError(dtype)
+    b = keys.astype(np.uint32, copy=False)
+    neg = (b >> np.uint32(31)) == 1
+    return np.where(neg, ~b, b | np.uint32(0x80000000)).astype(np.uint32)
+
+
+# ---------------------------------------------------------------------------
+# Part 1: the sorted output (definition)
+# ---------------------------------------------------------------------------
+
+def stable_sort(keys: np.ndarray, vals: np.ndarray | None, dtype: str):
+    """Stable ascending sort by ord(key); the payload travels with its key.
+
+    Section IV (end of IV-C): after the sort smaller entries sit on processors
+    with smaller IDs, and each entry's previous processor and index are kept
+    (step 6).  Equal keys keep their input order.
+    """
+    order = np.argsort(ord_bits(keys, dtype), kind="stable")
+    return keys[order], (None if vals is None else vals[order])
+
+
+# ---------------------------------------------------------------------------
+# Part 2: the method, step by step
+# ---------------------------------------------------------------------------
+
+def effective_partitions(n: int, P: int) -> int:
+    """P logical processors; more processors than keys collapse to one per key."""
+    if P < 1:
+        raise ValueError("P must be >= 1")
+    return max(1, min(P, n))
+
+
+def run_bounds(n: int, P: int) -> np.ndarray:
+    """Processor r owns input positions [floor(r n / P), floor((r+1) n / P)).
+
+    Step 1 of Section IV gives every processor its own share of the data; the
+    floor split is the reading for n not divisible by P.
+    """
+    return np.array([(r * n) // P for r in range(P + 1)], dtype=np.int64)
+
+
+def balanced_merge_schedule(k: int) -> list[list[tuple[int, int]]]:
+    """Rounds of the balanced pairwise merge of Fig. 2 (Section IV-A).
+
+    Round j merges list i + 2^j into list i for every i that is a multiple of
+    2^(j+1) with i + 2^j < k; each pair is (destination, source).  For k = 8:
+    (0<-1, 2<-3, 4<-5, 6<-7), then (0<-2, 4<-6), then (0<-4).
+    """
+    rounds = []
+    step = 1
+    while step < k:
+        rounds.append([(i, i + step) for i in range(0, k, 2 * step) if i + step < k])
+        step *= 2
+    return rounds
+
+
+def merge_two(ka, va, kb, vb, dtype):
+    """Stable merge of two sorted lists; on equal keys the first list wins."""
+    k = np.concatenate([ka, kb])
+    v = None if va is None else np.concatenate([va, vb])
+    order = np.argsort(ord_bits(k, dtype), kind="stable")
+    return k[order], (None if v is None else v[order])
+
+
+def balanced_merge(lists, dtype):
+    """Merge sorted (keys, vals) lists with the schedule of Fig. 2."""
+    if not lists:
+        return None
+    cur = list(lists)
+    for rnd in balanced_merge_schedule(len(cur)):
+        for dst, src in rnd:
+            ka, va = cur[dst]
+            kb, vb = cur[src]
+            cur[dst] = merge_two(ka, va, kb, vb, dtype)
+    return cur[0]
+
+
+def local_sort(keys, vals, dtype, threads: int = 32):
+    """Step 1 of Section IV and Section IV-A: split a processor's data equally
+    over worker threads, sort each piece, then merge the pieces with Fig. 2."""
+    n = len(keys)
+    t = max(1, min(threads, n))
+    cuts = [(i * n) // t for i in range(t + 1)]
+    pieces = []
+    for i in range(t):
+        pk, pv = stable_sort(keys[cuts[i]:cuts[i + 1]],
+                             None if vals is None else vals[cuts[i]:cuts[i + 1]], dtype)
+        pieces.append((pk, pv))
+    if not pieces:
+        return keys[:0], (None if vals is None else vals[:0])
+    return balanced_merge(pieces, dtype)
+
+
+def paper_samples_per_run(P: int, key_bytes: int) -> int:
+    """Section IV-B: each processor sends 256/p KB of samples to the Master.
+
+    Read as floor(262144 / (P * key_bytes)) keys per processor (keys only).
+    """
+    return max(1, SAMPLE_BUFFER_BYTES // (P * key_bytes))
+
+
+def guaranteed_samples_per_run(P: int, eps: float) -> int:
+    """Samples per run so that the balance bound 1 + P/s is at most 1 + eps."""
+    return int(np.ceil(P / eps))
+
+
+def regular_sample_positions(n_r: int, s: int) -> np.ndarray:
+    """Step 2 of Section IV: regular samples of a sorted run.
+
+    Reading: the run is cut into s_r = min(s, n_r) equal blocks and the last
+    element of each block is sampled, local position floor((i+1) n_r / s_r) - 1.
+    """
+    s_r = min(s, n_r)
+    if s_r == 0:
+        return np.zeros(0, dtype=np.int64)
+    i = np.arange(1, s_r + 1, dtype=np.int64)
+    return (i * n_r) // s_r - 1
+
+
+def select_splitters(samples_ord: np.ndarray, P: int) -> np.ndarray:
+    """Step 3 of Section IV: the Master sorts the gathered samples and picks P-1
+    final splitters.  Reading (regular sampling, as in PSRS): with S samples,
+    splitter t_b is the sample at sorted index floor(b S / P) - 1, b = 1..P-1.
+    The samples arrive in (run, position) order, so a stable sort orders them by
+    (key, run, position)."""
+    S = len(samples_ord)
+    srt = samples_ord[np.argsort(samples_ord, kind="stable")]
+    idx = [(b * S) // P - 1 for b in range(1, P)]
+    if any(i < 0 for i in idx):
+        raise ValueError("fewer samples than partitions")
+    return srt[np.array(idx, dtype=np.int64)] if idx else srt[:0]
+
+
+def investigator(run_ord: list[np.ndarray], t: np.ndarray, n: int, P: int,
+                 variant: int = INVESTIGATOR_RANK):
+    """Step 4 of Section IV with the investigator of Section IV-B (Fig. 5).
+
+    For splitter t_b on sorted run r: lb[r,b] = #{x < t_b} and cnt[r,b] = #{x = t_b}
+    (two binary searches).  Over all runs, L_b = sum_r lb, G_b = sum_r cnt and
+    pre[r,b] = sum_{r'<r} cnt[r',b].  The global target e_b picks how many stable
+    ranks go to buckets 0..b-1:
+
+    * RANK (default): e_b = clamp(floor(b n / P), L_b, L_b + G_b).  A value that
+      spans several splitters is split at each one's ideal rank, so its range is
+      divided into equal N/P pieces.
+    * EQUAL: a maximal group t_j = ... = t_{j+k-1} of k duplicated splitters gets
+      e_{j+i} = L + floor(G (i+1) / k); a splitter that is not duplicated is cut
+      by plain binary search (upper bound), as the paper states.
+    * OFF: plain upper bound everywhere, e_b = L_b + G_b (Fig. 5(b)).
+
+    Each run gives bucket b its elements of stable rank [e_b, e_{b+1}):
+    cut[r,b] = lb[r,b] + clamp(e_b - L_b - pre[r,b], 0, cnt[r,b]), with
+    cut[r,0] = 0 and cut[r,P] = n_r.  Returns (e, cut, lb, cnt).
+    """
+    R = len(run_ord)
+    lb = np.zeros((R, P + 1), dtype=np.int64)
+    cnt = np.zeros((R, P + 1), dtype=np.int64)
+    for r in range(R):
+        lb[r, 1:P] = np.searchsorted(run_ord[r], t, side="left")
+        cnt[r, 1:P] = np.searchsorted(run_ord[r], t, side="right") - lb[r, 1:P]
+    L = lb.sum(axis=0)
+    G = cnt.sum(axis=0)
+    pre = np.cumsum(cnt, axis=0) - cnt
+
+    e = np.zeros(P + 1, dtype=np.int64)
+    e[P] = n
+    if variant == INVESTIGATOR_RANK:
+        for b in range(1, P):
+            e[b] = min(max((b * n) // P, L[b]), L[b] + G[b])
+    elif variant == INVESTIGATOR_OFF:
+        for b in range(1, P):
+            e[b] = L[b] + G[b]
+    elif variant == INVESTIGATOR_EQUAL:
+        b = 1
+        while b < P:
+            k = 1
+            while b + k < P and t[b + k - 1] == t[b - 1]:
+                k += 1
+            for i in range(k):
+                e[b + i] = L[b] + (G[b] * (i + 1)) // k
+            b += k
+    else:
+        raise ValueError(variant)
+
+    cut = np.zeros((R, P + 1), dtype=np.int64)
+    cut[:, P] = [len(x) for x in run_ord]
+    take = np.clip(e[None, 1:P] - L[None, 1:P] - pre[:, 1:P], 0, cnt[:, 1:P])
+    cut[:, 1:P] = lb[:, 1:P] + take
+    return e, cut, lb, cnt
+
+
+def exchange_offsets(cut: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """Section IV-C: once the ranges are broadcast every receiver knows how much
+    it gets from each sender and writes at an offset.  Segment (r, b) lands at
+    dst[r,b] = e_b + sum_{r'<r} (cut[r',b+1] - cut[r',b])."""
+    R, P1 = cut.shape
+    P = P1 - 1
+    size = cut[:, 1:] - cut[:, :-1]
+    before = np.cumsum(size, axis=0) - size          # sum over r' < r
+    dst = e[None, :P] + before
+    return dst
+
+
+def load_stats(e: np.ndarray) -> dict:
+    """Per-processor data size after the sort (Table II): sizes and max/mean."""
+    sizes = np.diff(e)
+    P = len(sizes)
+    n = int(e[-1])
+    mean = n / P if P else 0.0
+    return {
+        "sizes": sizes,
+        "max": int(sizes.max()) if P else 0,
+        "min": int(sizes.min()) if P else 0,
+        "max_over_mean": (float(sizes.max()) / mean) if mean > 0 else 1.0,
+    }
+
+
+def sample_sort(keys: np.ndarray, vals: np.ndarray | None, P: int, dtype: str,
+                samples_per_run: int | None = None,
+                variant: int = INVESTIGATOR_RANK, threads: int = 32) -> dict:
+    """The six steps of Section IV on P logical processors.
+
+    1. every processor sorts its run (``local_sort``);
+    2. regular samples of each sorted run go to the Master;
+    3. the Master picks P-1 splitters;
+    4. binary searches plus the investigator give each run's send ranges;
+    5. every segment is written at its receive offset (the exchange);
+    6. each receiver merges its P segments with the Fig. 2 schedule.
+
+    Returns every intermediate result and the final keys/vals, which must equal
+    ``stable_sort`` for every investigator variant.
+    """
+    n = len(keys)
+    P = effective_partitions(n, P)
+    wbytes = KEY_BYTES[dtype]
+    s = paper_samples_per_run(P, wbytes) if samples_per_run is None else samples_per_run
+    bounds = run_bounds(n, P)
+
+    # Step 1.
+    runs = []
+    for r in range(P):
+        lo, hi = bounds[r], bounds[r + 1]
+        runs.append(local_sort(keys[lo:hi], None if vals is None else vals[lo:hi], dtype, threads))
+    run_ord = [ord_bits(k, dtype) for k, _ in runs]
+
+    # Step 2.
+    sample_list = [run_ord[r][regular_sample_positions(len(run_ord[r]), s)] for r in range(P)]
+    samples = np.concatenate(sample_list) if sample_list else np.zeros(0, run_ord[0].dtype)
+
+    # Step 3.
+    t = select_splitters(samples, P)
+
+    # Step 4.
+    e, cut, lb, cnt = investigator(run_ord, t, n, P, variant)
+
+    # Step 5.
+    dst = exchange_offsets(cut, e)
+    out_k = np.empty_like(keys)
+    out_v = None if vals is None else np.empty_like(vals)
+    for r in range(P):
+        rk, rv = runs[r]
+        for b in range(P):
+            a, z = cut[r, b], cut[r, b + 1]
+            out_k[dst[r, b]:dst[r, b] + (z - a)] = rk[a:z]
+            if vals is not None:
+                out_v[dst[r, b]:dst[r, b] + (z - a)] = rv[a:z]
+
+    # Step 6.
+    for b in range(P):
+        segs = []
+        for r in range(P):
+            lo = dst[r, b]
+            hi = lo + cut[r, b + 1] - cut[r, b]
+            segs.append((out_k[lo:hi], None if vals is None else out_v[lo:hi]))
+        mk, mv = balanced_merge(segs, dtype)
+        out_k[e[b]:e[b + 1]] = mk
+        if vals is not None:
+            out_v[e[b]:e[b + 1]] = mv
+
+    return {
+        "P": P, "s": s, "bounds": bounds, "samples": samples, "splitters": t,
+        "e": e, "cut": cut, "lb": lb, "cnt": cnt, "dst": dst,
+        "keys": out_k, "vals": out_v, "stats": load_stats(e),
+    }
+
+
+def buckets(keys: np.ndarray, P: int, dtype: str, samples_per_run: int | None = None,
+            variant: int = INVESTIGATOR_RANK) -> dict:
+    """Steps 1-4 only (no exchange, no merge): the bucket vector and cut matrix.
+
+    Step 1 here uses a plain stable sort of each run, which the local_sort tests
+    show to be the same result as the Fig. 2 thread merge.
+    """
+    n = len(keys)
+    P = effective_partitions(n, P)
+    s = paper_samples_per_run(P, KEY_BYTES[dtype]) if samples_per_run is None else samples_per_run
+    bounds = run_bounds(n, P)
+    o = ord_bits(keys, dtype)
+    run_ord = [np.sort(o[bounds[r]:bounds[r + 1]], kind="stable") for r in range(P)]
+    samples = np.concatenate([run_ord[r][regular_sample_positions(len(run_ord[r]), s)]
+                              for r in range(P)])
+    t = select_splitters(samples, P)
+    e, cut, lb, cnt = investigator(run_ord, t, n, P, variant)
+    return {"P": P, "s": s, "bounds": bounds, "splitters": t, "e": e, "cut": cut,
+            "stats": load_stats(e)}
