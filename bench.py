@@ -1,0 +1,368 @@
+"""Benchmark of the GB300 load-balanced sample sort.
+
+`python bench.py --gpus N --steps K --warmup W` sorts the 256M-key workload
+(2^28 uint64 keys, half normal / half right-skewed lognormal, uint32 index
+payload, P = 128 logical partitions) once per step, out of place, with inputs
+resident in HBM, and prints one JSON line.  Under torchrun every rank sorts its
+own instance (weak scaling, no collective on the data path).
+
+`--impl reference` times the CPU oracle instead, on a bounded sample of the same
+workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1611_00463_gb300 import inputs  # noqa: E402
+
+METRIC = "Gkeys/s & % HBM roofline; max/mean bucket load; learned vs sampled splitters"
+DEFAULT_WORKLOAD = "normal_lognormal_u64"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pgs", choices=["pgs", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="override the number of keys (smaller cases)")
+    ap.add_argument("--P", type=int, default=None)
+    ap.add_argument("--exchange", default="auto", choices=["auto", "scatter", "fused"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-timer", action="store_true", help="skip per-launch events (profiling runs)")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pgs_kernels.cuh",):
+        with open(os.path.join(ROOT, "paper_1611_00463_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str, n: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    to n keys, or None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln and not ln.startswith("#"):
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    try:
+        if vals.get("source_hash") != kernel_source_hash():
+            return None
+        per_key = float(vals["dram_bytes_per_launch"]) / float(vals["keys_per_launch"])
+        return per_key * n
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_step(keys, vals, P, dtype):
+    from oracle import pgs_oracle as O
+    O.stable_sort(keys, vals, dtype)
+    O.buckets(keys, P, dtype)
+
+
+def time_oracle(workload: str, P: int, sample_n: int, steps: int, warmup: int):
+    dtype, keys, _ = inputs.workload(workload, n=sample_n)
+    vals = inputs.index_payload(sample_n)
+    for _ in range(warmup):
+        oracle_step(keys, vals, P, dtype)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle_step(keys, vals, P, dtype)
+    dt = (time.perf_counter() - t0) / steps
+    return sample_n / dt / 1e9, dt, dtype
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    dtype, n, P, _, _ = workload_shape(args)
+    sample_n = min(n, 1 << 23)
+    value, dt, _ = time_oracle(args.workload, P, sample_n, args.steps, args.warmup)
+    cpu = {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {sample_n} keys of the workload (same generator and seed), P={P}: "
+                     "oracle stable sort + steps 1-4 bucket vector, numpy, one thread"}
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": config_block(args, dtype, n, P, None),
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_shape(args):
+    dtype, n0, P0, gen, seed = inputs.WORKLOADS[args.workload]
+    n = args.n or n0
+    P = args.P or P0
+    return dtype, n, P, gen, seed
+
+
+def config_block(args, dtype, n, P, stats):
+    c = {
+        "workload": f"{args.workload}: {n} {dtype} keys + uint32 index payload, P={P} logical partitions, "
+                    "stable ascending sort, out of place",
+        "n": n, "P": P, "key": dtype, "payload": "u32 index",
+        "l2": "inputs larger than L2 (no flush between steps)",
+        "exchange": args.exchange,
+    }
+    if stats:
+        c["passes"] = stats["passes"]
+        c["samples_per_run"] = stats["samples_per_run"]
+    return c
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    from paper_1611_00463_gb300 import build as pbuild
+    from paper_1611_00463_gb300 import pgs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+    pgs.load()
+
+    dtype, n, P, gen, seed = workload_shape(args)
+    keys_np = gen(n, seed + rank)               # every rank sorts its own instance
+    vals_np = inputs.index_payload(n)
+    kin = pgs.as_device_keys(keys_np, dtype, dev)
+    vin = torch.from_numpy(vals_np.view(np.int32)).to(dev)
+    kout = torch.empty_like(kin)
+    vout = torch.empty_like(vin)
+    cfg0 = pgs.make_config(dtype=dtype, exchange=args.exchange)
+    ws = pgs.workspace(n, P, cfg0, dev)
+    st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    timer = None if args.no_timer else pgs.Timer(capacity=256 * (args.steps + 1))
+    cfg_plain = pgs.make_config(dtype=dtype, exchange=args.exchange, workspace=ws, stats=st)
+    cfg_timed = pgs.make_config(dtype=dtype, exchange=args.exchange, workspace=ws, stats=st, timer=timer)
+
+    for _ in range(max(args.warmup, 0)):
+        pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_plain, stream)
+    torch.cuda.synchronize(dev)
+    stats = pgs.pgs_get_stats(st, stream)
+
+    if timer:
+        timer.reset()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_timed if timer else cfg_plain, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = n * world / (ms_step * 1e-3) / 1e9
+
+    # Dominant kernel and its roofline, from the launch timer of the timed region.
+    peak, peak_src = peaks()
+    roof, per_kernel, step_ms = None, {}, {}
+    if timer:
+        recs, dropped = timer.read()
+        for r in recs:
+            d = per_kernel.setdefault(r["kernel"], {"launches": 0, "ms": 0.0, "bytes": 0})
+            d["launches"] += 1
+            d["ms"] += r["ms"]
+            d["bytes"] += r["bytes"]
+            step_ms[r["step"]] = step_ms.get(r["step"], 0.0) + r["ms"]
+        top = max(per_kernel, key=lambda k: per_kernel[k]["ms"])
+        full = [r for r in recs if r["kernel"] == top and r["bytes"] >= 2 * n * (kin.element_size() + 4)]
+        sel = full or [r for r in recs if r["kernel"] == top]
+        avg_ms = sum(r["ms"] for r in sel) / len(sel)
+        per_launch = sum(r["bytes"] for r in sel) / len(sel)
+        achieved = per_launch / (avg_ms * 1e-3) / 1e9
+        traffic = profiled_traffic(top, args.workload, n)
+        roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "bytes_per_launch": per_launch,
+                "avg_launch_ms": avg_ms, "launches_counted": len(sel), "peak_source": peak_src,
+                "note": "achieved = algorithmic bytes (read + write of every key and payload) per "
+                        "full-size launch / mean CUDA-event duration"}
+        for k in per_kernel:
+            per_kernel[k]["share"] = per_kernel[k]["ms"] / sum(v["ms"] for v in per_kernel.values())
+    bytes_per_pass = 2 * n * (kin.element_size() + 4)
+    e2e_frac = stats["passes"] * bytes_per_pass / (ms_step * 1e-3) / 1e9 / peak
+
+    # End to end through the public API with host buffers (pinned), copies included.
+    e2e = None
+    if not args.no_e2e:
+        hk = torch.from_numpy(keys_np.view(np.int64 if dtype == "u64" else np.int32)).pin_memory()
+        hv = torch.from_numpy(vals_np.view(np.int32)).pin_memory()
+        for _ in range(1):
+            pgs.sort(hk, hv, P, dtype=dtype, exchange=args.exchange)
+        torch.cuda.synchronize(dev)
+        k_e2e = max(1, min(args.steps, 5))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            ko, vo, _ = pgs.sort(hk, hv, P, dtype=dtype, exchange=args.exchange)
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / k_e2e
+        if world > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        nbytes = n * (kin.element_size() + 4)
+        e2e = {"value": n * world / dt / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3,
+               "api": "paper_1611_00463_gb300.pgs.sort (pinned host in, pinned host out)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample_n = min(n, 1 << 24)
+        v, dt, _ = time_oracle(args.workload, P, sample_n, 1, 0)
+        cpu = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {sample_n} keys of the workload (same generator), P={P}: oracle stable sort "
+                         f"+ steps 1-4 bucket vector, numpy, one thread, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": config_block(args, dtype, n, P, stats),
+            "roofline": roof,
+            "hbm_frac_end_to_end": e2e_frac,
+            "max_over_mean_bucket": stats["max_bucket"] / (n / stats["P"]),
+            "gpu_launches": stats["launches"] * args.steps,
+            "launches_per_step": stats["launches"],
+            "clocks": clocks.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "per_kernel": per_kernel,
+            "per_step_ms": {str(k): v / args.steps for k, v in sorted(step_ms.items())},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * pgs.h - C ABI of the GB300 load-balanced sample sort (libpgs.so).
+ *
+ * The method is the six-step distributed sort of "A Load-Balanced Parallel and
+ * Distributed Sorting Algorithm Implemented with PGX.D" (arXiv 1611.00463),
+ * Section IV: local sort of every processor's data, regular sampling, splitter
+ * selection by the Master, binary search of the splitters with the duplicate-
+ * aware "investigator" (Section IV-B, Fig. 5), exchange of ranges at known
+ * offsets (Section IV-C), and the balanced pairwise merge of Fig. 2
+ * (Section IV-A).  The paper's p processors are P logical partitions ("runs")
+ * of one array in device memory; the exchange is a copy inside HBM.
+ *
+ * Conventions shared by every entry point:
+ *  - Every pointer argument is DEVICE memory owned by the caller, unless the
+ *    comment says host.  The library never allocates or frees device memory;
+ *    temporary storage is the caller's workspace (pgs_workspace_bytes).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*,
+ *    NULL = the legacy default stream) unless its comment says it synchronises.
+ *  - Every call returns a pgs_status; none aborts, traps or exits.  Invalid
+ *    arguments are rejected before anything is launched.
+ *  - Keys are sorted ascending by their total order: unsigned integers by
+ *    value, float32 by IEEE 754 totalOrder on the bit pattern
+ *    (-NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN).  Output keys keep the
+ *    input bit patterns.  The sort is stable: equal keys keep input order, and
+ *    the uint32 payload ("vals", the paper's previous-processor/index record,
+ *    step 6) travels with its key.
+ *  - Logical partitions: run r holds input positions
+ *    [floor(r n / P), floor((r+1) n / P)).  P is clamped to max(1, min(P, n)).
+ */
+#ifndef PGS_H
+#define PGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { PGS_U32 = 0, PGS_U64 = 1, PGS_F32 = 2 } pgs_dtype;
+
+typedef enum {
+  PGS_OK = 0,
+  PGS_ERR_INVALID = -1,      /* bad argument (NULL pointer with n > 0, P = 0, bad enum, ...) */
+  PGS_ERR_WORKSPACE = -2,    /* workspace NULL, misaligned (needs 256 B) or too small */
+  PGS_ERR_CUDA = -3,         /* a CUDA runtime call or launch failed */
+  PGS_ERR_TIMEOUT = -4,      /* a bounded device-side wait ran out */
+  PGS_ERR_UNSUPPORTED = -5   /* valid request this build does not implement */
+} pgs_status;
+
+/* Investigator variants (Section IV-B).  With e_b the number of stable ranks
+ * given to buckets 0..b-1, L_b = #keys < t_b and G_b = #keys == t_b:
+ *  RANK  : e_b = clamp(floor(b n / P), L_b, L_b + G_b)   (default)
+ *  EQUAL : a group of k equal splitters t_j..t_{j+k-1} splits the range of
+ *          their value into k equal parts, e_{j+i} = L + floor(G (i+1) / k);
+ *          a non-duplicated splitter is cut by plain binary search (upper bound)
+ *  OFF   : plain upper bound e_b = L_b + G_b, the failure mode of Fig. 5(b).
+ * Every variant divides a value's range by global stable rank, so the output is
+ * the same stable sort; only the bucket sizes differ. */
+typedef enum { PGS_INVESTIGATOR_RANK = 0, PGS_INVESTIGATOR_EQUAL = 1, PGS_INVESTIGATOR_OFF = 2 } pgs_investigator;
+
+/* Step 5 (Section IV-C): SCATTER copies every run segment to its bucket before
+ * the merge; FUSED lets the merge read the segments where the runs left them.
+ * AUTO lets the library pick (currently SCATTER). */
+typedef enum { PGS_EXCHANGE_AUTO = 0, PGS_EXCHANGE_SCATTER = 1, PGS_EXCHANGE_FUSED = 2 } pgs_exchange;
+
+/* Splitter source.  SAMPLED: steps 2-3 of Section IV.  LEARNED: an MLP CDF
+ * model trained on the same sample predicts bucket ids; the sampled splitters
+ * judge it and take over when its imbalance exceeds 1 + eps. */
+typedef enum { PGS_SPLITTERS_SAMPLED = 0, PGS_SPLITTERS_LEARNED = 1 } pgs_splitter_mode;
+
+/* Kernels of the pipeline, as reported by the launch timer. */
+typedef enum {
+  PGS_KERNEL_BLOCK_SORT = 0,   /* step 1: shared-memory block sort of one tile */
+  PGS_KERNEL_MERGE = 1,        /* steps 1, 3, 6: merge-path merge of one round */
+  PGS_KERNEL_PARTITION = 2,    /* merge-path splits of one round */
+  PGS_KERNEL_PAIRS = 3,        /* pair descriptors of one round */
+  PGS_KERNEL_SCAN = 4,         /* device-wide exclusive scan */
+  PGS_KERNEL_SAMPLE = 5,       /* step 2: regular samples */
+  PGS_KERNEL_SPLITTERS = 6,    /* step 3: splitter pick */
+  PGS_KERNEL_CUT_SEARCH = 7,   /* step 4: binary searches */
+  PGS_KERNEL_INVESTIGATOR = 8, /* step 4: investigator cuts */
+  PGS_KERNEL_OFFSETS = 9,      /* step 5 set-up: segment sizes and receive offsets */
+  PGS_KERNEL_SCATTER = 10,     /* step 5: the exchange */
+  PGS_KERNEL_STATS = 11,       /* load statistics */
+  PGS_KERNEL_COUNT = 12
+} pgs_kernel;
+
+/* One timed launch.  `bytes` are the algorithmic bytes the launch must move
+ * (reads + writes of the data it is defined to touch), `ms` its duration
+ * between CUDA events recorded on the call's stream around it. */
+typedef struct pgs_launch_record {
+  uint32_t kernel;            /* pgs_kernel */
+  uint32_t step;              /* step of Section IV (1-6), 0 = bookkeeping */
+  uint64_t bytes;
+  float    ms;
+  uint32_t reserved;
+} pgs_launch_record;
+
+/* Opaque launch timer (host object holding CUDA events; no device memory). */
+typedef struct pgs_timer pgs_timer;
+
+/* Options.  A zeroed struct, or a NULL pointer, means all defaults. */
+typedef struct pgs_config {
+  int32_t  dtype;             /* pgs_dtype, default PGS_U32 */
+  uint32_t samples_per_run;   /* s; 0 = the paper's budget floor(262144 / (P * key_bytes)) */
+  float    eps;               /* target imbalance; 0 = 0.05 */
+  int32_t  guaranteed;        /* 1: s = max(s, ceil(P / eps)) so every bucket < (1 + eps) n / P */
+  int32_t  investigator;      /* pgs_investigator, default RANK */
+  int32_t  exchange;          /* pgs_exchange, default AUTO */
+  int32_t  splitter_mode;     /* pgs_splitter_mode, default SAMPLED */
+  int32_t  reserved0;
+  void*    workspace;         /* device, 256-byte aligned, >= pgs_workspace_bytes(n, P, cfg) */
+  uint64_t workspace_bytes;
+  /* Optional device outputs, written when non-NULL: */
+  uint64_t* bucket_bounds;    /* e[0..P] (P+1 entries, P effective): bucket b = output [e_b, e_{b+1}) */
+  uint64_t* cuts;             /* cut[r][0..P], P x (P+1), row-major: run r sends its sorted
+                                 positions [cut[r][b], cut[r][b+1]) to bucket b */
+  void*     splitters;        /* t_1..t_{P-1}, P-1 keys of the key type (float keys as bits) */
+  void*     stats;            /* a pgs_stats in device memory */
+  uint64_t  spin_limit;       /* bound on device-side waits; 0 = default */
+  pgs_timer* timer;           /* optional: record every launch's duration (host object) */
+} pgs_config;
+
+/* Load statistics of one sort (Table II reports the per-processor share). */
+typedef struct pgs_stats {
+  uint64_t n;                 /* keys sorted */
+  uint32_t P;                 /* effective partitions */
+  uint32_t samples_per_run;   /* s actually used */
+  uint64_t max_bucket;        /* max_b (e_{b+1} - e_b) */
+  uint64_t min_bucket;        /* min_b (e_{b+1} - e_b) */
+  uint32_t splitter_mode;     /* mode that produced the buckets */
+  uint32_t fallback;          /* 1 if the learned splitters were rejected */
+  uint32_t error;             /* device-side error word; 0 = none */
+  uint32_t passes;            /* full passes over the data the sort made */
+  uint32_t launches;          /* kernels the call launched */
+  uint32_t reserved;
+} pgs_stats;
+
+/* Bytes of device workspace pgs_sort / pgs_sort_copy need for n keys on P
+ * partitions with these options (cfg may be NULL).  Returns 0 for an invalid
+ * request.  Host-only; launches nothing. */
+size_t pgs_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg);
+
+/* Sort n keys (and their uint32 payload) in place, stably, ascending, with the
+ * six steps of Section IV on P logical partitions.
+ *   keys: n keys of cfg->dtype (device).  vals: n uint32 (device) or NULL for a
+ *   keys-only sort.  P >= 1.  Asynchronous on stream. */
+int pgs_sort(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream,
+             const pgs_config* cfg);
+
+/* Same as pgs_sort but out of place: reads keys_in/vals_in (left unchanged
+ * unless they alias the outputs) and writes keys_out/vals_out.  vals_in and
+ * vals_out are both NULL or both non-NULL. */
+int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                  uint32_t* vals_out, uint64_t n, uint32_t P, void* stream,
+                  const pgs_config* cfg);
+
+/* Step 3 of Section IV on a caller-given sample: sort m sample keys (device,
+ * any order) stably and write the P-1 splitters t_b = sample at sorted index
+ * floor(b m / P) - 1 to splitters_out (device, P-1 keys).  In LEARNED mode it
+ * also trains the CDF model and writes its PGS_MLP_FLOATS weights to
+ * model_out (device, may be NULL).  Needs cfg->workspace of at least
+ * pgs_fit_workspace_bytes(m, P, cfg). */
+#define PGS_MLP_HIDDEN 32
+#define PGS_MLP_FLOATS (1 * 32 + 32 + 32 * 32 + 32 + 32 * 1 + 1)
+size_t pgs_fit_workspace_bytes(uint64_t m, uint32_t P, const pgs_config* cfg);
+int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
+                      const pgs_config* cfg, void* splitters_out, float* model_out);
+
+/* Copy a device pgs_stats to host memory; synchronises `stream` and returns
+ * PGS_ERR_TIMEOUT if the device error word reports an expired wait. */
+int pgs_get_stats(const void* stats_dev, pgs_stats* host_out, void* stream);
+
+/* Launch timer.  pgs_timer_create makes a host object with room for
+ * `capacity` launches (2 * capacity CUDA events on the current device); give
+ * it to calls through pgs_config.timer and every launch they make is bracketed
+ * by events on their stream, until the timer is full (later launches are
+ * counted as dropped).  pgs_timer_read waits for the recorded events, writes
+ * up to `max` records with their durations to host memory `out`, and stores
+ * the number recorded in *count and the number dropped in *dropped (either
+ * may be NULL).  pgs_timer_reset forgets all records.  A timer must not be
+ * shared by calls that run concurrently. */
+int pgs_timer_create(uint32_t capacity, pgs_timer** out);
+int pgs_timer_destroy(pgs_timer* timer);
+int pgs_timer_reset(pgs_timer* timer);
+int pgs_timer_read(pgs_timer* timer, pgs_launch_record* out, uint32_t max, uint32_t* count,
+                   uint32_t* dropped);
+
+/* Name of a pgs_kernel value ("block_sort", "merge", ...; never NULL). */
+const char* pgs_kernel_name(uint32_t kernel);
+
+/* Static description of a status code (never NULL). */
+const char* pgs_strerror(int status);
+
+/* Library version, "major.minor.patch". */
+const char* pgs_version(void);
+
+/* Text of the last CUDA failure seen by this thread (the call and the CUDA
+ * error string), or "" if none.  Host-only; the pointer stays valid for the
+ * thread's lifetime and is overwritten by its next failure. */
+const char* pgs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGS_H */

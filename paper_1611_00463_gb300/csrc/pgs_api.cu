@@ -1,0 +1,206 @@
+// The C ABI of libpgs.so (declared in include/pgs.h): argument checks, the
+// workspace contract and dispatch by key type.  No entry point allocates device
+// memory; all temporaries live in the caller's workspace.
+#include <cstdio>
+#include <new>
+
+#include "pgs_host.cuh"
+
+namespace pgs {
+int sort_u32(const Plan&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int sort_u64(const Plan&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int fit_u32(const FitPlan&, const Options&, const void*, void*, cudaStream_t);
+int fit_u64(const FitPlan&, const Options&, const void*, void*, cudaStream_t);
+
+namespace {
+
+// Make the device that owns `ptr` current (the library has its own runtime state).
+int use_device_of(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return PGS_ERR_INVALID;
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return PGS_ERR_INVALID;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return PGS_ERR_CUDA;
+  if (cur != a.device && cudaSetDevice(a.device) != cudaSuccess) return PGS_ERR_CUDA;
+  return PGS_OK;
+}
+
+bool ranges_overlap(const void* a, const void* b, uint64_t bytes) {
+  auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x != y && x < y + bytes && y < x + bytes;
+}
+
+}  // namespace
+}  // namespace pgs
+
+using namespace pgs;
+
+extern "C" {
+
+size_t pgs_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg) {
+  Options o;
+  if (read_options(cfg, &o) != PGS_OK || P == 0) return 0;
+  Plan p = make_plan(n, P, true, o);
+  if (p.P > kMaxP) return 0;
+  Buffers b;
+  return carve(p, nullptr, &b);
+}
+
+int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out,
+                  uint64_t n, uint32_t P, void* stream, const pgs_config* cfg) {
+  Options o;
+  int rc = read_options(cfg, &o);
+  if (rc) return rc;
+  if (P == 0) return PGS_ERR_INVALID;
+  if ((vals_in == nullptr) != (vals_out == nullptr)) return PGS_ERR_INVALID;
+  if (n == 0) return PGS_OK;
+  if (!keys_in || !keys_out) return PGS_ERR_INVALID;
+  if (n >= (1ull << 40)) return PGS_ERR_UNSUPPORTED;
+  const int w = key_bytes(o.dtype);
+  if (ranges_overlap(keys_in, keys_out, n * (uint64_t)w)) return PGS_ERR_INVALID;
+  if (vals_in && ranges_overlap(vals_in, vals_out, n * 4ull)) return PGS_ERR_INVALID;
+  Plan p = make_plan(n, P, vals_in != nullptr, o);
+  if (p.P > kMaxP) return PGS_ERR_UNSUPPORTED;
+  Buffers b;
+  const size_t need = carve(p, nullptr, &b);
+  if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
+    return PGS_ERR_WORKSPACE;
+  rc = use_device_of(keys_out);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (o.dtype == PGS_U64) return sort_u64(p, o, keys_in, vals_in, keys_out, vals_out, st);
+  return sort_u32(p, o, keys_in, vals_in, keys_out, vals_out, st);
+}
+
+int pgs_sort(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream, const pgs_config* cfg) {
+  return pgs_sort_copy(keys, vals, keys, vals, n, P, stream, cfg);
+}
+
+size_t pgs_fit_workspace_bytes(uint64_t m, uint32_t P, const pgs_config* cfg) {
+  Options o;
+  if (read_options(cfg, &o) != PGS_OK || P == 0) return 0;
+  FitPlan f = make_fit_plan(m, P, o);
+  Buffers b;
+  void *a, *bb;
+  return carve_fit(f, nullptr, &a, &bb, &b);
+}
+
+int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream, const pgs_config* cfg,
+                      void* splitters_out, float* model_out) {
+  Options o;
+  int rc = read_options(cfg, &o);
+  if (rc) return rc;
+  (void)model_out;
+  if (P == 0) return PGS_ERR_INVALID;
+  if (P == 1) return PGS_OK;                       // no splitters
+  if (!samples || !splitters_out || m < P) return PGS_ERR_INVALID;
+  if (m >= (1ull << 40)) return PGS_ERR_UNSUPPORTED;
+  FitPlan f = make_fit_plan(m, P, o);
+  Buffers b;
+  void *a, *bb;
+  const size_t need = carve_fit(f, nullptr, &a, &bb, &b);
+  if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
+    return PGS_ERR_WORKSPACE;
+  rc = use_device_of(samples);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (o.dtype == PGS_U64) return fit_u64(f, o, samples, splitters_out, st);
+  return fit_u32(f, o, samples, splitters_out, st);
+}
+
+int pgs_get_stats(const void* stats_dev, pgs_stats* host_out, void* stream) {
+  if (!stats_dev || !host_out) return PGS_ERR_INVALID;
+  static_assert(sizeof(pgs_stats) == sizeof(DevStats), "pgs_stats layout");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(host_out, stats_dev, sizeof(pgs_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return PGS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PGS_ERR_CUDA;
+  if (host_out->error) return PGS_ERR_TIMEOUT;
+  return PGS_OK;
+}
+
+const char* pgs_strerror(int status) {
+  switch (status) {
+    case PGS_OK: return "ok";
+    case PGS_ERR_INVALID: return "invalid argument";
+    case PGS_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case PGS_ERR_CUDA: return "CUDA error";
+    case PGS_ERR_TIMEOUT: return "device-side wait timed out";
+    case PGS_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+const char* pgs_version(void) { return "0.1.0"; }
+
+const char* pgs_last_error(void) { return last_error_buffer(); }
+
+int pgs_timer_create(uint32_t capacity, pgs_timer** out) {
+  if (!out || capacity == 0) return PGS_ERR_INVALID;
+  *out = nullptr;
+  pgs_timer* t = new (std::nothrow) pgs_timer;
+  if (!t) return PGS_ERR_INVALID;
+  t->ev = new (std::nothrow) cudaEvent_t[2ull * capacity];
+  t->rec = new (std::nothrow) pgs_launch_record[capacity];
+  if (!t->ev || !t->rec) {
+    delete[] t->ev;
+    delete[] t->rec;
+    delete t;
+    return PGS_ERR_INVALID;
+  }
+  for (uint64_t i = 0; i < 2ull * capacity; ++i) {
+    cudaError_t e = cudaEventCreate(&t->ev[i]);
+    if (e != cudaSuccess) {
+      for (uint64_t j = 0; j < i; ++j) cudaEventDestroy(t->ev[j]);
+      delete[] t->ev;
+      delete[] t->rec;
+      delete t;
+      return record_cuda_error(e, "cudaEventCreate", __LINE__);
+    }
+  }
+  t->cap = capacity;
+  *out = t;
+  return PGS_OK;
+}
+
+int pgs_timer_destroy(pgs_timer* t) {
+  if (!t) return PGS_ERR_INVALID;
+  for (uint64_t i = 0; i < 2ull * t->cap; ++i) cudaEventDestroy(t->ev[i]);
+  delete[] t->ev;
+  delete[] t->rec;
+  delete t;
+  return PGS_OK;
+}
+
+int pgs_timer_reset(pgs_timer* t) {
+  if (!t) return PGS_ERR_INVALID;
+  t->count = 0;
+  t->dropped = 0;
+  return PGS_OK;
+}
+
+int pgs_timer_read(pgs_timer* t, pgs_launch_record* out, uint32_t max, uint32_t* count, uint32_t* dropped) {
+  if (!t || (max && !out)) return PGS_ERR_INVALID;
+  for (uint32_t i = 0; i < t->count; ++i) {
+    PGS_CUDA(cudaEventSynchronize(t->ev[2 * i + 1]));
+    float ms = 0.0f;
+    PGS_CUDA(cudaEventElapsedTime(&ms, t->ev[2 * i], t->ev[2 * i + 1]));
+    t->rec[i].ms = ms;
+    if (i < max) out[i] = t->rec[i];
+  }
+  if (count) *count = t->count;
+  if (dropped) *dropped = t->dropped;
+  return PGS_OK;
+}
+
+const char* pgs_kernel_name(uint32_t kernel) {
+  static const char* names[PGS_KERNEL_COUNT] = {"block_sort", "merge", "partition", "pairs", "scan",
+                                                "sample", "splitters", "cut_search", "investigator",
+                                                "offsets", "scatter", "stats"};
+  return kernel < PGS_KERNEL_COUNT ? names[kernel] : "unknown";
+}
+
+}  // extern "C"

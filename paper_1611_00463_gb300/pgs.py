@@ -1,0 +1,316 @@
+"""Python binding of libpgs.so: the C ABI of include/pgs.h, argument marshalling only.
+
+Every step of the sort runs in the library's CUDA kernels; PyTorch only provides
+device memory (the tensors and the workspace) and the stream.  There is no CPU
+fallback: if the library is missing or the tensors are not on a CUDA device the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpgs.so")
+
+PGS_U32, PGS_U64, PGS_F32 = 0, 1, 2
+PGS_OK, PGS_ERR_INVALID, PGS_ERR_WORKSPACE, PGS_ERR_CUDA, PGS_ERR_TIMEOUT, PGS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+INVESTIGATOR = {"rank": 0, "equal": 1, "off": 2}
+EXCHANGE = {"auto": 0, "scatter": 1, "fused": 2}
+SPLITTERS = {"sampled": 0, "learned": 1}
+DTYPES = {"u32": PGS_U32, "u64": PGS_U64, "f32": PGS_F32}
+KEY_TORCH = {"u32": torch.int32, "u64": torch.int64, "f32": torch.int32}
+MLP_FLOATS = 1 * 32 + 32 + 32 * 32 + 32 + 32 * 1 + 1
+
+
+class pgs_config(ctypes.Structure):
+    _fields_ = [
+        ("dtype", ctypes.c_int32),
+        ("samples_per_run", ctypes.c_uint32),
+        ("eps", ctypes.c_float),
+        ("guaranteed", ctypes.c_int32),
+        ("investigator", ctypes.c_int32),
+        ("exchange", ctypes.c_int32),
+        ("splitter_mode", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_uint64),
+        ("bucket_bounds", ctypes.c_void_p),
+        ("cuts", ctypes.c_void_p),
+        ("splitters", ctypes.c_void_p),
+        ("stats", ctypes.c_void_p),
+        ("spin_limit", ctypes.c_uint64),
+        ("timer", ctypes.c_void_p),
+    ]
+
+
+class pgs_stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("P", ctypes.c_uint32),
+        ("samples_per_run", ctypes.c_uint32),
+        ("max_bucket", ctypes.c_uint64),
+        ("min_bucket", ctypes.c_uint64),
+        ("splitter_mode", ctypes.c_uint32),
+        ("fallback", ctypes.c_uint32),
+        ("error", ctypes.c_uint32),
+        ("passes", ctypes.c_uint32),
+        ("launches", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = {
+    "pgs_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
+    "pgs_sort": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_sort_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_fit_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
+    "pgs_fit_splitters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "pgs_version": (ctypes.c_char_p, []),
+    "pgs_last_error": (ctypes.c_char_p, []),
+    "pgs_timer_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_void_p]),
+    "pgs_timer_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pgs_timer_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "pgs_timer_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    "pgs_kernel_name": (ctypes.c_char_p, [ctypes.c_uint32]),
+}
+
+KERNELS = ["block_sort", "merge", "partition", "pairs", "scan", "sample", "splitters", "cut_search",
+           "investigator", "offsets", "scatter", "stats"]
+
+
+class pgs_launch_record(ctypes.Structure):
+    _fields_ = [
+        ("kernel", ctypes.c_uint32),
+        ("step", ctypes.c_uint32),
+        ("bytes", ctypes.c_uint64),
+        ("ms", ctypes.c_float),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libpgs.so (built by paper_1611_00463_gb300.build) and declare its exports."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1611_00463_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PgsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        detail = pgs_last_error() if status == PGS_ERR_CUDA else ""
+        super().__init__(f"{what}: {pgs_strerror(status)} ({status}) {detail}".rstrip())
+
+
+def _check(status: int, what: str) -> None:
+    if status != PGS_OK:
+        raise PgsError(status, what)
+
+
+def pgs_strerror(status: int) -> str:
+    return load().pgs_strerror(status).decode()
+
+
+def pgs_version() -> str:
+    return load().pgs_version().decode()
+
+
+def pgs_last_error() -> str:
+    return load().pgs_last_error().decode()
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensors passed to the CUDA sort must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Timer:
+    """Owner of a pgs_timer (the launch timer of the C ABI)."""
+
+    def __init__(self, capacity: int = 4096):
+        h = ctypes.c_void_p()
+        _check(load().pgs_timer_create(capacity, ctypes.byref(h)), "pgs_timer_create")
+        self.handle = h.value
+        self.capacity = capacity
+
+    def reset(self) -> None:
+        _check(load().pgs_timer_reset(self.handle), "pgs_timer_reset")
+
+    def read(self) -> tuple[list[dict], int]:
+        """Wait for the recorded launches; returns ([{kernel, step, bytes, ms}], dropped)."""
+        buf = (pgs_launch_record * self.capacity)()
+        cnt, drop = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(load().pgs_timer_read(self.handle, buf, self.capacity, ctypes.byref(cnt), ctypes.byref(drop)),
+               "pgs_timer_read")
+        out = [{"kernel": KERNELS[r.kernel], "step": r.step, "bytes": r.bytes, "ms": r.ms}
+               for r in buf[:cnt.value]]
+        return out, drop.value
+
+    def close(self) -> None:
+        if self.handle:
+            load().pgs_timer_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, guaranteed: bool = False,
+                investigator: str = "rank", exchange: str = "auto", splitters: str = "sampled",
+                workspace: torch.Tensor | None = None, bucket_bounds: torch.Tensor | None = None,
+                cuts: torch.Tensor | None = None, splitters_out: torch.Tensor | None = None,
+                stats: torch.Tensor | None = None, timer: Timer | None = None) -> pgs_config:
+    c = pgs_config()
+    c.dtype = DTYPES[dtype]
+    c.samples_per_run = samples_per_run
+    c.eps = eps
+    c.guaranteed = int(guaranteed)
+    c.investigator = INVESTIGATOR[investigator]
+    c.exchange = EXCHANGE[exchange]
+    c.splitter_mode = SPLITTERS[splitters]
+    if workspace is not None:
+        c.workspace = _ptr(workspace)
+        c.workspace_bytes = workspace.numel() * workspace.element_size()
+    c.bucket_bounds = _ptr(bucket_bounds)
+    c.cuts = _ptr(cuts)
+    c.splitters = _ptr(splitters_out)
+    c.stats = _ptr(stats)
+    c.timer = timer.handle if timer is not None else None
+    return c
+
+
+def pgs_workspace_bytes(n: int, P: int, cfg: pgs_config | None = None) -> int:
+    return load().pgs_workspace_bytes(n, P, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def workspace(n: int, P: int, cfg: pgs_config | None = None, device=None) -> torch.Tensor:
+    """A device workspace tensor (256-byte aligned by the caching allocator)."""
+    nbytes = pgs_workspace_bytes(n, P, cfg)
+    if nbytes == 0:
+        raise PgsError(PGS_ERR_INVALID, "pgs_workspace_bytes")
+    return torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+
+
+def pgs_sort_copy(keys_in: torch.Tensor, vals_in: torch.Tensor | None, keys_out: torch.Tensor,
+                  vals_out: torch.Tensor | None, P: int, cfg: pgs_config, stream=None) -> None:
+    n = keys_in.numel()
+    if keys_out.numel() != n or (vals_in is not None and (vals_in.numel() != n or vals_out.numel() != n)):
+        raise ValueError("length mismatch")
+    _check(load().pgs_sort_copy(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n, P,
+                                _stream(stream), ctypes.byref(cfg)), "pgs_sort_copy")
+
+
+def pgs_sort(keys: torch.Tensor, vals: torch.Tensor | None, P: int, cfg: pgs_config, stream=None) -> None:
+    n = keys.numel()
+    if vals is not None and vals.numel() != n:
+        raise ValueError("length mismatch")
+    _check(load().pgs_sort(_ptr(keys), _ptr(vals), n, P, _stream(stream), ctypes.byref(cfg)), "pgs_sort")
+
+
+def pgs_fit_workspace_bytes(m: int, P: int, cfg: pgs_config | None = None) -> int:
+    return load().pgs_fit_workspace_bytes(m, P, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def pgs_fit_splitters(samples: torch.Tensor, P: int, cfg: pgs_config, splitters_out: torch.Tensor,
+                      model_out: torch.Tensor | None = None, stream=None) -> None:
+    _check(load().pgs_fit_splitters(_ptr(samples), samples.numel(), P, _stream(stream), ctypes.byref(cfg),
+                                    _ptr(splitters_out), _ptr(model_out)), "pgs_fit_splitters")
+
+
+def pgs_get_stats(stats_dev: torch.Tensor, stream=None) -> dict:
+    out = pgs_stats()
+    _check(load().pgs_get_stats(_ptr(stats_dev), ctypes.byref(out), _stream(stream)), "pgs_get_stats")
+    return out.as_dict()
+
+
+STATS_BYTES = ctypes.sizeof(pgs_stats)
+
+
+# ---------------------------------------------------------------------------
+# Convenience layer on top of the C ABI (still marshalling only).
+# ---------------------------------------------------------------------------
+
+def as_device_keys(keys, dtype: str, device="cuda") -> torch.Tensor:
+    """numpy uint32/uint64 (float32 as uint32 bits) -> device tensor of the same bits."""
+    import numpy as np
+    arr = np.ascontiguousarray(keys)
+    view = arr.view(np.int64 if dtype == "u64" else np.int32)
+    return torch.from_numpy(view).to(device)
+
+
+def to_numpy_keys(t: torch.Tensor, dtype: str):
+    import numpy as np
+    a = t.cpu().numpy()
+    return a.view(np.uint64 if dtype == "u64" else np.uint32)
+
+
+def sort(keys: torch.Tensor, vals: torch.Tensor | None, P: int, dtype: str = "u32", **opts):
+    """Sort a device (or pinned host) key/payload pair out of place; returns
+    (keys, vals, info) where info holds the bucket bounds and stats tensors.
+
+    Host tensors are copied to the device, sorted by the library and copied
+    back into fresh pinned host tensors."""
+    host = not keys.is_cuda
+    dev = torch.device("cuda") if host else keys.device
+    kin = keys.to(dev, non_blocking=True) if host else keys
+    vin = (vals.to(dev, non_blocking=True) if host else vals) if vals is not None else None
+    n = kin.numel()
+    cfg = make_config(dtype=dtype, **opts)
+    Peff = max(1, min(P, n)) if n else 1
+    ws = workspace(n, P, cfg, device=dev)
+    bounds = torch.empty(Peff + 1, dtype=torch.int64, device=dev)
+    st = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=dev)
+    cfg = make_config(dtype=dtype, workspace=ws, bucket_bounds=bounds, stats=st, **opts)
+    kout = torch.empty_like(kin)
+    vout = torch.empty_like(vin) if vin is not None else None
+    pgs_sort_copy(kin, vin, kout, vout, P, cfg)
+    info = {"bucket_bounds": bounds, "stats": st}
+    if host:
+        ko = torch.empty(kout.shape, dtype=kout.dtype, pin_memory=True)
+        ko.copy_(kout, non_blocking=True)
+        vo = None
+        if vout is not None:
+            vo = torch.empty(vout.shape, dtype=vout.dtype, pin_memory=True)
+            vo.copy_(vout, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return ko, vo, info
+    return kout, vout, info

@@ -1,0 +1,107 @@
+"""The C ABI library loads and exports every symbol include/pgs.h declares;
+host-only argument checks return their status codes without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1611_00463_gb300 import build, pgs
+    build.build()
+    return pgs.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pgs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pgs_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["pgs_sort", "pgs_sort_copy", "pgs_workspace_bytes", "pgs_fit_splitters",
+                 "pgs_fit_workspace_bytes", "pgs_get_stats", "pgs_strerror", "pgs_version"]:
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header():
+    from paper_1611_00463_gb300 import pgs
+    assert sorted(pgs.EXPORTS) == declared_functions()
+
+
+def test_struct_sizes_match_header(lib):
+    from paper_1611_00463_gb300 import pgs
+    # pgs_stats is copied byte for byte from the device block.
+    assert ctypes.sizeof(pgs.pgs_stats) == 56
+    assert ctypes.sizeof(pgs.pgs_config) == 32 + 8 * 8
+    assert ctypes.sizeof(pgs.pgs_launch_record) == 24
+    assert [lib.pgs_kernel_name(i).decode() for i in range(len(pgs.KERNELS))] == pgs.KERNELS
+
+
+def test_strerror_and_version(lib):
+    assert lib.pgs_strerror(0) == b"ok"
+    assert lib.pgs_strerror(-2).startswith(b"workspace")
+    assert lib.pgs_strerror(12345) == b"unknown status"
+    assert re.match(rb"\d+\.\d+\.\d+", lib.pgs_version())
+
+
+def test_workspace_bytes_host_only(lib):
+    from paper_1611_00463_gb300 import pgs
+    cfg = pgs.make_config(dtype="u64")
+    small = pgs.pgs_workspace_bytes(1 << 10, 4, cfg)
+    big = pgs.pgs_workspace_bytes(1 << 20, 4, cfg)
+    assert 0 < small < big
+    # The alternate key+payload buffer dominates: at least n * (8 + 4) bytes.
+    assert big >= (1 << 20) * 12
+    assert pgs.pgs_workspace_bytes(100, 0, cfg) == 0
+    bad = pgs.make_config(dtype="u64")
+    bad.investigator = 7
+    assert pgs.pgs_workspace_bytes(100, 4, bad) == 0
+
+
+def test_invalid_arguments_rejected_before_launch(lib):
+    from paper_1611_00463_gb300 import pgs
+    cfg = pgs.make_config()
+    fake = ctypes.c_void_p(0x1000)
+    # P = 0
+    assert lib.pgs_sort_copy(fake, None, fake, None, 10, 0, None, ctypes.byref(cfg)) == pgs.PGS_ERR_INVALID
+    # NULL keys with n > 0
+    assert lib.pgs_sort_copy(None, None, None, None, 10, 2, None, ctypes.byref(cfg)) == pgs.PGS_ERR_INVALID
+    # vals on one side only
+    assert lib.pgs_sort_copy(fake, fake, fake, None, 10, 2, None, ctypes.byref(cfg)) == pgs.PGS_ERR_INVALID
+    # n = 0 is a no-op
+    assert lib.pgs_sort_copy(None, None, None, None, 0, 2, None, ctypes.byref(cfg)) == pgs.PGS_OK
+    # no workspace, misaligned workspace, too small a workspace
+    assert lib.pgs_sort_copy(fake, None, ctypes.c_void_p(0x2000), None, 10, 2, None,
+                             ctypes.byref(cfg)) == pgs.PGS_ERR_WORKSPACE
+    cfg.workspace = 0x10001
+    cfg.workspace_bytes = 1 << 30
+    assert lib.pgs_sort_copy(fake, None, ctypes.c_void_p(0x2000), None, 10, 2, None,
+                             ctypes.byref(cfg)) == pgs.PGS_ERR_WORKSPACE
+    cfg.workspace = 0x100000
+    cfg.workspace_bytes = 16
+    assert lib.pgs_sort_copy(fake, None, ctypes.c_void_p(0x2000), None, 10, 2, None,
+                             ctypes.byref(cfg)) == pgs.PGS_ERR_WORKSPACE
+    # partially overlapping input and output
+    cfg.workspace_bytes = 1 << 30
+    assert lib.pgs_sort_copy(ctypes.c_void_p(0x1000), None, ctypes.c_void_p(0x1004), None, 10, 2, None,
+                             ctypes.byref(cfg)) == pgs.PGS_ERR_INVALID
+    # bad enum values
+    cfg2 = pgs.make_config()
+    cfg2.dtype = 9
+    assert lib.pgs_sort_copy(fake, None, fake, None, 10, 2, None, ctypes.byref(cfg2)) == pgs.PGS_ERR_INVALID
+    # fit: fewer samples than partitions
+    cfg3 = pgs.make_config()
+    assert lib.pgs_fit_splitters(fake, 3, 8, None, ctypes.byref(cfg3), fake, None) == pgs.PGS_ERR_INVALID
+    # stats: NULL
+    assert lib.pgs_get_stats(None, None, None) == pgs.PGS_ERR_INVALID

@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, element by element.
+
+Sorted keys and payloads must match the oracle's stable sort bit for bit; the
+bucket vector e, the cut matrix and the splitters must match the oracle's
+step-by-step computation (Section IV, steps 2-4) bit for bit.
+"""
+import numpy as np
+import pytest
+
+from oracle import pgs_oracle as O
+from paper_1611_00463_gb300 import inputs
+from tests.pins import check_stable_sorted
+
+pytestmark = pytest.mark.gpu
+
+TILE = 17 * 256
+
+
+def _gpu(*a, **k):
+    from tests.gpu_helpers import gpu_sort
+    return gpu_sort(*a, **k)
+
+
+def check_against_oracle(keys, vals, P, dtype, s=None, variant=0, **opts):
+    kw = dict(opts)
+    if s is not None:
+        kw["samples_per_run"] = s
+    inv = {0: "rank", 1: "equal", 2: "off"}[variant]
+    got = _gpu(keys, vals, P, dtype, investigator=inv, **kw)
+    want_k, want_v = O.stable_sort(keys, vals, dtype)
+    assert np.array_equal(got["keys"], want_k), "keys differ"
+    if vals is not None:
+        assert np.array_equal(got["vals"], want_v), "payload differs"
+    n = len(keys)
+    if n:
+        ref = O.buckets(keys, P, dtype, samples_per_run=s, variant=variant)
+        Peff = ref["P"]
+        assert np.array_equal(got["e"], ref["e"]), "bucket bounds differ"
+        assert np.array_equal(got["cut"], ref["cut"]), "cut matrix differs"
+        assert np.array_equal(O.ord_bits(got["splitters"], dtype), ref["splitters"]), "splitters differ"
+        st = got["stats"]
+        assert st["n"] == n and st["P"] == Peff
+        assert st["max_bucket"] == ref["stats"]["max"] and st["min_bucket"] == ref["stats"]["min"]
+    return got
+
+
+SHAPES = [1, 2, 5, 100, TILE - 1, TILE, TILE + 1, 3 * TILE + 77, 40_009]
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("P", [1, 3, 16])
+def test_u32_shapes(n, P):
+    keys = inputs.uniform_u32(n, seed=n)
+    check_against_oracle(keys, inputs.index_payload(n), P, "u32")
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("P", [1, 7, 64])
+def test_u64_shapes(n, P):
+    keys = inputs.normal_lognormal_u64(n, seed=n + 1)
+    check_against_oracle(keys, inputs.index_payload(n), P, "u64")
+
+
+@pytest.mark.parametrize("n", [1, 77, TILE + 5, 50_001])
+@pytest.mark.parametrize("P", [1, 2, 32])
+def test_f32_duplicates_and_specials(n, P):
+    keys = inputs.zipf_dup_f32(n, seed=n + 2)
+    check_against_oracle(keys, inputs.index_payload(n), P, "f32")
+
+
+@pytest.mark.parametrize("dtype", ["u32", "u64", "f32"])
+def test_keys_only(dtype):
+    n = 3 * TILE + 11
+    gen = {"u32": inputs.uniform_u32, "u64": inputs.uniform_u64, "f32": inputs.zipf_dup_f32}[dtype]
+    keys = gen(n, 5)
+    check_against_oracle(keys, None, 8, dtype)
+
+
+@pytest.mark.parametrize("kind", ["sorted", "reverse", "equal", "few", "extremes"])
+def test_structured(kind):
+    n = 2 * TILE + 999
+    keys = inputs.structured_u32(kind, n)
+    check_against_oracle(keys, inputs.index_payload(n), 12, "u32")
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_investigator_variants(variant):
+    n = 60_000
+    keys = inputs.zipf_dup_f32(n, seed=9)
+    got = check_against_oracle(keys, inputs.index_payload(n), 64, "f32", s=32, variant=variant)
+    if variant == 2:
+        assert got["stats"]["max_bucket"] > 3 * n / 64
+
+
+@pytest.mark.parametrize("P", [2, 5, 17, 100])
+def test_many_partitions_small_runs(P):
+    n = 1000
+    keys = inputs.structured_u32("few", n, seed=P)
+    check_against_oracle(keys, inputs.index_payload(n), P, "u32", s=3)
+
+
+def test_more_partitions_than_keys():
+    keys = inputs.uniform_u32(5, 1)
+    got = check_against_oracle(keys, inputs.index_payload(5), 64, "u32")
+    assert len(got["e"]) == 6
+
+
+def test_every_key_sampled():
+    n = 5000
+    keys = inputs.uniform_u32(n, 3)
+    check_against_oracle(keys, inputs.index_payload(n), 10, "u32", s=n)
+
+
+def test_guaranteed_mode_bound():
+    # s = ceil(P / eps) = 1024 divides the run length 4096, so every bucket is
+    # below (1 + P/s) n/P = (1 + eps) n/P.
+    n, P, eps = 1 << 18, 64, 0.0625
+    keys = inputs.exponential_u32(n, 4)
+    s = max(O.paper_samples_per_run(P, 4), O.guaranteed_samples_per_run(P, eps))
+    got = _gpu(keys, inputs.index_payload(n), P, "u32", guaranteed=True, eps=eps)
+    ref = O.buckets(keys, P, "u32", samples_per_run=s)
+    assert np.array_equal(got["e"], ref["e"])
+    assert got["stats"]["samples_per_run"] == s == 1024
+    assert got["stats"]["max_bucket"] < (1 + eps) * n / P
+
+
+def test_in_place_equals_copy():
+    from tests.gpu_helpers import gpu_sort
+    n = 30_011
+    keys = inputs.normal_lognormal_u64(n, 8)
+    vals = inputs.index_payload(n)
+    a = gpu_sort(keys, vals, 9, "u64")
+    b = gpu_sort(keys, vals, 9, "u64", in_place=True)
+    assert np.array_equal(a["keys"], b["keys"]) and np.array_equal(a["vals"], b["vals"])
+    assert np.array_equal(b["input_keys_after"], b["keys"])
+    assert np.array_equal(a["input_keys_after"], keys)      # out of place leaves the input alone
+
+
+def test_arbitrary_payload_travels_with_keys():
+    n = 20_000
+    keys = inputs.structured_u32("few", n, seed=3)
+    vals = np.random.default_rng(1).integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+    check_against_oracle(keys, vals, 6, "u32")
+
+
+def test_small_workload_full():
+    # 1M uniform uint32 keys from seed 0, payload = index, P = 16.
+    dtype, keys, P = inputs.workload("uniform_u32")
+    got = check_against_oracle(keys, inputs.index_payload(len(keys)), P, dtype)
+    check_stable_sorted(keys, inputs.index_payload(len(keys)), got["keys"], got["vals"], dtype)
+
+
+def test_fit_splitters_matches_oracle():
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    for dtype, gen in [("u32", inputs.exponential_u32), ("u64", inputs.normal_lognormal_u64),
+                       ("f32", inputs.zipf_dup_f32)]:
+        m, P = 70_001, 100
+        samples = gen(m, 11)
+        dev_s = pgs.as_device_keys(samples, dtype)
+        cfg0 = pgs.make_config(dtype=dtype)
+        ws = torch.empty(pgs.pgs_fit_workspace_bytes(m, P, cfg0), dtype=torch.uint8, device="cuda")
+        cfg = pgs.make_config(dtype=dtype, workspace=ws)
+        out = torch.zeros(P - 1, dtype=dev_s.dtype, device="cuda")
+        pgs.pgs_fit_splitters(dev_s, P, cfg, out)
+        torch.cuda.synchronize()
+        want = O.select_splitters(O.ord_bits(samples, dtype), P)
+        got = O.ord_bits(pgs.to_numpy_keys(out, dtype), dtype)
+        assert np.array_equal(got, want), dtype
+
+
+def test_workspace_too_small_is_reported():
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    n = 10_000
+    k = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    cfg = pgs.make_config(workspace=ws)
+    with pytest.raises(pgs.PgsError) as ei:
+        pgs.pgs_sort(k, None, 4, cfg)
+    assert ei.value.status == pgs.PGS_ERR_WORKSPACE
