@@ -156,6 +156,26 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out,
                   uint32_t* vals_out, uint64_t n, uint32_t P, void* stream,
                   const pgs_config* cfg);
 
+/* pgs_sort without a workspace, for callers that cannot allocate device
+ * memory (an allocator or memory-pool callback, a plug-in whose host owns all
+ * device allocations, a path that must never wait on the driver's allocator).
+ * The paper has no counterpart: this is a deployment variant of pgs_sort.
+ *   Temporary storage is one file-scope device array of
+ *   PGS_STATIC_SCRATCH_BYTES inside the library, present on every GPU that
+ *   loads it until the process exits; the call allocates and frees nothing.
+ *   Limits: n <= PGS_STATIC_MAX_KEYS and P <= PGS_STATIC_MAX_P, otherwise
+ *   PGS_ERR_UNSUPPORTED before anything is launched; cfg->workspace must be
+ *   NULL (PGS_ERR_INVALID otherwise); every other option works as in pgs_sort.
+ *   The first call on a device looks up the array's device address with that
+ *   device current (set-up), so make that first call before any stream capture.
+ *   All calls share the array: two calls whose work overlaps on the GPU race
+ *   and corrupt each other's results; serialise them (one stream). */
+#define PGS_STATIC_MAX_KEYS (1u << 16)
+#define PGS_STATIC_MAX_P 64u
+#define PGS_STATIC_SCRATCH_BYTES (4u << 20)
+int pgs_sort_static(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream,
+                    const pgs_config* cfg);
+
 /* Step 3 of Section IV on a caller-given sample: sort m sample keys (device,
  * any order) stably and write the P-1 splitters t_b = sample at sorted index
  * floor(b m / P) - 1 to splitters_out (device, P-1 keys).  In LEARNED mode it

@@ -71,6 +71,8 @@ EXPORTS = {
                                 ctypes.c_void_p, ctypes.c_void_p]),
     "pgs_sort_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_sort_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "pgs_fit_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
     "pgs_fit_splitters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -244,6 +246,22 @@ def pgs_sort(keys: torch.Tensor, vals: torch.Tensor | None, P: int, cfg: pgs_con
     if vals is not None and vals.numel() != n:
         raise ValueError("length mismatch")
     _check(load().pgs_sort(_ptr(keys), _ptr(vals), n, P, _stream(stream), ctypes.byref(cfg)), "pgs_sort")
+
+
+STATIC_MAX_KEYS = 1 << 16
+STATIC_MAX_P = 64
+
+
+def pgs_sort_static(keys: torch.Tensor, vals: torch.Tensor | None, P: int, cfg: pgs_config | None = None,
+                    stream=None) -> None:
+    """In-place sort that uses the library's own static scratch (no workspace,
+    no allocation); n <= STATIC_MAX_KEYS, P <= STATIC_MAX_P."""
+    n = keys.numel()
+    if vals is not None and vals.numel() != n:
+        raise ValueError("length mismatch")
+    cfg = cfg if cfg is not None else pgs_config()
+    _check(load().pgs_sort_static(_ptr(keys), _ptr(vals), n, P, _stream(stream), ctypes.byref(cfg)),
+           "pgs_sort_static")
 
 
 def pgs_fit_workspace_bytes(m: int, P: int, cfg: pgs_config | None = None) -> int:
