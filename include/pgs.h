@@ -134,7 +134,7 @@ typedef struct pgs_stats {
   uint32_t error;             /* device-side error word; 0 = none */
   uint32_t passes;            /* full passes over the data the sort made */
   uint32_t launches;          /* kernels the call launched */
-  uint32_t reserved;
+  float    max_over_mean;     /* largest bucket / its instance's mean bucket n_i / P_i */
 } pgs_stats;
 
 /* Bytes of device workspace pgs_sort / pgs_sort_copy need for n keys on P
@@ -175,6 +175,35 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out,
 #define PGS_STATIC_SCRATCH_BYTES (4u << 20)
 int pgs_sort_static(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream,
                     const pgs_config* cfg);
+
+/* Batched sort: many independent instances in one launch sequence.  The
+ * paper's library sorts several data sets simultaneously (end of Section
+ * IV-C); here instance i is keys[offsets[i], offsets[i+1]) with its own P_i
+ * logical partitions, and every step of Section IV runs for all instances at
+ * once (one kernel per phase), so the whole batch is about as many launches
+ * as one sort and can be captured in one CUDA graph.
+ *   pgs_batch_create plans a batch on the host: offsets (HOST, num+1
+ *   entries, non-decreasing, offsets[0] = 0), P (HOST, num entries, or NULL
+ *   for the automatic rule pgs_batch_auto_partitions), cfg->dtype and
+ *   with_vals fix the key type and whether a payload travels.  Each P_i is
+ *   clamped to max(1, min(P_i, n_i)) and must stay <= 8192.
+ *   pgs_batch_workspace_bytes: device workspace the batch needs.
+ *   pgs_batch_upload copies the batch's tables into that workspace (256-byte
+ *   aligned) and waits for the copy; call it once per workspace, outside any
+ *   stream capture.
+ *   pgs_sort_batched sorts every instance in place, stably, with the same
+ *   options as pgs_sort (cfg->workspace must be the uploaded workspace; the
+ *   optional outputs bucket_bounds, cuts and splitters are not written for a
+ *   batch).  It only launches kernels on `stream`, so it may be captured.
+ *   pgs_batch_destroy frees the host plan. */
+typedef struct pgs_batch pgs_batch;
+uint32_t pgs_batch_auto_partitions(uint64_t n);   /* clamp(2^floor(log2(n / 65536)), 1, 256) */
+int pgs_batch_create(const uint64_t* offsets, uint32_t num, const uint32_t* P, int with_vals,
+                     const pgs_config* cfg, pgs_batch** out);
+size_t pgs_batch_workspace_bytes(const pgs_batch* batch);
+int pgs_batch_upload(pgs_batch* batch, void* workspace, uint64_t workspace_bytes, void* stream);
+int pgs_sort_batched(pgs_batch* batch, void* keys, uint32_t* vals, void* stream, const pgs_config* cfg);
+int pgs_batch_destroy(pgs_batch* batch);
 
 /* Step 3 of Section IV on a caller-given sample: sort m sample keys (device,
  * any order) stably and write the P-1 splitters t_b = sample at sorted index

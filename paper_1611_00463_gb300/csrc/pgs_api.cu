@@ -7,10 +7,10 @@
 #include "pgs_host.cuh"
 
 namespace pgs {
-int sort_u32(const Plan&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
-int sort_u64(const Plan&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
-int fit_u32(const FitPlan&, const Options&, const void*, void*, cudaStream_t);
-int fit_u64(const FitPlan&, const Options&, const void*, void*, cudaStream_t);
+int sort_u32(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int sort_u64(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int fit_u32(uint64_t, uint32_t, const Options&, const void*, void*, cudaStream_t);
+int fit_u64(uint64_t, uint32_t, const Options&, const void*, void*, cudaStream_t);
 
 namespace {
 
@@ -43,8 +43,8 @@ extern "C" {
 size_t pgs_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg) {
   Options o;
   if (read_options(cfg, &o) != PGS_OK || P == 0) return 0;
-  Plan p = make_plan(n, P, true, o);
-  if (p.P > kMaxP) return 0;
+  Shape p = single_shape(n, P, true, o);
+  if (p.Pmax > kMaxP) return 0;
   Buffers b;
   return carve(p, nullptr, &b);
 }
@@ -62,8 +62,8 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out, 
   const int w = key_bytes(o.dtype);
   if (ranges_overlap(keys_in, keys_out, n * (uint64_t)w)) return PGS_ERR_INVALID;
   if (vals_in && ranges_overlap(vals_in, vals_out, n * 4ull)) return PGS_ERR_INVALID;
-  Plan p = make_plan(n, P, vals_in != nullptr, o);
-  if (p.P > kMaxP) return PGS_ERR_UNSUPPORTED;
+  Shape p = single_shape(n, P, vals_in != nullptr, o);
+  if (p.Pmax > kMaxP) return PGS_ERR_UNSUPPORTED;
   Buffers b;
   const size_t need = carve(p, nullptr, &b);
   if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
@@ -82,10 +82,7 @@ int pgs_sort(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream, c
 size_t pgs_fit_workspace_bytes(uint64_t m, uint32_t P, const pgs_config* cfg) {
   Options o;
   if (read_options(cfg, &o) != PGS_OK || P == 0) return 0;
-  FitPlan f = make_fit_plan(m, P, o);
-  Buffers b;
-  void *a, *bb;
-  return carve_fit(f, nullptr, &a, &bb, &b);
+  return fit_workspace(m, o, nullptr, nullptr);
 }
 
 int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream, const pgs_config* cfg,
@@ -98,17 +95,14 @@ int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
   if (P == 1) return PGS_OK;                       // no splitters
   if (!samples || !splitters_out || m < P) return PGS_ERR_INVALID;
   if (m >= (1ull << 40)) return PGS_ERR_UNSUPPORTED;
-  FitPlan f = make_fit_plan(m, P, o);
-  Buffers b;
-  void *a, *bb;
-  const size_t need = carve_fit(f, nullptr, &a, &bb, &b);
+  const size_t need = fit_workspace(m, o, nullptr, nullptr);
   if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
     return PGS_ERR_WORKSPACE;
   rc = use_device_of(samples);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (o.dtype == PGS_U64) return fit_u64(f, o, samples, splitters_out, st);
-  return fit_u32(f, o, samples, splitters_out, st);
+  if (o.dtype == PGS_U64) return fit_u64(m, P, o, samples, splitters_out, st);
+  return fit_u32(m, P, o, samples, splitters_out, st);
 }
 
 int pgs_get_stats(const void* stats_dev, pgs_stats* host_out, void* stream) {

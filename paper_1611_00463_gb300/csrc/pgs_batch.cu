@@ -1,0 +1,172 @@
+// Batched sort: the host plan of a batch of instances, the upload of its
+// tables, and the launch of the whole pipeline for every instance at once.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pgs_host.cuh"
+
+namespace pgs {
+int batch_attrs_u32(bool vals);
+int batch_attrs_u64(bool vals);
+int batch_u32(const Shape&, const Options&, void*, uint32_t*, cudaStream_t);
+int batch_u64(const Shape&, const Options&, void*, uint32_t*, cudaStream_t);
+}  // namespace pgs
+
+using namespace pgs;
+
+struct pgs_batch {
+  Shape sh;
+  Options o;
+  std::vector<char> tables;   // the table region of the workspace, laid out by carve()
+  size_t tables_bytes = 0;
+  size_t ws_bytes = 0;
+};
+
+extern "C" {
+
+uint32_t pgs_batch_auto_partitions(uint64_t n) {
+  if (n < (1ull << 16)) return 1;
+  uint32_t k = 0;
+  while ((n >> (16 + k + 1)) != 0) ++k;               // floor(log2(n / 2^16))
+  return k >= 8 ? 256u : (1u << k);
+}
+
+int pgs_batch_create(const uint64_t* offsets, uint32_t num, const uint32_t* P, int with_vals,
+                     const pgs_config* cfg, pgs_batch** out) {
+  if (!out) return PGS_ERR_INVALID;
+  *out = nullptr;
+  if (!offsets || num == 0 || offsets[0] != 0) return PGS_ERR_INVALID;
+  Options o;
+  int rc = read_options(cfg, &o);
+  if (rc) return rc;
+  pgs_batch* bt = new (std::nothrow) pgs_batch;
+  if (!bt) return PGS_ERR_INVALID;
+  bt->o = o;
+  Shape& sh = bt->sh;
+  sh.I = num;
+  sh.w = key_bytes(o.dtype);
+  sh.vals = with_vals != 0;
+  sh.n = offsets[num];
+  std::vector<uint64_t> koff(num + 1), mat(num + 1), seg(num + 1), st(num);
+  std::vector<uint32_t> Pv(num), R0(num + 1);
+  uint64_t R = 0, Q = 0, MAT = 0, S = 0, maxlen = 0;
+  uint32_t Pmax = 1;
+  for (uint32_t i = 0; i < num; ++i) {
+    if (offsets[i + 1] < offsets[i]) { delete bt; return PGS_ERR_INVALID; }
+    const uint64_t ni = offsets[i + 1] - offsets[i];
+    uint64_t Pi = P ? P[i] : pgs_batch_auto_partitions(ni);
+    if (Pi == 0) { delete bt; return PGS_ERR_INVALID; }
+    Pi = std::max<uint64_t>(1, std::min<uint64_t>(Pi, ni));
+    if (Pi > kMaxP) { delete bt; return PGS_ERR_UNSUPPORTED; }
+    koff[i] = offsets[i];
+    Pv[i] = (uint32_t)Pi;
+    R0[i] = (uint32_t)R;
+    mat[i] = MAT;
+    seg[i] = Q;
+    st[i] = Pi > 1 ? samples_per_run((uint32_t)Pi, sh.w, o) : 0;
+    for (uint64_t r = 0; r < Pi; ++r) {
+      const uint64_t len = ((r + 1) * ni) / Pi - (r * ni) / Pi;
+      maxlen = std::max(maxlen, len);
+      S += std::min(st[i], len);
+    }
+    R += Pi;
+    Q += Pi * Pi;
+    MAT += Pi * (Pi + 1);
+    Pmax = std::max<uint32_t>(Pmax, (uint32_t)Pi);
+    if (R > 0xFFFFFFF0ull) { delete bt; return PGS_ERR_UNSUPPORTED; }
+  }
+  koff[num] = offsets[num];
+  R0[num] = (uint32_t)R;
+  mat[num] = MAT;
+  seg[num] = Q;
+  sh.R = (uint32_t)R;
+  sh.Pmax = Pmax;
+  sh.Q = Q;
+  sh.MAT = MAT;
+  sh.S = S;
+  sh.maxlen = maxlen;
+  sh.s = 0;
+  finish_shape(sh);
+
+  std::vector<uint64_t> run_off(R + 1);
+  std::vector<uint32_t> run_inst(R);
+  for (uint32_t i = 0; i < num; ++i) {
+    const uint64_t ni = koff[i + 1] - koff[i];
+    for (uint64_t r = 0; r < Pv[i]; ++r) {
+      run_off[R0[i] + r] = koff[i] + (r * ni) / Pv[i];
+      run_inst[R0[i] + r] = i;
+    }
+  }
+  run_off[R] = koff[num];
+
+  // Lay the tables out exactly where carve() puts them in a workspace.
+  Buffers b;
+  bt->ws_bytes = carve(sh, nullptr, &b, &bt->tables_bytes);
+  bt->tables.assign(bt->tables_bytes, 0);
+  carve(sh, bt->tables.data(), &b);
+  std::memcpy(b.koff, koff.data(), koff.size() * sizeof(uint64_t));
+  std::memcpy(b.Pt, Pv.data(), Pv.size() * sizeof(uint32_t));
+  std::memcpy(b.R0, R0.data(), R0.size() * sizeof(uint32_t));
+  std::memcpy(b.mat, mat.data(), mat.size() * sizeof(uint64_t));
+  std::memcpy(b.seg, seg.data(), seg.size() * sizeof(uint64_t));
+  std::memcpy(b.st, st.data(), st.size() * sizeof(uint64_t));
+  std::memcpy(b.run_off, run_off.data(), run_off.size() * sizeof(uint64_t));
+  std::memcpy(b.run_inst, run_inst.data(), run_inst.size() * sizeof(uint32_t));
+  *out = bt;
+  return PGS_OK;
+}
+
+size_t pgs_batch_workspace_bytes(const pgs_batch* bt) { return bt ? bt->ws_bytes : 0; }
+
+int pgs_batch_upload(pgs_batch* bt, void* workspace, uint64_t workspace_bytes, void* stream) {
+  if (!bt) return PGS_ERR_INVALID;
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 || workspace_bytes < bt->ws_bytes)
+    return PGS_ERR_WORKSPACE;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, workspace) != cudaSuccess) {
+    cudaGetLastError();
+    return PGS_ERR_INVALID;
+  }
+  PGS_CUDA(cudaSetDevice(a.device));
+  PGS_TRY(bt->o.dtype == PGS_U64 ? batch_attrs_u64(bt->sh.vals) : batch_attrs_u32(bt->sh.vals));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PGS_CUDA(cudaMemcpyAsync(workspace, bt->tables.data(), bt->tables_bytes, cudaMemcpyHostToDevice, st));
+  PGS_CUDA(cudaStreamSynchronize(st));
+  return PGS_OK;
+}
+
+int pgs_sort_batched(pgs_batch* bt, void* keys, uint32_t* vals, void* stream, const pgs_config* cfg) {
+  if (!bt) return PGS_ERR_INVALID;
+  Options o;
+  int rc = read_options(cfg, &o);
+  if (rc) return rc;
+  if (o.dtype != bt->o.dtype) return PGS_ERR_INVALID;
+  if ((vals != nullptr) != bt->sh.vals) return PGS_ERR_INVALID;
+  if (bt->sh.n == 0) return PGS_OK;
+  if (!keys) return PGS_ERR_INVALID;
+  if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < bt->ws_bytes)
+    return PGS_ERR_WORKSPACE;
+  // Batch options: the sampling and investigator settings fixed at create time,
+  // the per-call outputs of a single sort are not written.
+  Options run = bt->o;
+  run.workspace = o.workspace;
+  run.workspace_bytes = o.workspace_bytes;
+  run.stats = o.stats;
+  run.timer = o.timer;
+  run.investigator = o.investigator;
+  run.bucket_bounds = nullptr;
+  run.cuts = nullptr;
+  run.splitters = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (o.dtype == PGS_U64) return batch_u64(bt->sh, run, keys, vals, st);
+  return batch_u32(bt->sh, run, keys, vals, st);
+}
+
+int pgs_batch_destroy(pgs_batch* bt) {
+  if (!bt) return PGS_ERR_INVALID;
+  delete bt;
+  return PGS_OK;
+}
+
+}  // extern "C"

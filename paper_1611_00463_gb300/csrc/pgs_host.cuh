@@ -84,21 +84,25 @@ struct Carver {
   }
 };
 
-struct Plan {
-  uint64_t n = 0;
-  uint32_t P = 1;                 // effective partitions
-  int w = 4;                      // key bytes
+// Host-side scalars of a batch of sort instances (a single sort is a batch of one).
+struct Shape {
+  uint32_t I = 1;            // instances
+  uint32_t R = 1;            // runs = buckets, sum of P_i
+  uint32_t Pmax = 1;         // largest P_i
+  uint64_t n = 0;            // keys in all instances
+  uint64_t Q = 1;            // bucket segments, sum of P_i^2
+  uint64_t MAT = 2;          // entries of the P x (P+1) matrices, sum of P_i (P_i + 1)
+  uint64_t S = 0;            // samples of all runs
+  uint64_t maxlen = 0;       // longest run
+  uint64_t s = 0;            // samples per run of a single sort (reported in the stats)
+  int w = 4;                 // key bytes
   bool vals = false;
-  uint64_t s = 1;                 // samples per run
-  bool all_samples = false;       // s >= every run length: every key is a sample
-  uint64_t S = 0;                 // total samples
-  uint64_t nmax = 0;              // longest run
-  int run_rounds = 0;             // merge rounds to grow block-sorted tiles into runs
-  int bucket_rounds = 0;          // merge rounds of step 6 (ceil(log2 P))
+  int run_rounds = 0;        // merge rounds growing block-sorted tiles into runs (step 1)
+  int bucket_rounds = 0;     // merge rounds of steps 3 and 6: ceil(log2 Pmax)
   uint64_t max_pairs = 1;
   uint64_t max_tiles = 1;
-  uint64_t scan_len = 1;          // longest array scanned
-  int passes = 0;                 // full passes over the keys
+  uint64_t scan_len = 1;
+  int passes = 0;            // full passes over the keys
 };
 
 inline uint64_t samples_per_run(uint32_t P, int w, const Options& o) {
@@ -111,75 +115,96 @@ inline uint64_t samples_per_run(uint32_t P, int w, const Options& o) {
   return s;
 }
 
-inline Plan make_plan(uint64_t n, uint32_t P_req, bool vals, const Options& o) {
-  Plan p;
-  p.n = n;
-  p.w = key_bytes(o.dtype);
-  p.vals = vals;
-  p.P = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(P_req, n));
-  const uint32_t P = p.P;
-  p.nmax = ceil_div(n, P);
-  const uint64_t nmin = n / P;
-  p.s = samples_per_run(P, p.w, o);
-  p.all_samples = p.s >= p.nmax;
-  p.S = p.all_samples ? n : (uint64_t)P * p.s;
-  (void)nmin;
+// Completes a Shape whose I, R, Pmax, n, Q, MAT, S, maxlen, w and vals are set.
+inline void finish_shape(Shape& sh) {
   uint64_t w = kTile;
-  while (w < p.nmax) { w *= 2; ++p.run_rounds; }
-  p.bucket_rounds = P > 1 ? ceil_log2(P) : 0;
-  // Largest number of pairs in any round.
-  uint64_t mp = 1;
-  for (int k = 0; k < p.run_rounds; ++k)
-    mp = std::max<uint64_t>(mp, (uint64_t)P * ceil_div(p.nmax, 2ull * ((uint64_t)kTile << k)));
-  for (int k = 0; k < p.bucket_rounds; ++k) {
-    uint64_t per = ceil_div(P, 2ull << k);
-    mp = std::max<uint64_t>(mp, (uint64_t)P * per);
-  }
-  p.max_pairs = mp;
-  p.max_tiles = ceil_div(std::max<uint64_t>(n, 1), kTile) + mp + 1;
-  p.scan_len = std::max<uint64_t>(mp, (uint64_t)P * P);
-  p.passes = 1 + p.run_rounds + (P > 1 ? 1 + p.bucket_rounds : 0);
-  return p;
+  sh.run_rounds = 0;
+  while (w < sh.maxlen) { w *= 2; ++sh.run_rounds; }
+  sh.bucket_rounds = sh.Pmax > 1 ? ceil_log2(sh.Pmax) : 0;
+  uint64_t mp = std::max<uint64_t>(sh.R, sh.Q);
+  if (sh.run_rounds > 0) mp = std::max<uint64_t>(mp, (uint64_t)sh.R * ceil_div(sh.maxlen, 2ull * kTile));
+  sh.max_pairs = std::max<uint64_t>(mp, 1);
+  sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeTile) + sh.max_pairs + 1;
+  sh.scan_len = std::max<uint64_t>(sh.max_pairs, sh.Q);
+  sh.passes = 1 + sh.run_rounds + (sh.Pmax > 1 ? 1 + sh.bucket_rounds : 0);
+}
+
+// A single sort of n keys on P_req logical partitions.
+inline Shape single_shape(uint64_t n, uint32_t P_req, bool vals, const Options& o) {
+  Shape sh;
+  sh.n = n;
+  sh.w = key_bytes(o.dtype);
+  sh.vals = vals;
+  const uint32_t P = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(P_req, n));
+  sh.I = 1;
+  sh.R = P;
+  sh.Pmax = P;
+  sh.Q = (uint64_t)P * P;
+  sh.MAT = (uint64_t)P * (P + 1);
+  sh.maxlen = ceil_div(n, P);
+  sh.s = P > 1 ? samples_per_run(P, sh.w, o) : 0;
+  sh.S = P > 1 ? (sh.s >= sh.maxlen ? n : (uint64_t)P * sh.s) : 0;
+  finish_shape(sh);
+  return sh;
 }
 
 // Device buffers inside the workspace.
 struct Buffers {
   void* alt_k; uint32_t* alt_v;
   void* samp_a; void* samp_b; void* spl;
-  uint64_t *lb, *cnt, *cut, *sizes, *off, *e, *sample_off;
+  uint64_t *lb, *cnt, *cut, *sizes, *seg_src, *off, *e;
+  uint64_t *samp_counts, *samp_off;
   Pair* pairs; uint64_t *tcount, *tbegin;
-  uint32_t* tile_pair; uint64_t* part;
+  TileSplit* split;
   uint64_t *scan_sums, *scan_sums2;
   uint64_t* first_seg;
-  DevStats* stats; uint32_t* err;
+  // batch tables
+  uint64_t* koff; uint32_t* Pt; uint32_t* R0; uint64_t* mat; uint64_t* seg; uint64_t* st;
+  uint64_t* run_off; uint32_t* run_inst;
+  uint32_t* err;
+  float* max_ratio;
+  Geo geo(const Shape& sh) const {
+    return Geo{koff, Pt, R0, mat, seg, st, run_off, run_inst, sh.I, sh.R};
+  }
 };
 
-inline size_t carve(const Plan& p, void* base, Buffers* b) {
+// Lays the buffers out in the workspace (base may be NULL to only measure).
+// The tables come first so that a batch can upload them with one copy.
+inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_bytes = nullptr) {
   Carver c(base);
-  const uint64_t P = p.P;
-  b->alt_k = c.take<char>(p.n * p.w);
-  b->alt_v = p.vals ? c.take<uint32_t>(p.n) : nullptr;
-  b->samp_a = c.take<char>(p.S * p.w);
-  b->samp_b = c.take<char>(p.S * p.w);
-  b->spl = c.take<char>(P * p.w);
-  b->lb = c.take<uint64_t>(P * (P + 1));
-  b->cnt = c.take<uint64_t>(P * (P + 1));
-  b->cut = c.take<uint64_t>(P * (P + 1));
-  b->sizes = c.take<uint64_t>(P * P);
-  b->off = c.take<uint64_t>(P * P + 1);
-  b->e = c.take<uint64_t>(P + 1);
-  b->sample_off = c.take<uint64_t>(P + 1);
-  b->pairs = c.take<Pair>(p.max_pairs);
-  b->tcount = c.take<uint64_t>(p.max_pairs);
-  b->tbegin = c.take<uint64_t>(p.max_pairs + 1);
-  b->tile_pair = c.take<uint32_t>(p.max_tiles);
-  b->part = c.take<uint64_t>(p.max_tiles + 1);
-  const uint64_t chunks = ceil_div(p.scan_len, kScanChunk);
+  b->koff = c.take<uint64_t>(sh.I + 1);
+  b->Pt = c.take<uint32_t>(sh.I);
+  b->R0 = c.take<uint32_t>(sh.I + 1);
+  b->mat = c.take<uint64_t>(sh.I + 1);
+  b->seg = c.take<uint64_t>(sh.I + 1);
+  b->st = c.take<uint64_t>(sh.I);
+  b->run_off = c.take<uint64_t>(sh.R + 1);
+  b->run_inst = c.take<uint32_t>(sh.R);
+  if (tables_bytes) *tables_bytes = c.used;
+  b->alt_k = c.take<char>(sh.n * sh.w);
+  b->alt_v = sh.vals ? c.take<uint32_t>(sh.n) : nullptr;
+  b->samp_a = c.take<char>(sh.S * sh.w);
+  b->samp_b = c.take<char>(sh.S * sh.w);
+  b->spl = c.take<char>((uint64_t)sh.R * sh.w);
+  b->lb = c.take<uint64_t>(sh.MAT);
+  b->cnt = c.take<uint64_t>(sh.MAT);
+  b->cut = c.take<uint64_t>(sh.MAT);
+  b->sizes = c.take<uint64_t>(sh.Q);
+  b->seg_src = c.take<uint64_t>(sh.Q);
+  b->off = c.take<uint64_t>(sh.Q + 1);
+  b->e = c.take<uint64_t>((uint64_t)sh.R + sh.I);
+  b->samp_counts = c.take<uint64_t>(sh.R);
+  b->samp_off = c.take<uint64_t>(sh.R + 1);
+  b->pairs = c.take<Pair>(sh.max_pairs);
+  b->tcount = c.take<uint64_t>(sh.max_pairs);
+  b->tbegin = c.take<uint64_t>(sh.max_pairs + 1);
+  b->split = c.take<TileSplit>(sh.max_tiles);
+  const uint64_t chunks = ceil_div(sh.scan_len, kScanChunk);
   b->scan_sums = c.take<uint64_t>(chunks + 1);
   b->scan_sums2 = c.take<uint64_t>(chunks + 1);
-  b->first_seg = c.take<uint64_t>(ceil_div(std::max<uint64_t>(p.n, 1), kScatterTile));
-  b->stats = c.take<DevStats>(1);
+  b->first_seg = c.take<uint64_t>(ceil_div(std::max<uint64_t>(sh.n, 1), kScatterTile));
   b->err = c.take<uint32_t>(1);
+  b->max_ratio = c.take<float>(1);
   return c.used;
 }
 
@@ -283,51 +308,61 @@ template <typename K, bool V>
 inline int set_smem_attrs() {
   PGS_CUDA(cudaFuncSetAttribute(k_block_sort<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(BlockSortSmem<K>)));
-  PGS_CUDA(cudaFuncSetAttribute(k_merge<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sizeof(MergeSmem<K>)));
+  PGS_CUDA(cudaFuncSetAttribute(k_merge_tile<K, V, kMergeNT, kMergeVT>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Merge2Layout<K, V, kMergeNT, kMergeVT>::bytes));
   PGS_CUDA(cudaFuncSetAttribute(k_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ScatterSmem<K>)));
   return PGS_OK;
 }
 
-// One pairwise merge round over pairs already described in b.pairs / b.tcount.
-// `len` keys take part; every one of them is read and written once.
+// One pairwise merge round over pairs already described in b.pairs / b.tcount
+// (tile counts of kMergeTile).  `len` keys take part; every one of them is read
+// and written once.
 template <typename K, bool V>
 inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
                        uint64_t len, const Buffers& b, int f32_out, uint32_t step) {
   PGS_TRY(scan_u64(c, b.tcount, b.tbegin, npairs, b.scan_sums, b.scan_sums2, step));
-  const uint64_t tiles_ub = ceil_div(len, kTile) + npairs;
-  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 24 * ceil_div(len, kTile), [&] {
-    k_partition<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.tile_pair, b.part);
+  const uint64_t tiles_ub = ceil_div(len, kMergeTile) + npairs;
+  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, kMergeTile), [&] {
+    k_partition_split<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.split,
+                                                                    (uint32_t)kMergeTile);
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
+  constexpr size_t smem = Merge2Layout<K, V, kMergeNT, kMergeVT>::bytes;
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
-    k_merge<K, V><<<(unsigned)tiles_ub, kNT, sizeof(MergeSmem<K>), c.st>>>(ks, vs, kd, vd, b.pairs, b.tbegin,
-                                                                          npairs, b.tile_pair, b.part, f32_out);
+    k_merge_tile<K, V, kMergeNT, kMergeVT><<<(unsigned)tiles_ub, kMergeNT, smem, c.st>>>(
+        ks, vs, kd, vd, b.split, b.tbegin + npairs, f32_out, b.err);
   });
 }
 
 // ---------------------------------------------------------------------------
-// The sort: Section IV, steps 1-6.
+// The sort: Section IV, steps 1-6, for every instance of a batch at once.
+// The batch tables must already be in the workspace (k_tables_single for a
+// single sort, or uploaded by the batch API).
 // ---------------------------------------------------------------------------
 
 template <typename K, bool V>
-int run_sort(const Plan& p, const Options& o, const K* kin, const uint32_t* vin, K* kout,
-             uint32_t* vout, cudaStream_t st) {
+int set_all_smem_attrs() {
   PGS_TRY((set_smem_attrs<K, V>()));
-  PGS_TRY((set_smem_attrs<K, false>()));     // the sample sort runs keys only
-  Ctx c;
-  c.st = st;
-  c.timer = o.timer;
-  Buffers b;
-  carve(p, o.workspace, &b);
-  const uint64_t n = p.n;
-  const uint32_t P = p.P;
+  return set_smem_attrs<K, false>();          // the sample sort runs keys only
+}
+
+// The launch sequence itself (no attribute or allocation calls, so it can be
+// captured into a CUDA graph once set_all_smem_attrs has run on the device).
+template <typename K, bool V>
+int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
+                 Ctx& c, const Buffers& b) {
+  cudaStream_t st = c.st;
+  const Geo g = b.geo(sh);
+  const uint64_t n = sh.n;
+  const uint32_t R = sh.R;
   const int f32 = o.dtype == PGS_F32;
   const uint64_t kv = sizeof(K) + (V ? 4 : 0);       // bytes per key/payload pair
+  PGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), st));
 
   // Ping-pong so that the last pass lands in kout.
-  const int after_block = p.passes - 1;
+  const int after_block = sh.passes - 1;
   K* cur_k = (after_block % 2 == 0) ? kout : static_cast<K*>(b.alt_k);
   K* oth_k = (cur_k == kout) ? static_cast<K*>(b.alt_k) : kout;
   uint32_t* cur_v = V ? ((after_block % 2 == 0) ? vout : b.alt_v) : nullptr;
@@ -335,18 +370,19 @@ int run_sort(const Plan& p, const Options& o, const K* kin, const uint32_t* vin,
   int left = after_block;
 
   // Step 1: local sort of every run.  Block sort of kTile tiles ...
-  const uint32_t tiles_per_run = (uint32_t)ceil_div(p.nmax, kTile);
+  const uint32_t tiles_per_run = (uint32_t)std::max<uint64_t>(1, ceil_div(sh.maxlen, kTile));
   PGS_TRY(launch(c, PGS_KERNEL_BLOCK_SORT, 1, 2 * n * kv, [&] {
-    k_block_sort<K, V><<<(unsigned)((uint64_t)P * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
-        kin, vin, cur_k, cur_v, n, P, tiles_per_run, f32, left == 0 ? f32 : 0);
+    k_block_sort<K, V><<<(unsigned)((uint64_t)R * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
+        kin, vin, cur_k, cur_v, b.run_off, tiles_per_run, f32, left == 0 ? f32 : 0);
   }));
   // ... then balanced pairwise merge rounds (Fig. 2) until each run is one list.
-  for (int k = 0; k < p.run_rounds; ++k) {
+  for (int k = 0; k < sh.run_rounds; ++k) {
     const uint64_t w = (uint64_t)kTile << k;
-    const uint64_t ppr = ceil_div(p.nmax, 2 * w);
-    const uint64_t np = ppr * P;
+    const uint64_t cmax = ceil_div(sh.maxlen, 2 * w);
+    const uint64_t np = cmax * R;
     PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
-      k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, n, P, w, ppr);
+      k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, b.run_off, R, w, cmax,
+                                                      (uint32_t)kMergeTile);
     }));
     --left;
     PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, n, b, left == 0 ? f32 : 0, 1)));
@@ -354,159 +390,143 @@ int run_sort(const Plan& p, const Options& o, const K* kin, const uint32_t* vin,
     std::swap(cur_v, oth_v);
   }
 
-  if (P > 1) {
+  if (sh.Pmax > 1) {
     // Step 2: regular samples of every sorted run, gathered in (run, position) order.
     K* sa = static_cast<K*>(b.samp_a);
     K* sb = static_cast<K*>(b.samp_b);
-    PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 2 * p.S * sizeof(K), [&] {
-      k_sample<K><<<grid_for(p.S, 256), 256, 0, st>>>(cur_k, n, P, p.s, p.all_samples, sa, p.S);
+    PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 16 * (uint64_t)R, [&] {
+      k_sample_counts<<<grid_for(R, 256), 256, 0, st>>>(g, b.samp_counts);
     }));
-    PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 8 * (P + 1), [&] {
-      k_sample_offsets<<<grid_for(P + 1, 256), 256, 0, st>>>(b.sample_off, n, P, p.s, p.all_samples);
+    PGS_TRY(scan_u64(c, b.samp_counts, b.samp_off, R, b.scan_sums, b.scan_sums2, 2));
+    PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 2 * sh.S * sizeof(K), [&] {
+      k_sample<K><<<grid_for(sh.S, 256), 256, 0, st>>>(cur_k, g, b.samp_off, sa, sh.S);
     }));
-    // Step 3: the Master sorts the samples (merging the P sorted sample lists
-    // with the Fig. 2 schedule) and picks every (S/P)-th one.
-    for (int k = 0; k < p.bucket_rounds; ++k) {
+    // Step 3: the Master sorts the samples (merging each instance's P sorted
+    // sample lists with the Fig. 2 schedule) and picks every (S/P)-th one.
+    for (int k = 0; k < sh.bucket_rounds; ++k) {
       const uint32_t step = 1u << k;
-      const uint64_t np = ceil_div(P, 2ull * step);
-      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 3, 32 * np, [&] {
-        k_pairs_lists<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, b.sample_off, 0, 1, P, step, np);
+      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 3, 32 * (uint64_t)R, [&] {
+        k_pairs_sample_lists<<<grid_for(R, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.samp_off, step,
+                                                               (uint32_t)kMergeTile);
       }));
-      PGS_TRY((merge_round<K, false>(c, sa, nullptr, sb, nullptr, np, p.S, b, 0, 3)));
+      PGS_TRY((merge_round<K, false>(c, sa, nullptr, sb, nullptr, R, sh.S, b, 0, 3)));
       std::swap(sa, sb);
     }
-    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)P * sizeof(K), [&] {
-      k_pick_splitters<K><<<grid_for(P - 1, 256), 256, 0, st>>>(sa, p.S, P, static_cast<K*>(b.spl),
-                                                                static_cast<K*>(o.splitters), f32);
+    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)R * sizeof(K), [&] {
+      k_pick_splitters<K><<<grid_for(R, 256), 256, 0, st>>>(sa, g, b.samp_off, static_cast<K*>(b.spl),
+                                                            static_cast<K*>(o.splitters), f32);
     }));
     // Step 4: binary search of every splitter in every run, then the investigator.
-    PGS_TRY(launch(c, PGS_KERNEL_CUT_SEARCH, 4, 16 * (uint64_t)P * P, [&] {
-      k_cut_search<K><<<grid_for((uint64_t)P * (P - 1), 256), 256, 0, st>>>(
-          cur_k, n, P, static_cast<const K*>(b.spl), b.lb, b.cnt);
+    PGS_TRY(launch(c, PGS_KERNEL_CUT_SEARCH, 4, 16 * sh.Q, [&] {
+      k_cut_search<K><<<grid_for(sh.Q, 256), 256, 0, st>>>(cur_k, g, sh.Q, static_cast<const K*>(b.spl), b.lb,
+                                                           b.cnt);
     }));
-    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 16 * (uint64_t)P, [&] {
-      k_cut_edges<<<grid_for(P, 256), 256, 0, st>>>(b.cut, b.e, n, P);
+    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)R, [&] {
+      k_cut_edges<<<grid_for(R, 256), 256, 0, st>>>(g, b.cut, b.e);
     }));
-    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)P * P, [&] {
-      k_investigator<K><<<P - 1, 256, 0, st>>>(b.lb, b.cnt, static_cast<const K*>(b.spl), n, P, o.investigator,
-                                               b.cut, b.e);
+    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * sh.MAT, [&] {
+      k_investigator<K><<<R, 256, 0, st>>>(b.lb, b.cnt, static_cast<const K*>(b.spl), g, o.investigator, b.cut,
+                                           b.e);
     }));
-    // Section IV-C: receive offsets of every (run, bucket) segment.
-    PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 16 * (uint64_t)P * P, [&] {
-      k_bucket_sizes<<<grid_for((uint64_t)P * P, 256), 256, 0, st>>>(b.cut, P, b.sizes);
+    // Section IV-C: receive offsets of every (bucket, run) segment.
+    PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 32 * sh.Q, [&] {
+      k_bucket_sizes<<<grid_for(sh.Q, 256), 256, 0, st>>>(g, sh.Q, b.cut, b.sizes, b.seg_src);
     }));
-    PGS_TRY(scan_u64(c, b.sizes, b.off, (uint64_t)P * P, b.scan_sums, b.scan_sums2, 5));
+    PGS_TRY(scan_u64(c, b.sizes, b.off, sh.Q, b.scan_sums, b.scan_sums2, 5));
     // Step 5: the exchange, as an in-HBM scatter into bucket-major order.
     const uint64_t stiles = ceil_div(n, kScatterTile);
     PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 8 * stiles, [&] {
-      k_scatter_part<<<grid_for(stiles, 256), 256, 0, st>>>(b.off, (uint64_t)P * P, n, b.first_seg);
+      k_scatter_part<<<grid_for(stiles, 256), 256, 0, st>>>(b.off, sh.Q, n, b.first_seg);
     }));
     --left;
     PGS_TRY(launch(c, PGS_KERNEL_SCATTER, 5, 2 * n * kv, [&] {
       k_scatter<K, V><<<(unsigned)stiles, kScatterNT, sizeof(ScatterSmem<K>), st>>>(
-          cur_k, cur_v, oth_k, oth_v, b.off, b.cut, b.first_seg, n, P, left == 0 ? f32 : 0);
+          cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, left == 0 ? f32 : 0);
     }));
     std::swap(cur_k, oth_k);
     std::swap(cur_v, oth_v);
     // Step 6: every bucket merges its P segments with the Fig. 2 schedule.
-    for (int k = 0; k < p.bucket_rounds; ++k) {
+    for (int k = 0; k < sh.bucket_rounds; ++k) {
       const uint32_t step = 1u << k;
-      const uint64_t per = ceil_div(P, 2ull * step);
-      const uint64_t np = per * P;
-      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * np, [&] {
-        k_pairs_lists<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, b.off, P, P, P, step, per);
+      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * sh.Q, [&] {
+        k_pairs_bucket_lists<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, sh.Q, step,
+                                                                   (uint32_t)kMergeTile);
       }));
       --left;
-      PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, n, b, left == 0 ? f32 : 0, 6)));
+      PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
       std::swap(cur_k, oth_k);
       std::swap(cur_v, oth_v);
     }
   } else {
-    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 32, [&] { k_cut_edges<<<1, 32, 0, st>>>(b.cut, b.e, n, P); }));
+    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)R, [&] {
+      k_cut_edges<<<grid_for(R, 256), 256, 0, st>>>(g, b.cut, b.e);
+    }));
   }
   if (left != 0 || cur_k != kout) return PGS_ERR_CUDA;   // plan/launch mismatch: never expected
 
-  if (o.cuts) {
-    PGS_CUDA(cudaMemcpyAsync(o.cuts, b.cut, sizeof(uint64_t) * (uint64_t)P * (P + 1),
-                             cudaMemcpyDeviceToDevice, st));
+  if (o.cuts && sh.I == 1) {
+    PGS_CUDA(cudaMemcpyAsync(o.cuts, b.cut, sizeof(uint64_t) * sh.MAT, cudaMemcpyDeviceToDevice, st));
   }
-  PGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), st));
   const uint32_t launches = c.launches + 1;             // including the statistics kernel
-  return launch(c, PGS_KERNEL_STATS, 0, 8 * (uint64_t)(P + 1), [&] {
-    k_stats<<<1, 256, 0, st>>>(b.e, n, P, (uint32_t)std::min<uint64_t>(p.s, 0xFFFFFFFFu), PGS_SPLITTERS_SAMPLED,
-                               (uint32_t)p.passes, launches, b.err, static_cast<DevStats*>(o.stats),
-                               o.bucket_bounds);
+  return launch(c, PGS_KERNEL_STATS, 0, 8 * ((uint64_t)R + sh.I), [&] {
+    k_stats<<<1, 256, 0, st>>>(g, b.e, n, (uint32_t)std::min<uint64_t>(sh.s, 0xFFFFFFFFu), PGS_SPLITTERS_SAMPLED,
+                               (uint32_t)sh.passes, launches, b.err, static_cast<DevStats*>(o.stats),
+                               o.bucket_bounds, b.max_ratio);
   });
 }
 
-// ---------------------------------------------------------------------------
-// pgs_fit_splitters: step 3 on a caller-given sample.
-// ---------------------------------------------------------------------------
-
-struct FitPlan {
-  uint64_t m = 0;
-  uint32_t P = 1;
-  int w = 4;
-  int rounds = 0;
-  uint64_t max_pairs = 1, max_tiles = 1;
-};
-
-inline FitPlan make_fit_plan(uint64_t m, uint32_t P, const Options& o) {
-  FitPlan f;
-  f.m = m;
-  f.P = P;
-  f.w = key_bytes(o.dtype);
-  uint64_t w = kTile;
-  while (w < m) { w *= 2; ++f.rounds; }
-  f.max_pairs = std::max<uint64_t>(1, ceil_div(m, 2ull * kTile));
-  f.max_tiles = ceil_div(std::max<uint64_t>(m, 1), kTile) + f.max_pairs + 1;
-  return f;
-}
-
-inline size_t carve_fit(const FitPlan& f, void* base, void** a, void** bb, Buffers* b) {
-  Carver c(base);
-  *a = c.take<char>(f.m * f.w);
-  *bb = c.take<char>(f.m * f.w);
-  b->pairs = c.take<Pair>(f.max_pairs);
-  b->tcount = c.take<uint64_t>(f.max_pairs);
-  b->tbegin = c.take<uint64_t>(f.max_pairs + 1);
-  b->tile_pair = c.take<uint32_t>(f.max_tiles);
-  b->part = c.take<uint64_t>(f.max_tiles + 1);
-  const uint64_t chunks = ceil_div(f.max_pairs, kScanChunk);
-  b->scan_sums = c.take<uint64_t>(chunks + 1);
-  b->scan_sums2 = c.take<uint64_t>(chunks + 1);
-  return c.used;
-}
-
-template <typename K>
-int run_fit(const FitPlan& f, const Options& o, const K* samples, K* splitters_out, cudaStream_t st) {
-  PGS_TRY((set_smem_attrs<K, false>()));
+// A single sort: build the batch-of-one tables on the device, then the pipeline.
+template <typename K, bool V>
+int run_sort(const Shape& sh, const Options& o, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
+             cudaStream_t st) {
+  PGS_TRY((set_all_smem_attrs<K, V>()));
   Ctx c;
   c.st = st;
   c.timer = o.timer;
   Buffers b;
-  void *va, *vb;
-  carve_fit(f, o.workspace, &va, &vb, &b);
-  K* a = static_cast<K*>(va);
-  K* bb = static_cast<K*>(vb);
-  const int f32 = o.dtype == PGS_F32;
-  // Sort the sample as one run: block sort, then pairwise merge rounds.
-  const uint32_t tiles = (uint32_t)ceil_div(f.m, kTile);
-  PGS_TRY(launch(c, PGS_KERNEL_BLOCK_SORT, 3, 2 * f.m * sizeof(K), [&] {
-    k_block_sort<K, false><<<tiles, kNT, sizeof(BlockSortSmem<K>), st>>>(samples, nullptr, a, nullptr, f.m, 1,
-                                                                         tiles, f32, 0);
+  carve(sh, o.workspace, &b);
+  const uint32_t P = sh.R;
+  PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 0, 16 * (uint64_t)(P + 1), [&] {
+    k_tables_single<<<grid_for(P + 1, 256), 256, 0, st>>>(b.koff, b.Pt, b.R0, b.mat, b.seg, b.st, b.run_off,
+                                                          b.run_inst, sh.n, P, sh.s);
   }));
-  for (int k = 0; k < f.rounds; ++k) {
-    const uint64_t w = (uint64_t)kTile << k;
-    const uint64_t np = ceil_div(f.m, 2 * w);
-    PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 3, 32 * np, [&] {
-      k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, f.m, 1, w, np);
-    }));
-    PGS_TRY((merge_round<K, false>(c, a, nullptr, bb, nullptr, np, f.m, b, 0, 3)));
-    std::swap(a, bb);
-  }
-  return launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)f.P * sizeof(K), [&] {
-    k_pick_splitters<K><<<grid_for(f.P, 256), 256, 0, st>>>(a, f.m, f.P, bb, splitters_out, f32);
+  return run_pipeline<K, V>(sh, o, kin, vin, kout, vout, c, b);
+}
+
+// ---------------------------------------------------------------------------
+// pgs_fit_splitters: step 3 on a caller-given sample.  The sample is sorted as
+// one run (a single sort with P = 1, keys only) into a buffer after the sort's
+// own workspace, then every (m/P)-th key is picked.
+// ---------------------------------------------------------------------------
+
+inline size_t fit_workspace(uint64_t m, const Options& o, Shape* sh_out, size_t* sorted_at) {
+  Shape sh = single_shape(m, 1, false, o);
+  Buffers b;
+  size_t used = carve(sh, nullptr, &b);
+  used = (used + kAlign - 1) / kAlign * kAlign;
+  if (sorted_at) *sorted_at = used;
+  if (sh_out) *sh_out = sh;
+  return used + std::max<uint64_t>(m, 1) * key_bytes(o.dtype);
+}
+
+template <typename K>
+int run_fit(uint64_t m, uint32_t P, const Options& o, const K* samples, K* splitters_out, cudaStream_t st) {
+  Shape sh;
+  size_t sorted_at = 0;
+  fit_workspace(m, o, &sh, &sorted_at);
+  Options inner = o;
+  inner.bucket_bounds = nullptr;
+  inner.cuts = nullptr;
+  inner.splitters = nullptr;
+  inner.stats = nullptr;
+  K* sorted = reinterpret_cast<K*>(static_cast<char*>(o.workspace) + sorted_at);
+  PGS_TRY((run_sort<K, false>(sh, inner, samples, nullptr, sorted, nullptr, st)));
+  Ctx c;
+  c.st = st;
+  c.timer = o.timer;
+  return launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)P * sizeof(K), [&] {
+    // The inner sort already returned the caller's bit patterns: no transform here.
+    k_pick_splitters_flat<K><<<grid_for(P, 256), 256, 0, st>>>(sorted, m, P, splitters_out, 0);
   });
 }
 

@@ -9,11 +9,16 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "pgs_ptx.cuh"
+
 namespace pgs {
 
 constexpr int kNT = 256;             // threads per CTA of the sort and merge kernels
 constexpr int kVT = 17;              // items per thread; odd, so blocked smem access is conflict free
 constexpr int kTile = kNT * kVT;     // 4352 keys per block-sort tile and per merge tile
+constexpr int kMergeNT = 256;        // threads per merge CTA
+constexpr int kMergeVT = 9;          // outputs per merge thread (odd: conflict-free staging)
+constexpr int kMergeTile = kMergeNT * kMergeVT;   // 2304 outputs per merge tile
 constexpr int kScanNT = 1024;
 constexpr int kScanVT = 8;
 constexpr int kScanChunk = kScanNT * kScanVT;
@@ -25,6 +30,36 @@ constexpr int kScatterWindow = 1024;  // bucket segments staged per scatter CTA
 struct Pair {                         // one pairwise merge: [lo, mid) + [mid, hi) -> [lo, hi)
   uint64_t lo, mid, hi;
 };
+
+// Batch geometry: device tables describing I sort instances laid end to end.
+// Instance i owns keys [koff[i], koff[i+1]) split into P[i] runs (the paper's
+// processors); its runs, and its buckets, are the global indices
+// [R0[i], R0[i] + P[i]).  Its P x (P+1) matrices (lb, cnt, cut) start at
+// mat[i]; its P x P bucket segments (bucket-major) start at seg[i]; its
+// bucket vector e (P+1 entries) starts at R0[i] + i.  A single sort is a
+// batch of one.
+struct Geo {
+  const uint64_t* koff;      // I+1
+  const uint32_t* P;         // I
+  const uint32_t* R0;        // I+1
+  const uint64_t* mat;       // I+1
+  const uint64_t* seg;       // I+1
+  const uint64_t* s;         // I: samples per run (0 for an instance with one run)
+  const uint64_t* run_off;   // R+1: first key of every run
+  const uint32_t* run_inst;  // R: instance of every run
+  uint32_t I, R;
+};
+
+// Index of the last entry of a sorted table t[0..n] with t[k] <= x.
+template <typename T>
+__device__ __forceinline__ uint32_t last_le(const T* t, uint32_t n, T x) {
+  uint32_t lo = 0, hi = n;                  // invariant t[lo] <= x < t[hi] (t[n] > x assumed)
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (t[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 // ---------------------------------------------------------------------------
 // Key order
@@ -117,13 +152,13 @@ struct BlockSortSmem {
 template <typename K, bool VALS>
 __global__ void __launch_bounds__(kNT)
 k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kout, uint32_t* vout,
-             uint64_t n, uint32_t P, uint32_t tiles_per_run, int f32_in, int f32_out) {
+             const uint64_t* __restrict__ run_off, uint32_t tiles_per_run, int f32_in, int f32_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSortSmem<K>& sm = *reinterpret_cast<BlockSortSmem<K>*>(smem_raw);
   const int tid = threadIdx.x;
   const uint64_t r = blockIdx.x / tiles_per_run;
   const uint64_t t = blockIdx.x % tiles_per_run;
-  const uint64_t rs = run_start(r, n, P), re = run_start(r + 1, n, P);
+  const uint64_t rs = run_off[r], re = run_off[r + 1];
   const uint64_t g0 = rs + t * kTile;
   if (g0 >= re) return;
   const int cnt = (int)umin(kTile, re - g0);
@@ -194,43 +229,144 @@ k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kou
 // Pair descriptors for one merge round, and the tile bookkeeping.
 // ---------------------------------------------------------------------------
 
-// Run formation: inside every run, blocks [j 2w, j 2w + w) and [j 2w + w, (j+1) 2w) merge.
-static __global__ void k_pairs_runs(Pair* pairs, uint64_t* tcount, uint64_t n, uint32_t P, uint64_t w,
-                             uint64_t pairs_per_run) {
+__device__ __forceinline__ void put_pair(Pair* pairs, uint64_t* tcount, uint64_t p, uint64_t lo, uint64_t mid,
+                                         uint64_t hi, uint32_t tile) {
+  pairs[p] = Pair{lo, mid, hi};
+  tcount[p] = (hi - lo + tile - 1) / tile;
+}
+
+// Run formation (step 1): inside every run, blocks [j 2w, j 2w + w) and
+// [j 2w + w, (j+1) 2w) merge; a run that is already one list is copied.
+// Index space: run x pair slot (cmax slots per run, unused slots are empty).
+static __global__ void k_pairs_runs(Pair* pairs, uint64_t* tcount, const uint64_t* __restrict__ run_off,
+                                    uint32_t R, uint64_t w, uint64_t cmax, uint32_t tile) {
   uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (p >= pairs_per_run * P) return;
-  uint64_t r = p / pairs_per_run, j = p % pairs_per_run;
-  uint64_t rs = run_start(r, n, P), re = run_start(r + 1, n, P);
+  if (p >= (uint64_t)R * cmax) return;
+  uint64_t r = p / cmax, j = p % cmax;
+  uint64_t rs = run_off[r], re = run_off[r + 1];
   uint64_t lo = umin(rs + j * 2 * w, re);
+  if (j > 0 && lo >= re) lo = re;                     // empty slot
   uint64_t mid = umin(lo + w, re);
   uint64_t hi = umin(lo + 2 * w, re);
-  pairs[p] = Pair{lo, mid, hi};
-  tcount[p] = (hi - lo + kTile - 1) / kTile;
+  put_pair(pairs, tcount, p, lo, mid, hi, tile);
 }
 
-// Lists given by an offset table: segment g has L lists, list i = [tbl[g*stride + i],
-// tbl[g*stride + i + 1]).  Round `step` merges group [i, i+step) with [i+step, i+2 step).
-static __global__ void k_pairs_lists(Pair* pairs, uint64_t* tcount, const uint64_t* tbl, uint64_t stride,
-                              uint32_t segs, uint32_t L, uint32_t step, uint64_t pairs_per_seg) {
+// The Fig. 2 schedule over the P lists of one group: round `step` merges list
+// group [j, j+step) with [j+step, j+2 step) for j a multiple of 2 step.  Lists
+// of group g are [tbl[g0 + j], tbl[g0 + j + 1]); the index space is one slot
+// per list (slots that do not start a pair are empty).
+//  - samples (step 3): one group per instance, lists = its runs' samples,
+//    tbl = sample offsets indexed by global run, slot = global run;
+//  - buckets (step 6): one group per bucket, lists = its P segments,
+//    tbl = segment offsets (bucket-major), slot = global segment.
+static __global__ void k_pairs_sample_lists(Pair* pairs, uint64_t* tcount, Geo g,
+                                            const uint64_t* __restrict__ samp_off, uint32_t step, uint32_t tile) {
   uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (p >= pairs_per_seg * segs) return;
-  uint64_t g = p / pairs_per_seg, j = p % pairs_per_seg;
-  const uint64_t* o = tbl + g * stride;
-  uint64_t i0 = j * 2ull * step;
-  uint64_t lo = o[umin(i0, L)];
-  uint64_t mid = o[umin(i0 + step, L)];
-  uint64_t hi = o[umin(i0 + 2ull * step, L)];
-  pairs[p] = Pair{lo, mid, hi};
-  tcount[p] = (hi - lo + kTile - 1) / kTile;
+  if (p >= g.R) return;
+  const uint32_t i = g.run_inst[p];
+  const uint32_t r0 = g.R0[i], P = g.P[i];
+  const uint32_t j = (uint32_t)p - r0;
+  const uint64_t end = samp_off[r0 + P];
+  if (j % (2 * step) != 0) {
+    put_pair(pairs, tcount, p, end, end, end, tile);
+    return;
+  }
+  put_pair(pairs, tcount, p, samp_off[r0 + j], samp_off[r0 + min(j + step, P)],
+           samp_off[r0 + min(j + 2 * step, P)], tile);
 }
 
-// One thread per merge tile: find its pair, then the merge-path split at the
-// tile's first output.  Splits are computed up front so every merge CTA starts
-// with its two ranges known and moves equal output work.
+static __global__ void k_pairs_bucket_lists(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
+                                            uint64_t Q, uint32_t step, uint32_t tile) {
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
+  const uint64_t P = g.P[i];
+  const uint64_t local = q - g.seg[i];
+  const uint64_t b = local / P, j = local % P;
+  const uint64_t base = g.seg[i] + b * P;           // first segment of bucket b
+  if (j % (2 * step) != 0) {
+    const uint64_t end = off[base + P];
+    put_pair(pairs, tcount, q, end, end, end, tile);
+    return;
+  }
+  put_pair(pairs, tcount, q, off[base + j], off[base + umin(j + step, P)], off[base + umin(j + 2 * step, P)],
+           tile);
+}
+
+// ---------------------------------------------------------------------------
+// K2/K8: merge-path merge of one round (Section IV-A's pairwise merge; used for
+// step 1's run formation, step 3's sample sort and step 6's bucket merge).
+// Every CTA produces one tile of MT = NT x VT outputs of one pair: its two
+// input ranges arrive in shared memory by bulk asynchronous copy (one thread
+// issues them, an mbarrier counts the bytes), every thread merges VT outputs
+// straight into a shared-memory staging area, and the tile leaves with 16-byte
+// vector stores.  No key or payload array is kept in registers (32 registers a
+// thread), so eight CTAs share an SM and keep copies in flight.
+// ---------------------------------------------------------------------------
+
+template <typename K, bool VALS, int NT, int VT>
+struct Merge2Layout {
+  static constexpr int T = NT * VT;
+  static constexpr size_t kin = 16;                                   // after the mbarrier
+  static constexpr size_t vin = kin + (size_t)T * sizeof(K) + 64;
+  static constexpr size_t kout = vin + (VALS ? (size_t)T * 4 + 64 : 0);
+  static constexpr size_t vout = kout + (size_t)T * sizeof(K);
+  static constexpr size_t bytes = vout + (VALS ? (size_t)T * 4 : 0);
+  static_assert(T % 4 == 0, "staging offsets stay 16-byte aligned");
+};
+
+// A global range widened to 16-byte boundaries for a bulk copy.
+struct Span16 {
+  const char* base;
+  uint32_t bytes;   // multiple of 16 (0 for an empty range)
+  uint32_t skip;    // elements between base and the range's first element
+};
+
+template <typename T>
+__device__ __forceinline__ Span16 widen16(const T* p, uint32_t count) {
+  if (count == 0) return Span16{reinterpret_cast<const char*>(p), 0u, 0u};
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = a & ~uintptr_t(15);
+  const uintptr_t hi = (a + (uintptr_t)count * sizeof(T) + 15) & ~uintptr_t(15);
+  return Span16{reinterpret_cast<const char*>(lo), (uint32_t)(hi - lo), (uint32_t)((a - lo) / sizeof(T))};
+}
+
+// Store cnt elements from shared memory to global memory with 16-byte vector
+// stores where the destination allows it (unaligned head and tail element-wise).
+template <typename T, int NT>
+__device__ __forceinline__ void store_tile_vec(T* g, const T* s, int cnt) {
+  constexpr int E = 16 / sizeof(T);
+  const int tid = threadIdx.x;
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(g);
+  int head = (int)(((16 - (addr & 15)) & 15) / sizeof(T));
+  if (head > cnt) head = cnt;
+  if (tid < head) g[tid] = s[tid];
+  const int body = (cnt - head) / E;
+  uint4* gb = reinterpret_cast<uint4*>(g + head);
+  const T* sb = s + head;
+  for (int c = tid; c < body; c += NT) {
+    union { T e[E]; uint4 v; } u;
+#pragma unroll
+    for (int k = 0; k < E; ++k) u.e[k] = sb[c * E + k];
+    gb[c] = u.v;
+  }
+  for (int i = head + body * E + tid; i < cnt; i += NT) g[i] = s[i];
+}
+
+// The partition kernel writes, per merge tile, where the tile's A and B ranges
+// start and where its output goes, plus the ends of its pair (one merge-path
+// search per tile, all tiles in parallel); a merge CTA reads its split and the
+// next one together and knows both of its ranges after one dependent load.
+
+struct TileSplit {
+  uint64_t a, b, out;     // first A element, first B element, first output element
+  uint64_t a_end, b_end;  // end of the pair's A list and of its B list
+};
+
 template <typename K>
-__global__ void k_partition(const K* __restrict__ src, const Pair* __restrict__ pairs,
-                            const uint64_t* __restrict__ tbegin, uint64_t npairs,
-                            uint32_t* tile_pair, uint64_t* part) {
+__global__ void k_partition_split(const K* __restrict__ src, const Pair* __restrict__ pairs,
+                                  const uint64_t* __restrict__ tbegin, uint64_t npairs, TileSplit* split,
+                                  uint32_t tile) {
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t total = tbegin[npairs];
   if (i >= total) return;
@@ -239,92 +375,109 @@ __global__ void k_partition(const K* __restrict__ src, const Pair* __restrict__ 
     uint64_t mid = (lo + hi) >> 1;
     if (tbegin[mid] <= i) lo = mid; else hi = mid;
   }
-  uint64_t p = lo;
-  Pair pr = pairs[p];
-  uint64_t diag = (i - tbegin[p]) * kTile;
-  uint64_t na = pr.mid - pr.lo, nb = pr.hi - pr.mid;
-  tile_pair[i] = (uint32_t)p;
-  part[i] = merge_path<K, uint64_t>(src + pr.lo, na, src + pr.mid, nb, diag);
+  const Pair pr = pairs[lo];
+  const uint64_t na = pr.mid - pr.lo, nb = pr.hi - pr.mid;
+  const uint64_t d0 = (i - tbegin[lo]) * tile;
+  const uint64_t a0 = merge_path<K, uint64_t>(src + pr.lo, na, src + pr.mid, nb, d0);
+  split[i] = TileSplit{pr.lo + a0, pr.mid + (d0 - a0), pr.lo + d0, pr.mid, pr.hi};
 }
 
-// ---------------------------------------------------------------------------
-// K2/K8: merge-path merge.  Each CTA produces kTile outputs of one pair.
-// ---------------------------------------------------------------------------
+template <typename K, bool VALS, int NT, int VT>
+__global__ void __launch_bounds__(NT)
+k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
+             uint32_t* __restrict__ vdst, const TileSplit* __restrict__ split, const uint64_t* __restrict__ total_ptr,
+             int f32_out, uint32_t* err) {
+  using L = Merge2Layout<K, VALS, NT, VT>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  K* s_kin = reinterpret_cast<K*>(smem_raw + L::kin);
+  uint32_t* s_vin = reinterpret_cast<uint32_t*>(smem_raw + L::vin);
+  K* s_kout = reinterpret_cast<K*>(smem_raw + L::kout);
+  uint32_t* s_vout = reinterpret_cast<uint32_t*>(smem_raw + L::vout);
+  __shared__ uint32_t s_na, s_nb;
+  __shared__ uint64_t s_a, s_b, s_out;
 
-template <typename K>
-struct MergeSmem {
-  K keys[kTile];
-  uint32_t vals[kTile];
-};
-
-template <typename K, bool VALS>
-__global__ void __launch_bounds__(kNT)
-k_merge(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
-        uint32_t* __restrict__ vdst, const Pair* __restrict__ pairs, const uint64_t* __restrict__ tbegin,
-        uint64_t npairs, const uint32_t* __restrict__ tile_pair, const uint64_t* __restrict__ part,
-        int f32_out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  MergeSmem<K>& sm = *reinterpret_cast<MergeSmem<K>*>(smem_raw);
   const uint64_t tile = blockIdx.x;
-  if (tile >= tbegin[npairs]) return;
   const int tid = threadIdx.x;
-  const uint32_t p = tile_pair[tile];
-  const Pair pr = pairs[p];
-  const uint64_t na_all = pr.mid - pr.lo, total = pr.hi - pr.lo;
-  const uint64_t d0 = (tile - tbegin[p]) * kTile;
-  const uint64_t d1 = umin(d0 + kTile, total);
-  const uint64_t a0 = part[tile];
-  const uint64_t a1 = (d1 == total) ? na_all : part[tile + 1];
-  const int na = (int)(a1 - a0);
-  const int cnt = (int)(d1 - d0);
-  const K* ka = ksrc + pr.lo + a0;
-  const K* kb = ksrc + pr.mid + (d0 - a0);
-#pragma unroll
-  for (int i = 0; i < kVT; ++i) {
-    int idx = i * kNT + tid;
-    if (idx < cnt) sm.keys[idx] = idx < na ? ka[idx] : kb[idx - na];
-  }
-  if (VALS) {
-    const uint32_t* va = vsrc + pr.lo + a0;
-    const uint32_t* vb = vsrc + pr.mid + (d0 - a0);
-#pragma unroll
-    for (int i = 0; i < kVT; ++i) {
-      int idx = i * kNT + tid;
-      if (idx < cnt) sm.vals[idx] = idx < na ? va[idx] : vb[idx - na];
+  if (tid == 0) {
+    const uint64_t total = *total_ptr;
+    uint32_t na = 0, nb = 0;
+    TileSplit t{};
+    if (tile < total) {
+      t = split[tile];
+      bool same = false;
+      TileSplit nx{};
+      if (tile + 1 < total) {
+        nx = split[tile + 1];
+        same = nx.a_end == t.a_end && nx.b_end == t.b_end;
+      }
+      na = (uint32_t)((same ? nx.a : t.a_end) - t.a);
+      nb = (uint32_t)((same ? nx.b : t.b_end) - t.b);
+      const Span16 ka = widen16(ksrc + t.a, na), kb = widen16(ksrc + t.b, nb);
+      Span16 va{nullptr, 0, 0}, vb{nullptr, 0, 0};
+      if (VALS) {
+        va = widen16(vsrc + t.a, na);
+        vb = widen16(vsrc + t.b, nb);
+      }
+      mbar_init(bar, 1);
+      fence_barrier_init();
+      mbar_arrive_expect_tx(bar, ka.bytes + kb.bytes + va.bytes + vb.bytes);
+      if (ka.bytes) bulk_load(s_kin, ka.base, ka.bytes, bar);
+      if (kb.bytes) bulk_load(reinterpret_cast<char*>(s_kin) + ka.bytes, kb.base, kb.bytes, bar);
+      if (VALS) {
+        if (va.bytes) bulk_load(s_vin, va.base, va.bytes, bar);
+        if (vb.bytes) bulk_load(reinterpret_cast<char*>(s_vin) + va.bytes, vb.base, vb.bytes, bar);
+      }
     }
+    s_na = na;
+    s_nb = nb;
+    s_a = t.a;
+    s_b = t.b;
+    s_out = t.out;
   }
   __syncthreads();
-  const int diag = min(tid * kVT, cnt);
-  const int a = merge_path<K, int>(sm.keys, na, sm.keys + na, cnt - na, diag);
-  K key[kVT];
-  int pos[kVT];
-  const int mine = min(kVT, cnt - diag);
-  serial_merge<K, kVT>(sm.keys, a, na, na + (diag - a), cnt, mine, key, pos);
-  uint32_t val[kVT];
+  const int na = (int)s_na, nb = (int)s_nb, cnt = na + nb;
+  if (cnt == 0) return;                                 // tile beyond the round's total
+  const uint64_t ga = s_a, gb = s_b;
+  const Span16 ka = widen16(ksrc + ga, na), kb = widen16(ksrc + gb, nb);
+  const K* sa = s_kin + ka.skip;
+  const K* sb = reinterpret_cast<const K*>(reinterpret_cast<const char*>(s_kin) + ka.bytes) + kb.skip;
+  const uint32_t* sva = nullptr;
+  const uint32_t* svb = nullptr;
   if (VALS) {
-#pragma unroll
-    for (int j = 0; j < kVT; ++j)
-      if (j < mine) val[j] = sm.vals[pos[j]];
+    const Span16 va = widen16(vsrc + ga, na), vb = widen16(vsrc + gb, nb);
+    sva = s_vin + va.skip;
+    svb = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(s_vin) + va.bytes) + vb.skip;
   }
-  __syncthreads();
+  if (!mbar_wait(bar, 0)) {
+    if (tid == 0) atomicOr(err, kErrWaitTimeout);
+    mbar_wait(bar, 0);
+    return;
+  }
+  const int diag = min(tid * VT, cnt);
+  const int mine = min(VT, cnt - diag);
+  int ai = merge_path<K, int>(sa, na, sb, nb, diag);
+  int bi = diag - ai;
+  K ak = ai < na ? sa[ai] : key_max<K>();
+  K bk = bi < nb ? sb[bi] : key_max<K>();
 #pragma unroll
-  for (int j = 0; j < kVT; ++j) {
+  for (int j = 0; j < VT; ++j) {
     if (j < mine) {
-      sm.keys[diag + j] = key[j];
-      if (VALS) sm.vals[diag + j] = val[j];
+      const bool take_a = (bi >= nb) || (ai < na && ak <= bk);
+      s_kout[diag + j] = from_order<K>(take_a ? ak : bk, f32_out);
+      if (VALS) s_vout[diag + j] = take_a ? sva[ai] : svb[bi];
+      if (take_a) {
+        ++ai;
+        ak = ai < na ? sa[ai] : key_max<K>();
+      } else {
+        ++bi;
+        bk = bi < nb ? sb[bi] : key_max<K>();
+      }
     }
   }
   __syncthreads();
-  K* ko = kdst + pr.lo + d0;
-  uint32_t* vo = vdst + pr.lo + d0;
-#pragma unroll
-  for (int i = 0; i < kVT; ++i) {
-    int idx = i * kNT + tid;
-    if (idx < cnt) {
-      ko[idx] = from_order<K>(sm.keys[idx], f32_out);
-      if (VALS) vo[idx] = sm.vals[idx];
-    }
-  }
+  store_tile_vec<K, NT>(kdst + s_out, s_kout, cnt);
+  if (VALS) store_tile_vec<uint32_t, NT>(vdst + s_out, s_vout, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,145 +560,206 @@ k_scan_chunks(const uint64_t* __restrict__ in, uint64_t m, uint64_t* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// Tables of a single sort of n keys on P runs (a batch of one).
+// ---------------------------------------------------------------------------
+
+static __global__ void k_tables_single(uint64_t* koff, uint32_t* Pt, uint32_t* R0, uint64_t* mat, uint64_t* seg,
+                                       uint64_t* st, uint64_t* run_off, uint32_t* run_inst, uint64_t n, uint32_t P,
+                                       uint64_t s) {
+  uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (r > P) return;
+  run_off[r] = run_start(r, n, P);
+  if (r < P) run_inst[r] = 0;
+  if (r == 0) {
+    koff[0] = 0; koff[1] = n;
+    Pt[0] = P;
+    R0[0] = 0; R0[1] = P;
+    mat[0] = 0; mat[1] = (uint64_t)P * (P + 1);
+    seg[0] = 0; seg[1] = (uint64_t)P * P;
+    st[0] = P > 1 ? s : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K3: regular samples (step 2 of Section IV).
 // Run r is cut into s_r = min(s, n_r) equal blocks; the last key of each block
 // is sampled, local position floor((i+1) n_r / s_r) - 1.  Samples are written
-// in (run, position) order, each run's samples sorted.
+// in (run, position) order, so each run's samples are sorted.
 // ---------------------------------------------------------------------------
 
+// Samples per run, s_r = min(s, n_r) (the scan of these gives every run's first sample).
+static __global__ void k_sample_counts(Geo g, uint64_t* counts) {
+  uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (r >= g.R) return;
+  counts[r] = umin(g.s[g.run_inst[r]], g.run_off[r + 1] - g.run_off[r]);
+}
+
 template <typename K>
-__global__ void k_sample(const K* __restrict__ runs, uint64_t n, uint32_t P, uint64_t s,
-                         int all, K* __restrict__ samples, uint64_t S) {
+__global__ void k_sample(const K* __restrict__ runs, Geo g, const uint64_t* __restrict__ samp_off,
+                         K* __restrict__ samples, uint64_t S) {
   uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (j >= S) return;
-  if (all) {                        // s >= every run length: every key is a sample
-    samples[j] = runs[j];
-    return;
-  }
-  uint64_t r = j / s, i = j % s;
-  uint64_t rs = run_start(r, n, P), nr = run_start(r + 1, n, P) - rs;
-  uint64_t pos = (uint64_t)(((unsigned __int128)(i + 1) * nr) / s) - 1;   // exact for any s, n_r
+  const uint32_t r = last_le<uint64_t>(samp_off, g.R, j);
+  const uint64_t i = j - samp_off[r], sr = samp_off[r + 1] - samp_off[r];
+  const uint64_t rs = g.run_off[r], nr = g.run_off[r + 1] - rs;
+  const uint64_t pos = (uint64_t)(((unsigned __int128)(i + 1) * nr) / sr) - 1;   // exact for any s_r, n_r
   samples[j] = runs[rs + pos];
 }
 
-// Offsets of the per-run sample lists: r s, or the run starts when all keys are samples.
-static __global__ void k_sample_offsets(uint64_t* off, uint64_t n, uint32_t P, uint64_t s, int all) {
-  uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (r > P) return;
-  off[r] = all ? run_start(r, n, P) : r * s;
+// Step 3 of Section IV: with S_i samples, t_b = sorted sample at index
+// floor(b S_i / P_i) - 1, b = 1..P_i-1.  t is indexed by global run (slot b of
+// instance i is R0[i] + b; slot 0 unused).
+template <typename K>
+__global__ void k_pick_splitters(const K* __restrict__ sorted, Geo g, const uint64_t* __restrict__ samp_off, K* t,
+                                 K* user_out, int f32) {
+  uint64_t beta = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (beta >= g.R) return;
+  const uint32_t i = g.run_inst[beta];
+  const uint32_t r0 = g.R0[i];
+  const uint64_t b = beta - r0, P = g.P[i];
+  if (b == 0) return;
+  const uint64_t s0 = samp_off[r0], S = samp_off[r0 + P] - s0;
+  const K v = sorted[s0 + (b * S) / P - 1];
+  t[beta] = v;
+  if (user_out && g.I == 1) user_out[b - 1] = from_order<K>(v, f32);
 }
 
-// Step 3 of Section IV: t_b = sorted sample at index floor(b S / P) - 1, b = 1..P-1.
+// The same pick on one sorted sample of m keys: out[b-1] = sorted[floor(b m / P) - 1].
 template <typename K>
-__global__ void k_pick_splitters(const K* __restrict__ sorted, uint64_t S, uint32_t P, K* t,
-                                 K* user_out, int f32) {
+__global__ void k_pick_splitters_flat(const K* __restrict__ sorted, uint64_t m, uint32_t P, K* out, int f32) {
   uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x + 1;
   if (b >= P) return;
-  K v = sorted[(b * S) / P - 1];
-  t[b - 1] = v;
-  if (user_out) user_out[b - 1] = from_order<K>(v, f32);
+  out[b - 1] = from_order<K>(sorted[(b * m) / P - 1], f32);
 }
 
 // ---------------------------------------------------------------------------
 // K5: cut search + investigator (step 4 of Section IV, Section IV-B).
 // ---------------------------------------------------------------------------
 
-// lb[r][b] = #{x in run r : x < t_b}, cnt[r][b] = #{x in run r : x == t_b}; b = 1..P-1.
+// lb[r][b] = #{x in run r : x < t_b}, cnt[r][b] = #{x in run r : x == t_b},
+// b = 1..P-1, for every run of every instance (index space: the P x P
+// segments; entries with b = 0 do nothing).
 template <typename K>
-__global__ void k_cut_search(const K* __restrict__ runs, uint64_t n, uint32_t P,
-                             const K* __restrict__ t, uint64_t* lb, uint64_t* cnt) {
+__global__ void k_cut_search(const K* __restrict__ runs, Geo g, uint64_t Q, const K* __restrict__ t,
+                             uint64_t* lb, uint64_t* cnt) {
   uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  uint64_t Pm1 = P - 1;
-  if (q >= (uint64_t)P * Pm1) return;
-  uint64_t r = q / Pm1, b = q % Pm1 + 1;
-  uint64_t rs = run_start(r, n, P), nr = run_start(r + 1, n, P) - rs;
+  if (q >= Q) return;
+  const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
+  const uint64_t P = g.P[i];
+  const uint64_t local = q - g.seg[i];
+  const uint64_t rl = local / P, b = local % P;
+  if (b == 0) return;
+  const uint32_t r0 = g.R0[i];
+  const uint64_t rs = g.run_off[r0 + rl], nr = g.run_off[r0 + rl + 1] - rs;
   const K* x = runs + rs;
-  K v = t[b - 1];
+  const K v = t[r0 + b];
   uint64_t lo = 0, hi = nr;
   while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] < v) lo = mid + 1; else hi = mid; }
-  uint64_t l = lo;
+  const uint64_t l = lo;
   hi = nr;
   while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] <= v) lo = mid + 1; else hi = mid; }
-  lb[r * (P + 1) + b] = l;
-  cnt[r * (P + 1) + b] = lo - l;
+  const uint64_t at = g.mat[i] + rl * (P + 1) + b;
+  lb[at] = l;
+  cnt[at] = lo - l;
 }
 
-// One CTA per splitter b = 1..P-1.  L_b = sum_r lb, G_b = sum_r cnt,
-// pre[r] = sum_{r'<r} cnt.  The variant picks e_b, then every run cuts
-// cut[r][b] = lb + clamp(e_b - L_b - pre[r], 0, cnt): the keys equal to t_b
-// are handed out in stable order (run, position) until e_b ranks are reached.
+// One CTA per splitter b = 1..P_i-1 of every instance (CTAs of slot b = 0
+// exit).  L_b = sum_r lb, G_b = sum_r cnt, pre[r] = sum_{r'<r} cnt.  The
+// variant picks e_b, then every run cuts cut[r][b] = lb + clamp(e_b - L_b -
+// pre[r], 0, cnt): the keys equal to t_b are handed out in stable order (run,
+// position) until e_b ranks are reached.
 template <typename K>
 __global__ void __launch_bounds__(256)
-k_investigator(const uint64_t* __restrict__ lb, const uint64_t* __restrict__ cnt,
-               const K* __restrict__ t, uint64_t n, uint32_t P, int variant,
-               uint64_t* cut, uint64_t* e) {
-  const uint64_t b = blockIdx.x + 1;
+k_investigator(const uint64_t* __restrict__ lb, const uint64_t* __restrict__ cnt, const K* __restrict__ t, Geo g,
+               int variant, uint64_t* cut, uint64_t* e) {
+  const uint32_t beta = blockIdx.x;
+  const uint32_t i = g.run_inst[beta];
+  const uint32_t r0 = g.R0[i];
+  const uint64_t b = beta - r0, P = g.P[i];
+  if (b == 0) return;
+  const uint64_t n = g.koff[i + 1] - g.koff[i];
   const uint64_t W = P + 1;
+  const uint64_t* lbi = lb + g.mat[i];
+  const uint64_t* cnti = cnt + g.mat[i];
+  uint64_t* cuti = cut + g.mat[i];
   __shared__ uint64_t sh_L, sh_e;
-  // L_b and G_b.
   uint64_t ls = 0, gs = 0;
   for (uint64_t r = threadIdx.x; r < P; r += blockDim.x) {
-    ls += lb[r * W + b];
-    gs += cnt[r * W + b];
+    ls += lbi[r * W + b];
+    gs += cnti[r * W + b];
   }
   uint64_t Lb, Gb;
   block_exclusive_scan(ls, &Lb);
   block_exclusive_scan(gs, &Gb);
   if (threadIdx.x == 0) {
-    uint64_t target = (b * n) / P;
+    const uint64_t target = (b * n) / P;
     uint64_t eb;
     if (variant == 0) {
       eb = umin(umax(target, Lb), Lb + Gb);
     } else if (variant == 2) {
       eb = Lb + Gb;
     } else {
-      // Group of equal splitters containing t_b: [g0, g1) in splitter index (0-based).
-      K v = t[b - 1];
-      uint64_t lo = 0, hi = P - 1;
-      while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (t[m] < v) lo = m + 1; else hi = m; }
-      uint64_t g0 = lo;
-      hi = P - 1;
-      while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (t[m] <= v) lo = m + 1; else hi = m; }
-      uint64_t k = lo - g0, i = (b - 1) - g0;
-      eb = Lb + (Gb * (i + 1)) / k;
+      // Group of equal splitters containing t_b: [g0, g1) in splitter slots 1..P-1.
+      const K* ti = t + r0;
+      const K v = ti[b];
+      uint64_t lo = 1, hi = P;
+      while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (ti[m] < v) lo = m + 1; else hi = m; }
+      const uint64_t g0 = lo;
+      hi = P;
+      while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (ti[m] <= v) lo = m + 1; else hi = m; }
+      const uint64_t k = lo - g0, j = b - g0;
+      eb = Lb + (Gb * (j + 1)) / k;
     }
     sh_L = Lb;
     sh_e = eb;
-    e[b] = eb;
+    e[r0 + i + b] = eb;
   }
   __syncthreads();
   const uint64_t L = sh_L, eb = sh_e;
   uint64_t carry = 0;
-  for (uint64_t r0 = 0; r0 < P; r0 += blockDim.x) {
-    uint64_t r = r0 + threadIdx.x;
-    uint64_t c = r < P ? cnt[r * W + b] : 0;
+  for (uint64_t rb = 0; rb < P; rb += blockDim.x) {
+    const uint64_t r = rb + threadIdx.x;
+    const uint64_t c = r < P ? cnti[r * W + b] : 0;
     uint64_t chunk;
-    uint64_t pre = block_exclusive_scan(c, &chunk) + carry;
+    const uint64_t pre = block_exclusive_scan(c, &chunk) + carry;
     if (r < P) {
-      uint64_t want = eb - L;                        // >= 0: L <= e_b in every variant
-      uint64_t take = want > pre ? umin(want - pre, c) : 0;
-      cut[r * W + b] = lb[r * W + b] + take;
+      const uint64_t want = eb - L;                 // >= 0: L <= e_b in every variant
+      const uint64_t take = want > pre ? umin(want - pre, c) : 0;
+      cuti[r * W + b] = lbi[r * W + b] + take;
     }
     carry += chunk;
   }
 }
 
-// cut[r][0] = 0, cut[r][P] = n_r, e[0] = 0, e[P] = n.
-static __global__ void k_cut_edges(uint64_t* cut, uint64_t* e, uint64_t n, uint32_t P) {
+// cut[r][0] = 0, cut[r][P] = n_r for every run; e[0] = 0, e[P] = n_i.
+static __global__ void k_cut_edges(Geo g, uint64_t* cut, uint64_t* e) {
   uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (r == 0) { e[0] = 0; e[P] = n; }
-  if (r >= P) return;
-  cut[r * (P + 1)] = 0;
-  cut[r * (P + 1) + P] = run_start(r + 1, n, P) - run_start(r, n, P);
+  if (r >= g.R) return;
+  const uint32_t i = g.run_inst[r];
+  const uint32_t r0 = g.R0[i];
+  const uint64_t P = g.P[i], rl = r - r0;
+  uint64_t* row = cut + g.mat[i] + rl * (P + 1);
+  row[0] = 0;
+  row[P] = g.run_off[r + 1] - g.run_off[r];
+  if (rl == 0) {
+    e[r0 + i] = 0;
+    e[r0 + i + P] = g.koff[i + 1] - g.koff[i];
+  }
 }
 
-// Sizes of the P x P segments in bucket-major order: size[b P + r] = cut[r][b+1] - cut[r][b].
-static __global__ void k_bucket_sizes(const uint64_t* __restrict__ cut, uint32_t P, uint64_t* sizes) {
+// Segments (bucket b, run r) of every instance, bucket-major: their sizes
+// cut[r][b+1] - cut[r][b] and the global position where they start.
+static __global__ void k_bucket_sizes(Geo g, uint64_t Q, const uint64_t* __restrict__ cut, uint64_t* sizes,
+                                      uint64_t* src) {
   uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (q >= (uint64_t)P * P) return;
-  uint64_t b = q / P, r = q % P;
-  const uint64_t* c = cut + r * (P + 1);
+  if (q >= Q) return;
+  const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
+  const uint64_t P = g.P[i];
+  const uint64_t local = q - g.seg[i];
+  const uint64_t b = local / P, rl = local % P;
+  const uint64_t* c = cut + g.mat[i] + rl * (P + 1);
   sizes[q] = c[b + 1] - c[b];
+  src[q] = g.run_off[g.R0[i] + rl] + c[b];
 }
 
 // ---------------------------------------------------------------------------
@@ -580,32 +794,26 @@ struct ScatterSmem {
 template <typename K, bool VALS>
 __global__ void __launch_bounds__(kScatterNT)
 k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
-          uint32_t* __restrict__ vdst, const uint64_t* __restrict__ off, const uint64_t* __restrict__ cut,
-          const uint64_t* __restrict__ first_seg, uint64_t n, uint32_t P, int f32_out) {
+          uint32_t* __restrict__ vdst, const uint64_t* __restrict__ off, const uint64_t* __restrict__ seg_src,
+          const uint64_t* __restrict__ first_seg, uint64_t n, uint64_t Q, int f32_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sm = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
-  const uint64_t Q = (uint64_t)P * P;
   const uint64_t o = blockIdx.x * (uint64_t)kScatterTile;
   const int cnt = (int)umin(kScatterTile, n - o);
   const uint64_t q0 = first_seg[blockIdx.x];
   const int wn = (int)umin(kScatterWindow, Q - q0);
   for (int i = threadIdx.x; i <= wn; i += blockDim.x) sm.off[i] = off[q0 + i];
-  for (int i = threadIdx.x; i < wn; i += blockDim.x) {
-    uint64_t q = q0 + i, b = q / P, r = q % P;
-    sm.src[i] = run_start(r, n, P) + cut[r * (P + 1) + b];
-  }
+  for (int i = threadIdx.x; i < wn; i += blockDim.x) sm.src[i] = seg_src[q0 + i];
   __syncthreads();
   // Warp w copies positions [o + w 32 VT, ...) 32 at a time; lane l walks its segment forward.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int base = warp * 32 * kScatterVT;
-  int p0 = base + lane;
-  // Locate the first segment of this lane inside the staged window.
   int lo = 0, hi = wn;
-  uint64_t gp = o + p0;
+  uint64_t gp = o + base + lane;
   while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (sm.off[mid] <= gp) lo = mid; else hi = mid; }
   int q = lo;
   for (int k = 0; k < kScatterVT; ++k) {
-    int p = base + k * 32 + lane;
+    const int p = base + k * 32 + lane;
     if (p >= cnt) break;
     gp = o + p;
     uint64_t s;
@@ -618,17 +826,16 @@ k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __re
         uint64_t mid = (glo + ghi) >> 1;
         if (off[mid] <= gp) glo = mid; else ghi = mid;
       }
-      uint64_t b = glo / P, r = glo % P;
-      s = run_start(r, n, P) + cut[r * (P + 1) + b] + (gp - off[glo]);
+      s = seg_src[glo] + (gp - off[glo]);
     }
     sm.keys[p] = ksrc[s];
     if (VALS) sm.vals[p] = vsrc[s];
   }
   __syncthreads();
-  for (int p = threadIdx.x; p < cnt; p += blockDim.x) {
-    kdst[o + p] = from_order<K>(sm.keys[p], f32_out);
-    if (VALS) vdst[o + p] = sm.vals[p];
-  }
+  for (int p = threadIdx.x; p < cnt; p += blockDim.x) sm.keys[p] = from_order<K>(sm.keys[p], f32_out);
+  __syncthreads();
+  store_tile_vec<K, kScatterNT>(kdst + o, sm.keys, cnt);
+  if (VALS) store_tile_vec<uint32_t, kScatterNT>(vdst + o, sm.vals, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -640,43 +847,57 @@ struct DevStats {                     // layout of pgs_stats
   uint32_t P, s;
   uint64_t max_bucket, min_bucket;
   uint32_t splitter_mode, fallback, error, passes;
-  uint32_t launches, reserved;
+  uint32_t launches;
+  float max_over_mean;
 };
 
+// Bucket sizes e_{b+1} - e_b over all buckets of all instances: the largest,
+// the smallest, and the largest ratio to its instance's mean n_i / P_i.
 static __global__ void __launch_bounds__(256)
-k_stats(const uint64_t* __restrict__ e, uint64_t n, uint32_t P, uint32_t s, uint32_t mode,
-        uint32_t passes, uint32_t launches, uint32_t* err_word, DevStats* st, uint64_t* user_bounds) {
+k_stats(Geo g, const uint64_t* __restrict__ e, uint64_t n_total, uint32_t s, uint32_t mode, uint32_t passes,
+        uint32_t launches, uint32_t* err_word, DevStats* st, uint64_t* user_bounds, float* max_ratio_out) {
   __shared__ uint64_t smax[256], smin[256];
+  __shared__ float sratio[256];
   uint64_t mx = 0, mn = ~0ull;
-  for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) {
-    uint64_t sz = e[b + 1] - e[b];
+  float ratio = 0.0f;
+  for (uint32_t beta = threadIdx.x; beta < g.R; beta += blockDim.x) {
+    const uint32_t i = g.run_inst[beta];
+    const uint32_t b = beta - g.R0[i];
+    const uint64_t sz = e[g.R0[i] + i + b + 1] - e[g.R0[i] + i + b];
     mx = umax(mx, sz);
     mn = umin(mn, sz);
+    const uint64_t ni = g.koff[i + 1] - g.koff[i];
+    if (ni) ratio = fmaxf(ratio, (float)((double)sz * g.P[i] / (double)ni));
   }
   smax[threadIdx.x] = mx;
   smin[threadIdx.x] = mn;
+  sratio[threadIdx.x] = ratio;
   __syncthreads();
   for (int d = 128; d > 0; d >>= 1) {
     if (threadIdx.x < d) {
       smax[threadIdx.x] = umax(smax[threadIdx.x], smax[threadIdx.x + d]);
       smin[threadIdx.x] = umin(smin[threadIdx.x], smin[threadIdx.x + d]);
+      sratio[threadIdx.x] = fmaxf(sratio[threadIdx.x], sratio[threadIdx.x + d]);
     }
     __syncthreads();
   }
-  if (user_bounds)
-    for (uint32_t b = threadIdx.x; b <= P; b += blockDim.x) user_bounds[b] = e[b];
-  if (threadIdx.x == 0 && st) {
-    st->n = n;
-    st->P = P;
-    st->s = s;
-    st->max_bucket = smax[0];
-    st->min_bucket = P ? smin[0] : 0;
-    st->splitter_mode = mode;
-    st->fallback = 0;
-    st->error = err_word ? *err_word : 0;
-    st->passes = passes;
-    st->launches = launches;
-    st->reserved = 0;
+  if (user_bounds && g.I == 1)
+    for (uint32_t b = threadIdx.x; b <= g.P[0]; b += blockDim.x) user_bounds[b] = e[b];
+  if (threadIdx.x == 0) {
+    if (max_ratio_out) *max_ratio_out = sratio[0];
+    if (st) {
+      st->n = n_total;
+      st->P = g.I == 1 ? g.P[0] : g.R;
+      st->s = s;
+      st->max_bucket = smax[0];
+      st->min_bucket = g.R ? smin[0] : 0;
+      st->splitter_mode = mode;
+      st->fallback = 0;
+      st->error = err_word ? *err_word : 0;
+      st->passes = passes;
+      st->launches = launches;
+      st->max_over_mean = sratio[0];
+    }
   }
 }
 

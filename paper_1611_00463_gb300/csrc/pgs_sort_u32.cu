@@ -3,7 +3,7 @@
 
 namespace pgs {
 
-int sort_u32(const Plan& p, const Options& o, const void* kin, const uint32_t* vin, void* kout,
+int sort_u32(const Shape& p, const Options& o, const void* kin, const uint32_t* vin, void* kout,
              uint32_t* vout, cudaStream_t st) {
   auto ki = static_cast<const uint32_t*>(kin);
   auto ko = static_cast<uint32_t*>(kout);
@@ -11,8 +11,23 @@ int sort_u32(const Plan& p, const Options& o, const void* kin, const uint32_t* v
   return run_sort<uint32_t, false>(p, o, ki, nullptr, ko, nullptr, st);
 }
 
-int fit_u32(const FitPlan& f, const Options& o, const void* samples, void* out, cudaStream_t st) {
-  return run_fit<uint32_t>(f, o, static_cast<const uint32_t*>(samples), static_cast<uint32_t*>(out), st);
+int fit_u32(uint64_t m, uint32_t P, const Options& o, const void* samples, void* out, cudaStream_t st) {
+  return run_fit<uint32_t>(m, P, o, static_cast<const uint32_t*>(samples), static_cast<uint32_t*>(out), st);
+}
+
+int batch_attrs_u32(bool vals) {
+  return vals ? set_all_smem_attrs<uint32_t, true>() : set_all_smem_attrs<uint32_t, false>();
+}
+
+int batch_u32(const Shape& sh, const Options& o, void* keys, uint32_t* vals, cudaStream_t st) {
+  Ctx c;
+  c.st = st;
+  c.timer = o.timer;
+  Buffers b;
+  carve(sh, o.workspace, &b);
+  auto k = static_cast<uint32_t*>(keys);
+  if (vals) return run_pipeline<uint32_t, true>(sh, o, k, vals, k, vals, c, b);
+  return run_pipeline<uint32_t, false>(sh, o, k, nullptr, k, nullptr, c, b);
 }
 
 }  // namespace pgs

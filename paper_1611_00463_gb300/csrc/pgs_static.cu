@@ -18,8 +18,8 @@
 static __device__ __align__(256) unsigned char g_pgs_static_scratch[PGS_STATIC_SCRATCH_BYTES];
 
 namespace pgs {
-int sort_u32(const Plan&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
-int sort_u64(const Plan&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int sort_u32(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int sort_u64(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
 
 namespace {
 
@@ -58,7 +58,7 @@ extern "C" int pgs_sort_static(void* keys, uint32_t* vals, uint64_t n, uint32_t 
   if (n == 0) return PGS_OK;
   if (!keys) return PGS_ERR_INVALID;
   if (n > PGS_STATIC_MAX_KEYS || P > PGS_STATIC_MAX_P) return PGS_ERR_UNSUPPORTED;
-  Plan p = make_plan(n, P, vals != nullptr, o);
+  Shape p = single_shape(n, P, vals != nullptr, o);
   Buffers b;
   const size_t need = carve(p, nullptr, &b);
   if (need > PGS_STATIC_SCRATCH_BYTES) return PGS_ERR_UNSUPPORTED;

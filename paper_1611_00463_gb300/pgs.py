@@ -58,7 +58,7 @@ class pgs_stats(ctypes.Structure):
         ("error", ctypes.c_uint32),
         ("passes", ctypes.c_uint32),
         ("launches", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("max_over_mean", ctypes.c_float),
     ]
 
     def as_dict(self) -> dict:
@@ -86,6 +86,14 @@ EXPORTS = {
     "pgs_timer_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                                       ctypes.c_void_p]),
     "pgs_kernel_name": (ctypes.c_char_p, [ctypes.c_uint32]),
+    "pgs_batch_auto_partitions": (ctypes.c_uint32, [ctypes.c_uint64]),
+    "pgs_batch_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "pgs_batch_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "pgs_sort_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "pgs_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 KERNELS = ["block_sort", "merge", "partition", "pairs", "scan", "sample", "splitters", "cut_search",
@@ -262,6 +270,57 @@ def pgs_sort_static(keys: torch.Tensor, vals: torch.Tensor | None, P: int, cfg: 
     cfg = cfg if cfg is not None else pgs_config()
     _check(load().pgs_sort_static(_ptr(keys), _ptr(vals), n, P, _stream(stream), ctypes.byref(cfg)),
            "pgs_sort_static")
+
+
+def pgs_batch_auto_partitions(n: int) -> int:
+    return load().pgs_batch_auto_partitions(n)
+
+
+class Batch:
+    """A batch of independent sort instances (pgs_batch_create / upload / sort).
+
+    offsets: host sequence of num+1 key offsets; P: host sequence of num
+    partition counts, or None for the automatic rule."""
+
+    def __init__(self, offsets, P=None, dtype: str = "u32", with_vals: bool = True, device=None, **opts):
+        import numpy as np
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+        self.num = len(off) - 1
+        self.n = int(off[-1])
+        pv = None if P is None else np.ascontiguousarray(np.asarray(P, dtype=np.uint32))
+        self.dtype = dtype
+        self.opts = opts
+        cfg = make_config(dtype=dtype, **opts)
+        h = ctypes.c_void_p()
+        _check(load().pgs_batch_create(off.ctypes.data, self.num, pv.ctypes.data if pv is not None else None,
+                                       int(with_vals), ctypes.byref(cfg), ctypes.byref(h)), "pgs_batch_create")
+        self.handle = h.value
+        nbytes = load().pgs_batch_workspace_bytes(self.handle)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+        _check(load().pgs_batch_upload(self.handle, self.workspace.data_ptr(), nbytes,
+                                       _stream(None)), "pgs_batch_upload")
+
+    def config(self, stats: torch.Tensor | None = None, timer: "Timer | None" = None) -> pgs_config:
+        return make_config(dtype=self.dtype, workspace=self.workspace, stats=stats, timer=timer, **self.opts)
+
+    def sort(self, keys: torch.Tensor, vals: torch.Tensor | None, stream=None, cfg: pgs_config | None = None):
+        """Sort every instance of keys (and vals) in place."""
+        if keys.numel() != self.n or (vals is not None and vals.numel() != self.n):
+            raise ValueError("length mismatch")
+        cfg = cfg if cfg is not None else self.config()
+        _check(load().pgs_sort_batched(self.handle, _ptr(keys), _ptr(vals), _stream(stream), ctypes.byref(cfg)),
+               "pgs_sort_batched")
+
+    def close(self):
+        if self.handle:
+            load().pgs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def pgs_fit_workspace_bytes(m: int, P: int, cfg: pgs_config | None = None) -> int:

@@ -43,6 +43,8 @@ def test_struct_sizes_match_header(lib):
     from paper_1611_00463_gb300 import pgs
     # pgs_stats is copied byte for byte from the device block.
     assert ctypes.sizeof(pgs.pgs_stats) == 56
+    assert [lib.pgs_batch_auto_partitions(n) for n in [1, 65535, 65536, 131071, 131072, 1 << 24, 1 << 30]] == \
+        [1, 1, 1, 1, 2, 256, 256]
     assert ctypes.sizeof(pgs.pgs_config) == 32 + 8 * 8
     assert ctypes.sizeof(pgs.pgs_launch_record) == 24
     assert [lib.pgs_kernel_name(i).decode() for i in range(len(pgs.KERNELS))] == pgs.KERNELS
@@ -105,3 +107,24 @@ def test_invalid_arguments_rejected_before_launch(lib):
     assert lib.pgs_fit_splitters(fake, 3, 8, None, ctypes.byref(cfg3), fake, None) == pgs.PGS_ERR_INVALID
     # stats: NULL
     assert lib.pgs_get_stats(None, None, None) == pgs.PGS_ERR_INVALID
+
+
+def test_batch_plan_host_only(lib):
+    import numpy as np
+    from paper_1611_00463_gb300 import pgs
+    cfg = pgs.make_config(dtype="u64")
+    off = np.array([0, 10, 10, 200_000, 200_005], dtype=np.uint64)
+    h = ctypes.c_void_p()
+    assert lib.pgs_batch_create(off.ctypes.data, 4, None, 1, ctypes.byref(cfg), ctypes.byref(h)) == pgs.PGS_OK
+    ws = lib.pgs_batch_workspace_bytes(h)
+    assert ws >= 200_005 * 12
+    # uploading to a misaligned or small workspace is refused before any copy
+    assert lib.pgs_batch_upload(h, ctypes.c_void_p(0x1001), 1 << 40, None) == pgs.PGS_ERR_WORKSPACE
+    assert lib.pgs_batch_upload(h, ctypes.c_void_p(0x1000), 16, None) == pgs.PGS_ERR_WORKSPACE
+    assert lib.pgs_batch_destroy(h) == pgs.PGS_OK
+    bad = np.array([0, 10, 5], dtype=np.uint64)                     # decreasing offsets
+    assert lib.pgs_batch_create(bad.ctypes.data, 2, None, 1, ctypes.byref(cfg), ctypes.byref(h)) == \
+        pgs.PGS_ERR_INVALID
+    zeroP = np.array([0], dtype=np.uint32)
+    assert lib.pgs_batch_create(off.ctypes.data, 1, zeroP.ctypes.data, 1, ctypes.byref(cfg),
+                                ctypes.byref(h)) == pgs.PGS_ERR_INVALID
