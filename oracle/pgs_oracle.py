@@ -367,3 +367,183 @@ def buckets(keys: np.ndarray, P: int, dtype: str, samples_per_run: int | None = 
     e, cut, lb, cnt = investigator(run_ord, t, n, P, variant)
     return {"P": P, "s": s, "bounds": bounds, "splitters": t, "e": e, "cut": cut,
             "stats": load_stats(e)}
+
+
+# ---------------------------------------------------------------------------
+# Learned-CDF splitters (not in the paper): a 1 -> 32 -> 32 -> 1 ReLU model of
+# the key CDF, trained on the method's own sample, predicts bucket ids; the
+# sampled splitters with the investigator judge its imbalance.
+#
+# Monotone by construction: units 0..15 see +x through positive weights and
+# enter the output with positive weights (a rising convex part); units 16..31
+# see -x and enter with negative weights (a rising concave part); layer 2 only
+# connects units of the same half, with positive weights.  Every fp32
+# operation of the evaluation is monotone in the right direction, so the fp32
+# bucket id is non-decreasing in the key and the buckets are key ranges.
+#
+# Parity: bucket ids are pinned bit for bit (same fp32 operation order on both
+# sides, no fused multiply-add); training is "parity unpinned" bit for bit and
+# pinned by its properties (finite-difference gradients, loss decrease,
+# monotonicity, loss close to this fp64 reference trainer).
+# ---------------------------------------------------------------------------
+
+MLP_H = 32
+MLP_HALF = 16
+MLP_FLOATS = 1 * 32 + 32 + 32 * 32 + 32 + 32 * 1 + 1
+MLP_STEPS = 300
+MLP_LR = 0.01
+MLP_OFF_DIAG = -6.0
+
+
+def mlp_block_mask() -> np.ndarray:
+    """W2[k, j] exists only when units k and j are in the same half."""
+    i = np.arange(MLP_H)
+    return (i[:, None] < MLP_HALF) == (i[None, :] < MLP_HALF)
+
+
+def mlp_sign() -> np.ndarray:
+    return np.where(np.arange(MLP_H) < MLP_HALF, 1.0, -1.0)
+
+
+def mlp_norm(sorted_sample_ord: np.ndarray):
+    """Input normalisation: x = f32(f64(max(k, kmin) - kmin)) * scale with
+    scale = f32(1) / f32(f64(kmax - kmin)) (0 when every sample is equal)."""
+    kmin = int(sorted_sample_ord[0])
+    span = int(sorted_sample_ord[-1]) - kmin
+    scale = np.float32(0.0) if span == 0 else np.float32(1.0) / np.float32(np.float64(span))
+    return kmin, np.float32(scale)
+
+
+def mlp_inputs(keys_ord: np.ndarray, kmin: int, scale: np.float32) -> np.ndarray:
+    d = np.maximum(keys_ord.astype(np.uint64), np.uint64(kmin)) - np.uint64(kmin)
+    return d.astype(np.float64).astype(np.float32) * np.float32(scale)
+
+
+def mlp_init(x_sorted: np.ndarray) -> dict:
+    """Deterministic start: layer-1 knots at the training inputs of sorted index
+    floor((j + 1/2) m / 16), layer 2 close to the identity inside each half."""
+    m = len(x_sorted)
+    q = np.array([float(x_sorted[((2 * j + 1) * m) // (2 * MLP_HALF)]) for j in range(MLP_HALF)])
+    b1 = np.concatenate([-q, q])
+    V2 = np.where(np.eye(MLP_H, dtype=bool), 0.0, MLP_OFF_DIAG)
+    V2 = np.where(mlp_block_mask(), V2, 0.0)
+    return {"v1": np.zeros(MLP_H), "b1": b1, "V2": V2, "b2": np.zeros(MLP_H),
+            "v3": np.full(MLP_H, np.log(1.0 / MLP_H)), "b3": np.array(0.5)}
+
+
+def mlp_effective(raw: dict) -> dict:
+    """Signed, exponentiated weights of the monotone network."""
+    s = mlp_sign()
+    mask = mlp_block_mask()
+    return {"w1": s * np.exp(raw["v1"]), "b1": raw["b1"],
+            "W2": np.where(mask, np.exp(np.where(mask, raw["V2"], 0.0)), 0.0), "b2": raw["b2"],
+            "w3": s * np.exp(raw["v3"]), "b3": raw["b3"]}
+
+
+def mlp_forward64(eff: dict, x: np.ndarray):
+    z1 = x[:, None] * eff["w1"] + eff["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ eff["W2"].T + eff["b2"]
+    h2 = np.maximum(z2, 0.0)
+    return h2 @ eff["w3"] + eff["b3"], (z1, h1, z2, h2)
+
+
+def mlp_loss_grad(raw: dict, x: np.ndarray, t: np.ndarray):
+    """Mean squared error of the CDF fit and its gradient in the raw parameters."""
+    eff = mlp_effective(raw)
+    y, (z1, h1, z2, h2) = mlp_forward64(eff, x)
+    m = len(x)
+    r = y - t
+    dy = 2.0 * r / m
+    g = {"b3": np.array(dy.sum())}
+    g["v3"] = (h2.T @ dy) * eff["w3"]                       # d w3 / d v3 = w3
+    dz2 = (dy[:, None] * eff["w3"]) * (z2 > 0)
+    g["b2"] = dz2.sum(axis=0)
+    g["V2"] = np.where(mlp_block_mask(), (dz2.T @ h1) * eff["W2"], 0.0)
+    dz1 = (dz2 @ eff["W2"]) * (z1 > 0)
+    g["b1"] = dz1.sum(axis=0)
+    g["v1"] = (dz1 * x[:, None]).sum(axis=0) * eff["w1"]
+    return float(np.mean(r * r)), g
+
+
+def mlp_train(x_sorted: np.ndarray, steps: int = MLP_STEPS, lr: float = MLP_LR):
+    """Full-batch Adam (beta1 0.9, beta2 0.999, eps 1e-8) on targets (i + 1/2)/m,
+    in float64.  Returns the raw parameters and the loss before the last step."""
+    x = np.asarray(x_sorted, dtype=np.float64)
+    m = len(x)
+    t = (np.arange(m) + 0.5) / m
+    raw = mlp_init(x)
+    mom = {k: np.zeros_like(v) for k, v in raw.items()}
+    vel = {k: np.zeros_like(v) for k, v in raw.items()}
+    mask = mlp_block_mask()
+    loss = None
+    for step in range(1, steps + 1):
+        loss, g = mlp_loss_grad(raw, x, t)
+        for k in raw:
+            mom[k] = 0.9 * mom[k] + 0.1 * g[k]
+            vel[k] = 0.999 * vel[k] + 0.001 * g[k] * g[k]
+            upd = lr * (mom[k] / (1 - 0.9 ** step)) / (np.sqrt(vel[k] / (1 - 0.999 ** step)) + 1e-8)
+            raw[k] = raw[k] - (np.where(mask, upd, 0.0) if k == "V2" else upd)
+    return raw, loss
+
+
+def mlp_pack(eff: dict) -> np.ndarray:
+    """The 1153 float32 weights in library order: w1, b1, W2 (row k, column j), b2, w3, b3."""
+    return np.concatenate([eff["w1"], eff["b1"], eff["W2"].reshape(-1), eff["b2"], eff["w3"],
+                           np.atleast_1d(eff["b3"])]).astype(np.float32)
+
+
+def mlp_unpack(w: np.ndarray) -> dict:
+    w = np.asarray(w, dtype=np.float32)
+    return {"w1": w[0:32], "b1": w[32:64], "W2": w[64:1088].reshape(32, 32), "b2": w[1088:1120],
+            "w3": w[1120:1152], "b3": w[1152]}
+
+
+def mlp_monotone(w: np.ndarray) -> bool:
+    """Sign pattern that makes the network non-decreasing (off-half W2 entries are unused)."""
+    e = mlp_unpack(w)
+    A = slice(0, MLP_HALF)
+    Bh = slice(MLP_HALF, MLP_H)
+    return bool(np.all(e["w1"][A] >= 0) and np.all(e["w1"][Bh] <= 0) and np.all(e["W2"][A, A] >= 0)
+                and np.all(e["W2"][Bh, Bh] >= 0) and np.all(e["w3"][A] >= 0) and np.all(e["w3"][Bh] <= 0))
+
+
+def mlp_bucket_f32(w: np.ndarray, x32: np.ndarray, P: int) -> np.ndarray:
+    """Bucket id min(P-1, floor(P * clamp(y, 0, 1))) with y evaluated in float32 in
+    this exact order (every product and sum rounded, no fused multiply-add):
+    h1_j = max(w1_j x + b1_j, 0); acc = b2_k, acc += W2_kj h1_j over j of k's half
+    in increasing j, h2_k = max(acc, 0); y = b3, y += w3_k h2_k for k = 0..31."""
+    e = mlp_unpack(w)
+    f = np.float32
+    x32 = np.asarray(x32, dtype=np.float32)
+    h1 = [np.maximum(e["w1"][j] * x32 + e["b1"][j], f(0)) for j in range(MLP_H)]
+    h2 = []
+    for k in range(MLP_H):
+        acc = np.full(x32.shape, e["b2"][k], dtype=np.float32)
+        lo = 0 if k < MLP_HALF else MLP_HALF
+        for j in range(lo, lo + MLP_HALF):
+            acc = acc + e["W2"][k, j] * h1[j]
+        h2.append(np.maximum(acc, f(0)))
+    y = np.full(x32.shape, e["b3"], dtype=np.float32)
+    for k in range(MLP_H):
+        y = y + e["w3"][k] * h2[k]
+    c = np.minimum(np.maximum(y, f(0)), f(1))
+    b = np.floor(f(P) * c).astype(np.int64)
+    return np.minimum(b, P - 1)
+
+
+def learned_buckets(keys: np.ndarray, P: int, dtype: str, w: np.ndarray, kmin: int, scale) -> dict:
+    """Steps 1 and 4 with model bucket ids: every run sorted, every key's bucket
+    from the model, cut[r][b] = #keys of run r with bucket id < b, e_b = sum_r cut."""
+    n = len(keys)
+    P = effective_partitions(n, P)
+    bounds = run_bounds(n, P)
+    o = ord_bits(keys, dtype)
+    cut = np.zeros((P, P + 1), dtype=np.int64)
+    for r in range(P):
+        run = np.sort(o[bounds[r]:bounds[r + 1]], kind="stable")
+        ids = mlp_bucket_f32(w, mlp_inputs(run, kmin, scale), P)
+        hist = np.bincount(ids, minlength=P)
+        cut[r, 1:] = np.cumsum(hist)
+    e = cut.sum(axis=0)
+    return {"P": P, "cut": cut, "e": e, "stats": load_stats(e)}
