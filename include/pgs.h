@@ -120,6 +120,11 @@ typedef struct pgs_config {
   void*     stats;            /* a pgs_stats in device memory */
   uint64_t  spin_limit;       /* bound on device-side waits; 0 = default */
   pgs_timer* timer;           /* optional: record every launch's duration (host object) */
+  /* LEARNED mode only (single sorts): */
+  const float* model;         /* optional device model of PGS_MLP_WORDS words to use instead of
+                                 training one; rejected (sampled cuts kept) if its signs do not make
+                                 it monotone */
+  float*    model_out;        /* optional device buffer of PGS_MLP_WORDS words: the model used */
 } pgs_config;
 
 /* Load statistics of one sort (Table II reports the per-processor share). */
@@ -130,7 +135,7 @@ typedef struct pgs_stats {
   uint64_t max_bucket;        /* max_b (e_{b+1} - e_b) */
   uint64_t min_bucket;        /* min_b (e_{b+1} - e_b) */
   uint32_t splitter_mode;     /* mode that produced the buckets */
-  uint32_t fallback;          /* 1 if the learned splitters were rejected */
+  uint32_t fallback;          /* LEARNED: 1 if the sampled splitters replaced the model's */
   uint32_t error;             /* device-side error word; 0 = none */
   uint32_t passes;            /* full passes over the data the sort made */
   uint32_t launches;          /* kernels the call launched */
@@ -208,11 +213,21 @@ int pgs_batch_destroy(pgs_batch* batch);
 /* Step 3 of Section IV on a caller-given sample: sort m sample keys (device,
  * any order) stably and write the P-1 splitters t_b = sample at sorted index
  * floor(b m / P) - 1 to splitters_out (device, P-1 keys).  In LEARNED mode it
- * also trains the CDF model and writes its PGS_MLP_FLOATS weights to
- * model_out (device, may be NULL).  Needs cfg->workspace of at least
+ * also trains the CDF model on the sorted sample and writes its
+ * PGS_MLP_WORDS words to model_out (device, may be NULL).  Needs cfg->workspace of at least
  * pgs_fit_workspace_bytes(m, P, cfg). */
+/* Learned-CDF model: 1 -> 32 -> 32 -> 1 ReLU, FP32.  Layout of its
+ * PGS_MLP_WORDS 4-byte words: w1[32], b1[32], W2[32][32] (row = output unit),
+ * b2[32], w3[32], b3 (the PGS_MLP_FLOATS weights), then the input
+ * normalisation kmin (low word, high word), scale (float), and a validity flag
+ * (1 = monotone).  Input x = f32(f64(max(key, kmin) - kmin)) * scale on the
+ * key's total-order bits; bucket = min(P-1, floor(P * clamp(y, 0, 1))).
+ * Units 0..15 must have w1 >= 0 and w3 >= 0, units 16..31 w1 <= 0 and
+ * w3 <= 0, W2 >= 0 within each half (entries across halves are ignored), so
+ * that the bucket id never decreases as the key grows. */
 #define PGS_MLP_HIDDEN 32
 #define PGS_MLP_FLOATS (1 * 32 + 32 + 32 * 32 + 32 + 32 * 1 + 1)
+#define PGS_MLP_WORDS (PGS_MLP_FLOATS + 4)
 size_t pgs_fit_workspace_bytes(uint64_t m, uint32_t P, const pgs_config* cfg);
 int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
                       const pgs_config* cfg, void* splitters_out, float* model_out);

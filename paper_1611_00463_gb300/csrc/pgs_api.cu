@@ -9,8 +9,8 @@
 namespace pgs {
 int sort_u32(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
 int sort_u64(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
-int fit_u32(uint64_t, uint32_t, const Options&, const void*, void*, cudaStream_t);
-int fit_u64(uint64_t, uint32_t, const Options&, const void*, void*, cudaStream_t);
+int fit_u32(uint64_t, uint32_t, const Options&, const void*, void*, float*, cudaStream_t);
+int fit_u64(uint64_t, uint32_t, const Options&, const void*, void*, float*, cudaStream_t);
 
 namespace {
 
@@ -90,7 +90,6 @@ int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
   Options o;
   int rc = read_options(cfg, &o);
   if (rc) return rc;
-  (void)model_out;
   if (P == 0) return PGS_ERR_INVALID;
   if (P == 1) return PGS_OK;                       // no splitters
   if (!samples || !splitters_out || m < P) return PGS_ERR_INVALID;
@@ -101,8 +100,8 @@ int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
   rc = use_device_of(samples);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (o.dtype == PGS_U64) return fit_u64(m, P, o, samples, splitters_out, st);
-  return fit_u32(m, P, o, samples, splitters_out, st);
+  if (o.dtype == PGS_U64) return fit_u64(m, P, o, samples, splitters_out, model_out, st);
+  return fit_u32(m, P, o, samples, splitters_out, model_out, st);
 }
 
 int pgs_get_stats(const void* stats_dev, pgs_stats* host_out, void* stream) {

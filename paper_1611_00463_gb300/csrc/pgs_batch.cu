@@ -40,6 +40,7 @@ int pgs_batch_create(const uint64_t* offsets, uint32_t num, const uint32_t* P, i
   Options o;
   int rc = read_options(cfg, &o);
   if (rc) return rc;
+  if (o.splitter_mode == PGS_SPLITTERS_LEARNED) return PGS_ERR_UNSUPPORTED;   // single sorts only
   pgs_batch* bt = new (std::nothrow) pgs_batch;
   if (!bt) return PGS_ERR_INVALID;
   bt->o = o;
@@ -142,6 +143,7 @@ int pgs_sort_batched(pgs_batch* bt, void* keys, uint32_t* vals, void* stream, co
   int rc = read_options(cfg, &o);
   if (rc) return rc;
   if (o.dtype != bt->o.dtype) return PGS_ERR_INVALID;
+  if (o.splitter_mode == PGS_SPLITTERS_LEARNED) return PGS_ERR_UNSUPPORTED;
   if ((vals != nullptr) != bt->sh.vals) return PGS_ERR_INVALID;
   if (bt->sh.n == 0) return PGS_OK;
   if (!keys) return PGS_ERR_INVALID;

@@ -11,6 +11,7 @@
 
 #include "pgs.h"
 #include "pgs_kernels.cuh"
+#include "pgs_learned.cuh"
 
 namespace pgs {
 
@@ -40,6 +41,8 @@ struct Options {
   void* splitters = nullptr;
   void* stats = nullptr;
   pgs_timer* timer = nullptr;
+  const float* model = nullptr;
+  float* model_out = nullptr;
 };
 
 // Validates and copies a (possibly NULL) pgs_config.  Returns PGS_OK or an error.
@@ -59,13 +62,14 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->splitters = cfg->splitters;
   o->stats = cfg->stats;
   o->timer = cfg->timer;
+  o->model = cfg->model;
+  o->model_out = cfg->model_out;
   if (o->dtype < PGS_U32 || o->dtype > PGS_F32) return PGS_ERR_INVALID;
   if (!(o->eps > 0.0f) || o->eps > 1.0f) return PGS_ERR_INVALID;
   if (o->investigator < 0 || o->investigator > 2) return PGS_ERR_INVALID;
   if (o->exchange < 0 || o->exchange > 2) return PGS_ERR_INVALID;
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
   if (o->exchange == PGS_EXCHANGE_FUSED) return PGS_ERR_UNSUPPORTED;
-  if (o->splitter_mode == PGS_SPLITTERS_LEARNED) return PGS_ERR_UNSUPPORTED;
   return PGS_OK;
 }
 
@@ -97,6 +101,7 @@ struct Shape {
   uint64_t s = 0;            // samples per run of a single sort (reported in the stats)
   int w = 4;                 // key bytes
   bool vals = false;
+  bool learned = false;      // learned-CDF splitters (single sorts only)
   int run_rounds = 0;        // merge rounds growing block-sorted tiles into runs (step 1)
   int bucket_rounds = 0;     // merge rounds of steps 3 and 6: ceil(log2 Pmax)
   uint64_t max_pairs = 1;
@@ -144,6 +149,7 @@ inline Shape single_shape(uint64_t n, uint32_t P_req, bool vals, const Options& 
   sh.maxlen = ceil_div(n, P);
   sh.s = P > 1 ? samples_per_run(P, sh.w, o) : 0;
   sh.S = P > 1 ? (sh.s >= sh.maxlen ? n : (uint64_t)P * sh.s) : 0;
+  sh.learned = o.splitter_mode == PGS_SPLITTERS_LEARNED && P > 1;
   finish_shape(sh);
   return sh;
 }
@@ -163,6 +169,9 @@ struct Buffers {
   uint64_t* run_off; uint32_t* run_inst;
   uint32_t* err;
   float* max_ratio;
+  // learned splitters
+  MlpState* mlp; float* mlp_part; float* model; uint64_t* hist; uint64_t* hscan; uint64_t* cutL; uint64_t* eL;
+  uint32_t* fallback; float* learned_ratio;
   Geo geo(const Shape& sh) const {
     return Geo{koff, Pt, R0, mat, seg, st, run_off, run_inst, sh.I, sh.R};
   }
@@ -205,6 +214,23 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->first_seg = c.take<uint64_t>(ceil_div(std::max<uint64_t>(sh.n, 1), kScatterTile));
   b->err = c.take<uint32_t>(1);
   b->max_ratio = c.take<float>(1);
+  b->mlp = nullptr;
+  b->mlp_part = nullptr;
+  b->model = nullptr;
+  b->hist = b->hscan = b->cutL = b->eL = nullptr;
+  b->fallback = nullptr;
+  b->learned_ratio = nullptr;
+  if (sh.learned) {
+    b->mlp = c.take<MlpState>(1);
+    b->mlp_part = c.take<float>(ceil_div(std::max<uint64_t>(sh.S, 1), kMlpBatch) * (kMlpW + 1));
+    b->model = c.take<float>(kMlpWords);
+    b->hist = c.take<uint64_t>(sh.Q);
+    b->hscan = c.take<uint64_t>(sh.Q + 1);
+    b->cutL = c.take<uint64_t>(sh.MAT);
+    b->eL = c.take<uint64_t>(sh.R + 1);
+    b->fallback = c.take<uint32_t>(1);
+    b->learned_ratio = c.take<float>(1);
+  }
   return c.used;
 }
 
@@ -313,6 +339,8 @@ inline int set_smem_attrs() {
                                 (int)Merge2Layout<K, V, kMergeNT, kMergeVT>::bytes));
   PGS_CUDA(cudaFuncSetAttribute(k_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ScatterSmem<K>)));
+  PGS_CUDA(cudaFuncSetAttribute(k_mlp_grad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sizeof(MlpGradSmem)));
   return PGS_OK;
 }
 
@@ -341,6 +369,58 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
 // The batch tables must already be in the workspace (k_tables_single for a
 // single sort, or uploaded by the batch API).
 // ---------------------------------------------------------------------------
+
+// Learned splitters (single sort, P > 1): the model (trained on the sorted
+// sample `sorted` or the caller's), the per-run histogram of every key's
+// bucket, the learned cuts, and the judge's choice between them and the
+// sampled cuts already in b.cut / b.e.
+template <typename K>
+int learned_cuts(const Shape& sh, const Options& o, const K* sorted, const K* runs, Ctx& c, const Buffers& b) {
+  cudaStream_t st = c.st;
+  const uint32_t P = sh.R;
+  const uint64_t S = sh.S;
+  if (o.model) {
+    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 8 * kMlpWords, [&] {
+      k_mlp_validate<<<1, 256, 0, st>>>(o.model, b.model);
+    }));
+  } else {
+    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 16 * kMlpW, [&] { k_mlp_init<K><<<1, 256, 0, st>>>(sorted, S, b.mlp); }));
+    const uint32_t nparts = (uint32_t)ceil_div(S, kMlpBatch);
+    for (uint32_t step = 1; step <= (uint32_t)kMlpSteps; ++step) {
+      PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, S * sizeof(K), [&] {
+        k_mlp_grad<K><<<nparts, kMlpBatch, sizeof(MlpGradSmem), st>>>(sorted, S, b.mlp, b.mlp_part);
+      }));
+      PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 4ull * nparts * (kMlpW + 1), [&] {
+        k_mlp_adam<<<1, 1024, 0, st>>>(b.mlp_part, nparts, b.mlp, step, S);
+      }));
+    }
+    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 16 * kMlpW, [&] { k_mlp_finalize<<<1, 256, 0, st>>>(b.mlp, b.model); }));
+  }
+  if (o.model_out) {
+    PGS_CUDA(cudaMemcpyAsync(o.model_out, b.model, 4ull * kMlpWords, cudaMemcpyDeviceToDevice, st));
+  }
+  // K11: every key's bucket, one pass over the sorted runs, as per-run counts.
+  PGS_CUDA(cudaMemsetAsync(b.hist, 0, sizeof(uint64_t) * sh.Q, st));
+  const uint64_t segs_per_run = std::max<uint64_t>(1, ceil_div(sh.maxlen, kHistWarpKeys));
+  const uint64_t warps = segs_per_run * P;
+  PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 4, sh.n * sizeof(K) / 2, [&] {
+    k_learned_hist<K><<<(unsigned)ceil_div(warps, kHistNT / 32), kHistNT, 0, st>>>(runs, b.run_off, P, segs_per_run,
+                                                                                  b.model, b.hist);
+  }));
+  PGS_TRY(scan_u64(c, b.hist, b.hscan, sh.Q, b.scan_sums, b.scan_sums2, 4));
+  PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 16 * sh.MAT, [&] {
+    k_learned_cuts<<<grid_for(sh.MAT, 256), 256, 0, st>>>(b.hscan, P, b.cutL);
+  }));
+  PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 8 * sh.MAT, [&] {
+    k_learned_colsum<<<grid_for(P + 1, 256), 256, 0, st>>>(b.cutL, P, b.eL);
+  }));
+  PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 8 * (uint64_t)P, [&] {
+    k_learned_judge<<<1, 256, 0, st>>>(b.eL, P, sh.n, o.eps, b.model, b.fallback, b.learned_ratio);
+  }));
+  return launch(c, PGS_KERNEL_INVESTIGATOR, 4, 16 * sh.MAT, [&] {
+    k_learned_select<<<grid_for(sh.MAT, 256), 256, 0, st>>>(b.cutL, b.eL, P, b.fallback, b.cut, b.e);
+  });
+}
 
 template <typename K, bool V>
 int set_all_smem_attrs() {
@@ -428,6 +508,7 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       k_investigator<K><<<R, 256, 0, st>>>(b.lb, b.cnt, static_cast<const K*>(b.spl), g, o.investigator, b.cut,
                                            b.e);
     }));
+    if (sh.learned) PGS_TRY((learned_cuts<K>(sh, o, sa, cur_k, c, b)));
     // Section IV-C: receive offsets of every (bucket, run) segment.
     PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 32 * sh.Q, [&] {
       k_bucket_sizes<<<grid_for(sh.Q, 256), 256, 0, st>>>(g, sh.Q, b.cut, b.sizes, b.seg_src);
@@ -469,9 +550,10 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
   }
   const uint32_t launches = c.launches + 1;             // including the statistics kernel
   return launch(c, PGS_KERNEL_STATS, 0, 8 * ((uint64_t)R + sh.I), [&] {
-    k_stats<<<1, 256, 0, st>>>(g, b.e, n, (uint32_t)std::min<uint64_t>(sh.s, 0xFFFFFFFFu), PGS_SPLITTERS_SAMPLED,
-                               (uint32_t)sh.passes, launches, b.err, static_cast<DevStats*>(o.stats),
-                               o.bucket_bounds, b.max_ratio);
+    k_stats<<<1, 256, 0, st>>>(g, b.e, n, (uint32_t)std::min<uint64_t>(sh.s, 0xFFFFFFFFu),
+                               sh.learned ? PGS_SPLITTERS_LEARNED : PGS_SPLITTERS_SAMPLED, (uint32_t)sh.passes,
+                               launches, b.err, b.fallback, static_cast<DevStats*>(o.stats), o.bucket_bounds,
+                               b.max_ratio);
   });
 }
 
@@ -499,35 +581,79 @@ int run_sort(const Shape& sh, const Options& o, const K* kin, const uint32_t* vi
 // own workspace, then every (m/P)-th key is picked.
 // ---------------------------------------------------------------------------
 
-inline size_t fit_workspace(uint64_t m, const Options& o, Shape* sh_out, size_t* sorted_at) {
-  Shape sh = single_shape(m, 1, false, o);
+struct FitLayout {
+  size_t sorted = 0, ordered = 0, mlp = 0, part = 0, total = 0;
+};
+
+// The fit's workspace: a single sort of the sample (P = 1, keys only), the
+// sorted sample, and for LEARNED mode its order-form copy and the trainer state.
+inline size_t fit_workspace(uint64_t m, const Options& o, Shape* sh_out, FitLayout* lay_out) {
+  Options inner = o;
+  inner.splitter_mode = PGS_SPLITTERS_SAMPLED;
+  Shape sh = single_shape(m, 1, false, inner);
   Buffers b;
-  size_t used = carve(sh, nullptr, &b);
-  used = (used + kAlign - 1) / kAlign * kAlign;
-  if (sorted_at) *sorted_at = used;
+  Carver c(nullptr);
+  c.used = carve(sh, nullptr, &b);
+  FitLayout lay;
+  const uint64_t mm = std::max<uint64_t>(m, 1);
+  c.take<char>(0);
+  lay.sorted = (c.used + kAlign - 1) / kAlign * kAlign;
+  c.used = lay.sorted + mm * key_bytes(o.dtype);
+  if (o.splitter_mode == PGS_SPLITTERS_LEARNED) {
+    lay.ordered = (c.used + kAlign - 1) / kAlign * kAlign;
+    c.used = lay.ordered + mm * key_bytes(o.dtype);
+    lay.mlp = (c.used + kAlign - 1) / kAlign * kAlign;
+    c.used = lay.mlp + sizeof(MlpState);
+    lay.part = (c.used + kAlign - 1) / kAlign * kAlign;
+    c.used = lay.part + ceil_div(mm, kMlpBatch) * (kMlpW + 1) * sizeof(float);
+  }
+  lay.total = c.used;
   if (sh_out) *sh_out = sh;
-  return used + std::max<uint64_t>(m, 1) * key_bytes(o.dtype);
+  if (lay_out) *lay_out = lay;
+  return lay.total;
 }
 
 template <typename K>
-int run_fit(uint64_t m, uint32_t P, const Options& o, const K* samples, K* splitters_out, cudaStream_t st) {
+int run_fit(uint64_t m, uint32_t P, const Options& o, const K* samples, K* splitters_out, float* model_out,
+            cudaStream_t st) {
   Shape sh;
-  size_t sorted_at = 0;
-  fit_workspace(m, o, &sh, &sorted_at);
+  FitLayout lay;
+  fit_workspace(m, o, &sh, &lay);
   Options inner = o;
+  inner.splitter_mode = PGS_SPLITTERS_SAMPLED;
   inner.bucket_bounds = nullptr;
   inner.cuts = nullptr;
   inner.splitters = nullptr;
   inner.stats = nullptr;
-  K* sorted = reinterpret_cast<K*>(static_cast<char*>(o.workspace) + sorted_at);
+  char* ws = static_cast<char*>(o.workspace);
+  K* sorted = reinterpret_cast<K*>(ws + lay.sorted);
   PGS_TRY((run_sort<K, false>(sh, inner, samples, nullptr, sorted, nullptr, st)));
   Ctx c;
   c.st = st;
   c.timer = o.timer;
-  return launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)P * sizeof(K), [&] {
-    // The inner sort already returned the caller's bit patterns: no transform here.
+  // The inner sort already returned the caller's bit patterns: no transform here.
+  PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)P * sizeof(K), [&] {
     k_pick_splitters_flat<K><<<grid_for(P, 256), 256, 0, st>>>(sorted, m, P, splitters_out, 0);
-  });
+  }));
+  if (o.splitter_mode != PGS_SPLITTERS_LEARNED || !model_out) return PGS_OK;
+  // K10 on the sorted sample, in order form.
+  K* ordered = reinterpret_cast<K*>(ws + lay.ordered);
+  MlpState* mlp = reinterpret_cast<MlpState*>(ws + lay.mlp);
+  float* part = reinterpret_cast<float*>(ws + lay.part);
+  PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 3, 2 * m * sizeof(K), [&] {
+    k_to_order<K><<<grid_for(m, 256), 256, 0, st>>>(sorted, ordered, m, o.dtype == PGS_F32);
+  }));
+  PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 16 * kMlpW, [&] { k_mlp_init<K><<<1, 256, 0, st>>>(ordered, m, mlp); }));
+  const uint32_t nparts = (uint32_t)ceil_div(m, kMlpBatch);
+  for (uint32_t step = 1; step <= (uint32_t)kMlpSteps; ++step) {
+    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, m * sizeof(K), [&] {
+      k_mlp_grad<K><<<nparts, kMlpBatch, sizeof(MlpGradSmem), st>>>(ordered, m, mlp, part);
+    }));
+    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 4ull * nparts * (kMlpW + 1), [&] {
+      k_mlp_adam<<<1, 1024, 0, st>>>(part, nparts, mlp, step, m);
+    }));
+  }
+  return launch(c, PGS_KERNEL_SPLITTERS, 3, 16 * kMlpW, [&] { k_mlp_finalize<<<1, 256, 0, st>>>(mlp, model_out); });
 }
 
 }  // namespace pgs

@@ -855,7 +855,8 @@ struct DevStats {                     // layout of pgs_stats
 // the smallest, and the largest ratio to its instance's mean n_i / P_i.
 static __global__ void __launch_bounds__(256)
 k_stats(Geo g, const uint64_t* __restrict__ e, uint64_t n_total, uint32_t s, uint32_t mode, uint32_t passes,
-        uint32_t launches, uint32_t* err_word, DevStats* st, uint64_t* user_bounds, float* max_ratio_out) {
+        uint32_t launches, const uint32_t* err_word, const uint32_t* fallback_word, DevStats* st,
+        uint64_t* user_bounds, float* max_ratio_out) {
   __shared__ uint64_t smax[256], smin[256];
   __shared__ float sratio[256];
   uint64_t mx = 0, mn = ~0ull;
@@ -892,7 +893,7 @@ k_stats(Geo g, const uint64_t* __restrict__ e, uint64_t n_total, uint32_t s, uin
       st->max_bucket = smax[0];
       st->min_bucket = g.R ? smin[0] : 0;
       st->splitter_mode = mode;
-      st->fallback = 0;
+      st->fallback = fallback_word ? *fallback_word : 0;
       st->error = err_word ? *err_word : 0;
       st->passes = passes;
       st->launches = launches;

@@ -1,0 +1,407 @@
+// Learned-CDF splitters: a monotone 1 -> 32 -> 32 -> 1 ReLU model of the key
+// CDF, trained in FP32 on the method's own sorted sample (K10), predicts every
+// key's bucket in one pass over the sorted runs (K11), whose per-run histogram
+// gives the cut matrix.  The sampled splitters with the investigator stay the
+// judge: if the learned buckets are more unbalanced than 1 + eps, or a given
+// model is not monotone, the sampled cuts are kept.
+//
+// Model layout (PGS_MLP_WORDS 4-byte words): w1[32], b1[32], W2[32][32]
+// (row k, column j; only entries with k and j in the same half are used),
+// b2[32], w3[32], b3, then kmin (low, high 32-bit words), scale (float) and a
+// validity flag.  Units 0..15 take +x and enter the output with weight >= 0;
+// units 16..31 take -x (w1 <= 0) and enter with weight <= 0; W2 >= 0.  With
+// these signs every fp32 operation of the evaluation below is monotone, so
+// the bucket id is non-decreasing in the key.
+#pragma once
+
+#include <cstdint>
+
+#include "pgs_kernels.cuh"
+
+namespace pgs {
+
+constexpr int kMlpH = 32;
+constexpr int kMlpHalf = 16;
+constexpr int kMlpW = 1153;                 // weights
+constexpr int kMlpWords = kMlpW + 4;        // + kmin lo, kmin hi, scale, flag
+constexpr int kMlpOffW1 = 0, kMlpOffB1 = 32, kMlpOffW2 = 64, kMlpOffB2 = 1088, kMlpOffW3 = 1120, kMlpOffB3 = 1152;
+constexpr int kMlpSteps = 300;
+constexpr float kMlpLr = 0.01f;
+constexpr float kMlpOffDiag = -6.0f;
+constexpr int kMlpBatch = 256;              // training samples per CTA
+
+__device__ __forceinline__ bool same_half(int k, int j) { return (k < kMlpHalf) == (j < kMlpHalf); }
+
+// Key -> model input: x = f32(f64(max(k, kmin) - kmin)) * scale.
+template <typename K>
+__device__ __forceinline__ float mlp_input(K key, uint64_t kmin, float scale) {
+  const uint64_t k = (uint64_t)key;
+  const uint64_t d = k > kmin ? k - kmin : 0;
+  return __fmul_rn(__double2float_rn(__ull2double_rn(d)), scale);
+}
+
+// Bucket id min(P-1, floor(P clamp(y, 0, 1))), y evaluated in fp32 in a fixed
+// order with every product and sum rounded separately (no fused multiply-add):
+// h1_j = max(w1_j x + b1_j, 0); acc = b2_k; acc += W2_kj h1_j for j of k's half
+// in increasing order; h2_k = max(acc, 0); y = b3; y += w3_k h2_k, k = 0..31.
+__device__ __forceinline__ uint32_t mlp_bucket(const float* __restrict__ w, float x, uint32_t P) {
+  float h1[kMlpH];
+#pragma unroll
+  for (int j = 0; j < kMlpH; ++j) {
+    const float z = __fadd_rn(__fmul_rn(w[kMlpOffW1 + j], x), w[kMlpOffB1 + j]);
+    h1[j] = z > 0.0f ? z : 0.0f;
+  }
+  float y = w[kMlpOffB3];
+#pragma unroll
+  for (int k = 0; k < kMlpH; ++k) {
+    float acc = w[kMlpOffB2 + k];
+    const int lo = k < kMlpHalf ? 0 : kMlpHalf;
+#pragma unroll
+    for (int j = 0; j < kMlpHalf; ++j) acc = __fadd_rn(acc, __fmul_rn(w[kMlpOffW2 + k * kMlpH + lo + j], h1[lo + j]));
+    const float h2 = acc > 0.0f ? acc : 0.0f;
+    y = __fadd_rn(y, __fmul_rn(w[kMlpOffW3 + k], h2));
+  }
+  const float c = fminf(fmaxf(y, 0.0f), 1.0f);
+  const float t = floorf(__fmul_rn((float)P, c));
+  const uint32_t b = (uint32_t)t;
+  return b < P ? b : P - 1;
+}
+
+// ---------------------------------------------------------------------------
+// K10: training.  Raw parameters (v1, b1, V2, b2, v3, b3) map to the weights
+// w1 = +-exp(v1), W2 = exp(V2) inside a half, w3 = +-exp(v3); full-batch Adam
+// on the mean squared error against the empirical CDF (i + 1/2) / S.
+// ---------------------------------------------------------------------------
+
+struct MlpState {
+  float raw[kMlpW];
+  float m[kMlpW];
+  float v[kMlpW];
+  uint64_t kmin;
+  float scale;
+  float loss;
+};
+
+__device__ __forceinline__ float mlp_sign(int j) { return j < kMlpHalf ? 1.0f : -1.0f; }
+
+// One CTA: normalisation from the sorted sample, knots of layer 1 at the
+// samples of sorted index floor((2j + 1) S / 32), layer 2 close to the identity.
+template <typename K>
+__global__ void k_mlp_init(const K* __restrict__ sorted, uint64_t S, MlpState* st) {
+  const uint64_t kmin = (uint64_t)sorted[0];
+  const uint64_t span = (uint64_t)sorted[S - 1] - kmin;
+  const float scale = span == 0 ? 0.0f : __fdiv_rn(1.0f, __double2float_rn(__ull2double_rn(span)));
+  for (int p = threadIdx.x; p < kMlpW; p += blockDim.x) {
+    float r = 0.0f;
+    if (p >= kMlpOffB1 && p < kMlpOffW2) {
+      const int j = p - kMlpOffB1;
+      const int jj = j % kMlpHalf;
+      const float q = mlp_input<K>(sorted[((2ull * jj + 1) * S) / (2 * kMlpHalf)], kmin, scale);
+      r = j < kMlpHalf ? -q : q;
+    } else if (p >= kMlpOffW2 && p < kMlpOffB2) {
+      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
+      r = same_half(k, j) ? (k == j ? 0.0f : kMlpOffDiag) : 0.0f;
+    } else if (p >= kMlpOffW3 && p < kMlpOffB3) {
+      r = -3.4657359f;                                    // log(1/32)
+    } else if (p == kMlpOffB3) {
+      r = 0.5f;
+    }
+    st->raw[p] = r;
+    st->m[p] = 0.0f;
+    st->v[p] = 0.0f;
+  }
+  if (threadIdx.x == 0) {
+    st->kmin = kmin;
+    st->scale = scale;
+    st->loss = 0.0f;
+  }
+}
+
+struct MlpGradSmem {
+  float w[kMlpW];                 // effective weights
+  float h1[kMlpBatch][kMlpH];
+  float dz1[kMlpBatch][kMlpH];
+  float h2[kMlpBatch][kMlpH];
+  float dz2[kMlpBatch][kMlpH];
+  float x[kMlpBatch];
+  float dy[kMlpBatch];
+  float r2[kMlpBatch];
+};
+
+// Partial gradient of one CTA's kMlpBatch samples (deterministic order):
+// part[blockIdx.x][p] for the kMlpW raw parameters, part[..][kMlpW] the sum of
+// squared residuals.
+template <typename K>
+__global__ void __launch_bounds__(kMlpBatch)
+k_mlp_grad(const K* __restrict__ sorted, uint64_t S, const MlpState* __restrict__ st, float* part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MlpGradSmem& sm = *reinterpret_cast<MlpGradSmem*>(smem_raw);
+  const int tid = threadIdx.x;
+  for (int p = tid; p < kMlpW; p += blockDim.x) {
+    const float r = st->raw[p];
+    float w = r;
+    if (p < kMlpOffB1) w = mlp_sign(p) * expf(r);
+    else if (p >= kMlpOffW2 && p < kMlpOffB2) {
+      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
+      w = same_half(k, j) ? expf(r) : 0.0f;
+    } else if (p >= kMlpOffW3 && p < kMlpOffB3) w = mlp_sign(p - kMlpOffW3) * expf(r);
+    sm.w[p] = w;
+  }
+  __syncthreads();
+  const uint64_t i = blockIdx.x * (uint64_t)kMlpBatch + tid;
+  const bool live = i < S;
+  const float x = live ? mlp_input<K>(sorted[i], st->kmin, st->scale) : 0.0f;
+  const float t = live ? ((float)i + 0.5f) / (float)S : 0.0f;
+  float z1[kMlpH], h1[kMlpH], z2[kMlpH], h2[kMlpH];
+#pragma unroll
+  for (int j = 0; j < kMlpH; ++j) {
+    z1[j] = sm.w[kMlpOffW1 + j] * x + sm.w[kMlpOffB1 + j];
+    h1[j] = fmaxf(z1[j], 0.0f);
+  }
+  float y = sm.w[kMlpOffB3];
+#pragma unroll
+  for (int k = 0; k < kMlpH; ++k) {
+    float acc = sm.w[kMlpOffB2 + k];
+    const int lo = k < kMlpHalf ? 0 : kMlpHalf;
+#pragma unroll
+    for (int j = 0; j < kMlpHalf; ++j) acc += sm.w[kMlpOffW2 + k * kMlpH + lo + j] * h1[lo + j];
+    z2[k] = acc;
+    h2[k] = fmaxf(acc, 0.0f);
+    y += sm.w[kMlpOffW3 + k] * h2[k];
+  }
+  const float r = live ? y - t : 0.0f;
+  const float dy = 2.0f * r / (float)S;
+  float dz2[kMlpH];
+#pragma unroll
+  for (int k = 0; k < kMlpH; ++k) dz2[k] = z2[k] > 0.0f ? dy * sm.w[kMlpOffW3 + k] : 0.0f;
+#pragma unroll
+  for (int j = 0; j < kMlpH; ++j) {
+    const int lo = j < kMlpHalf ? 0 : kMlpHalf;
+    float acc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMlpHalf; ++k) acc += dz2[lo + k] * sm.w[kMlpOffW2 + (lo + k) * kMlpH + j];
+    sm.dz1[tid][j] = z1[j] > 0.0f ? acc : 0.0f;
+    sm.h1[tid][j] = h1[j];
+    sm.h2[tid][j] = h2[j];
+    sm.dz2[tid][j] = dz2[j];
+  }
+  sm.x[tid] = x;
+  sm.dy[tid] = dy;
+  sm.r2[tid] = r * r;
+  __syncthreads();
+  float* out = part + (uint64_t)blockIdx.x * (kMlpW + 1);
+  for (int p = tid; p <= kMlpW; p += blockDim.x) {
+    float g = 0.0f;
+    if (p < kMlpOffB1) {
+      for (int s = 0; s < kMlpBatch; ++s) g += sm.dz1[s][p] * sm.x[s];
+      g *= sm.w[p];
+    } else if (p < kMlpOffW2) {
+      for (int s = 0; s < kMlpBatch; ++s) g += sm.dz1[s][p - kMlpOffB1];
+    } else if (p < kMlpOffB2) {
+      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
+      if (same_half(k, j)) {
+        for (int s = 0; s < kMlpBatch; ++s) g += sm.dz2[s][k] * sm.h1[s][j];
+        g *= sm.w[p];
+      }
+    } else if (p < kMlpOffW3) {
+      for (int s = 0; s < kMlpBatch; ++s) g += sm.dz2[s][p - kMlpOffB2];
+    } else if (p < kMlpOffB3) {
+      for (int s = 0; s < kMlpBatch; ++s) g += sm.dy[s] * sm.h2[s][p - kMlpOffW3];
+      g *= sm.w[p];
+    } else if (p == kMlpOffB3) {
+      for (int s = 0; s < kMlpBatch; ++s) g += sm.dy[s];
+    } else {
+      for (int s = 0; s < kMlpBatch; ++s) g += sm.r2[s];
+    }
+    out[p] = g;
+  }
+}
+
+// One CTA: sum the partial gradients in CTA order, then one Adam step
+// (beta1 0.9, beta2 0.999, eps 1e-8).  Entries of W2 across halves stay 0.
+static __global__ void __launch_bounds__(1024)
+k_mlp_adam(const float* __restrict__ part, uint32_t nparts, MlpState* st, uint32_t step, uint64_t S) {
+  const float c1 = 1.0f - powf(0.9f, (float)step), c2 = 1.0f - powf(0.999f, (float)step);
+  for (int p = threadIdx.x; p <= kMlpW; p += blockDim.x) {
+    float g = 0.0f;
+    for (uint32_t c = 0; c < nparts; ++c) g += part[(uint64_t)c * (kMlpW + 1) + p];
+    if (p == kMlpW) {
+      st->loss = g / (float)S;
+      continue;
+    }
+    if (p >= kMlpOffW2 && p < kMlpOffB2) {
+      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
+      if (!same_half(k, j)) continue;
+    }
+    const float m = 0.9f * st->m[p] + 0.1f * g;
+    const float v = 0.999f * st->v[p] + 0.001f * g * g;
+    st->m[p] = m;
+    st->v[p] = v;
+    st->raw[p] -= kMlpLr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+  }
+}
+
+// Effective weights and normalisation of the trained model.
+static __global__ void k_mlp_finalize(const MlpState* __restrict__ st, float* model) {
+  for (int p = threadIdx.x; p < kMlpW; p += blockDim.x) {
+    const float r = st->raw[p];
+    float w = r;
+    if (p < kMlpOffB1) w = mlp_sign(p) * expf(r);
+    else if (p >= kMlpOffW2 && p < kMlpOffB2) {
+      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
+      w = same_half(k, j) ? expf(r) : 0.0f;
+    } else if (p >= kMlpOffW3 && p < kMlpOffB3) w = mlp_sign(p - kMlpOffW3) * expf(r);
+    model[p] = w;
+  }
+  if (threadIdx.x == 0) {
+    uint32_t* u = reinterpret_cast<uint32_t*>(model);
+    u[kMlpW] = (uint32_t)st->kmin;
+    u[kMlpW + 1] = (uint32_t)(st->kmin >> 32);
+    model[kMlpW + 2] = st->scale;
+    u[kMlpW + 3] = 1u;
+  }
+}
+
+// A caller's model: copy it and mark it valid only if its signs make it monotone.
+static __global__ void k_mlp_validate(const float* __restrict__ given, float* model) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int p = threadIdx.x; p < kMlpWords; p += blockDim.x) {
+    const float w = given[p];
+    model[p] = w;
+    bool ok = true;
+    if (p < kMlpOffB1) ok = p < kMlpHalf ? w >= 0.0f : w <= 0.0f;
+    else if (p >= kMlpOffW2 && p < kMlpOffB2) {
+      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
+      ok = !same_half(k, j) || w >= 0.0f;
+    } else if (p >= kMlpOffW3 && p < kMlpOffB3) ok = (p - kMlpOffW3) < kMlpHalf ? w >= 0.0f : w <= 0.0f;
+    if (p < kMlpW && !(w == w)) ok = false;                 // NaN
+    if (!ok) atomicOr(&bad, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) reinterpret_cast<uint32_t*>(model)[kMlpW + 3] = bad ? 0u : 1u;
+}
+
+// ---------------------------------------------------------------------------
+// K11: bucket ids of every key of the sorted runs, in one pass, as a per-run
+// histogram.  A warp covers 32 x 32 consecutive keys of one run: lane l first
+// evaluates the first and the last key of its sub-block of 32; because the
+// bucket id is monotone and the run sorted, equal ids at both ends give the
+// whole sub-block that id.  Sub-blocks with a bucket boundary inside are then
+// evaluated key by key by the whole warp.  Counts are accumulated with
+// warp-aggregated atomics: __match_any_sync groups the lanes holding the same
+// bucket and one lane adds the group's count.
+// ---------------------------------------------------------------------------
+
+constexpr int kHistSub = 32;                    // keys per lane sub-block
+constexpr int kHistWarpKeys = 32 * kHistSub;    // keys per warp segment
+constexpr int kHistNT = 256;
+
+__device__ __forceinline__ void hist_add(uint64_t* row, uint32_t bucket, uint32_t count, bool active) {
+  const uint32_t act = __ballot_sync(0xFFFFFFFFu, active);
+  if (!active) return;
+  const uint32_t peers = __match_any_sync(act, bucket);       // lanes holding the same bucket
+  const uint32_t sum = __reduce_add_sync(peers, count);
+  const int leader = __ffs(peers) - 1;
+  if ((int)(threadIdx.x & 31) == leader)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&row[bucket]), (unsigned long long)sum);
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kHistNT)
+k_learned_hist(const K* __restrict__ runs, const uint64_t* __restrict__ run_off, uint32_t P,
+               uint64_t segs_per_run, const float* __restrict__ model, uint64_t* hist) {
+  __shared__ float w[kMlpW];
+  for (int p = threadIdx.x; p < kMlpW; p += blockDim.x) w[p] = model[p];
+  __syncthreads();
+  const uint32_t* u = reinterpret_cast<const uint32_t*>(model);
+  const uint64_t kmin = (uint64_t)u[kMlpW] | ((uint64_t)u[kMlpW + 1] << 32);
+  const float scale = model[kMlpW + 2];
+  const int lane = threadIdx.x & 31;
+  const uint64_t seg = blockIdx.x * (uint64_t)(kHistNT / 32) + (threadIdx.x >> 5);
+  const uint64_t r = seg / segs_per_run, sidx = seg % segs_per_run;
+  if (r >= P) return;
+  const uint64_t rs = run_off[r], re = run_off[r + 1];
+  const uint64_t s0 = rs + sidx * kHistWarpKeys;
+  if (s0 >= re) return;                                      // warp-uniform
+  uint64_t* row = hist + r * P;
+  const uint64_t a = s0 + (uint64_t)lane * kHistSub;
+  const uint64_t b = umin(a + kHistSub, re);                 // [a, b): this lane's sub-block
+  const bool has = a < re;
+  uint32_t bf = 0, bl = 0;
+  if (has) {
+    bf = mlp_bucket(w, mlp_input<K>(runs[a], kmin, scale), P);
+    bl = mlp_bucket(w, mlp_input<K>(runs[b - 1], kmin, scale), P);
+  }
+  const bool whole = has && bf == bl;
+  hist_add(row, bf, (uint32_t)(b - a), whole);
+  uint32_t mixed = __ballot_sync(0xFFFFFFFFu, has && !whole);
+  while (mixed) {
+    const int l = __ffs(mixed) - 1;
+    mixed &= mixed - 1;
+    const uint64_t la = s0 + (uint64_t)l * kHistSub;
+    const uint64_t lb = umin(la + kHistSub, re);
+    const uint64_t p = la + lane;
+    const bool in = p < lb;
+    const uint32_t id = in ? mlp_bucket(w, mlp_input<K>(runs[p], kmin, scale), P) : 0;
+    hist_add(row, id, 1, in);
+  }
+}
+
+// cut[r][b] = sum_{b' < b} hist[r][b'] (from the run-major exclusive scan of
+// the histogram), the learned bucket vector e_b = sum_r cut[r][b], and the
+// decision: keep the learned cuts only for a valid model whose largest bucket
+// is at most (1 + eps) n / P.
+static __global__ void k_learned_cuts(const uint64_t* __restrict__ scanned, uint32_t P, uint64_t* cutL) {
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= (uint64_t)P * (P + 1)) return;
+  const uint64_t r = q / (P + 1), b = q % (P + 1);
+  cutL[q] = scanned[r * P + b] - scanned[r * P];
+}
+
+static __global__ void k_learned_colsum(const uint64_t* __restrict__ cutL, uint32_t P, uint64_t* eL) {
+  const uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (b > P) return;
+  uint64_t s = 0;
+  for (uint32_t r = 0; r < P; ++r) s += cutL[(uint64_t)r * (P + 1) + b];
+  eL[b] = s;
+}
+
+static __global__ void __launch_bounds__(256)
+k_learned_judge(const uint64_t* __restrict__ eL, uint32_t P, uint64_t n, float eps, const float* __restrict__ model,
+                uint32_t* fallback, float* ratio_out) {
+  __shared__ uint64_t smax[256];
+  uint64_t mx = 0;
+  for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) mx = umax(mx, eL[b + 1] - eL[b]);
+  smax[threadIdx.x] = mx;
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if (threadIdx.x < d) smax[threadIdx.x] = umax(smax[threadIdx.x], smax[threadIdx.x + d]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const bool valid = reinterpret_cast<const uint32_t*>(model)[kMlpW + 3] == 1u;
+    const double ratio = n ? (double)smax[0] * P / (double)n : 1.0;
+    *ratio_out = (float)ratio;
+    *fallback = (!valid || ratio > 1.0 + (double)eps) ? 1u : 0u;
+  }
+}
+
+// Order form of sorted user keys (float32 bits to their totalOrder image).
+template <typename K>
+__global__ void k_to_order(const K* __restrict__ in, K* out, uint64_t m, int f32) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = to_order<K>(in[i], f32);
+}
+
+// Keep the learned cuts and bucket vector unless the judge fell back.
+static __global__ void k_learned_select(const uint64_t* __restrict__ cutL, const uint64_t* __restrict__ eL, uint32_t P,
+                                        const uint32_t* __restrict__ fallback, uint64_t* cut, uint64_t* e) {
+  if (*fallback) return;
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q < (uint64_t)P * (P + 1)) cut[q] = cutL[q];
+  if (q <= P) e[q] = eL[q];
+}
+
+}  // namespace pgs

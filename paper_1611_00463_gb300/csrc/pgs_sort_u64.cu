@@ -11,8 +11,9 @@ int sort_u64(const Shape& p, const Options& o, const void* kin, const uint32_t* 
   return run_sort<uint64_t, false>(p, o, ki, nullptr, ko, nullptr, st);
 }
 
-int fit_u64(uint64_t m, uint32_t P, const Options& o, const void* samples, void* out, cudaStream_t st) {
-  return run_fit<uint64_t>(m, P, o, static_cast<const uint64_t*>(samples), static_cast<uint64_t*>(out), st);
+int fit_u64(uint64_t m, uint32_t P, const Options& o, const void* samples, void* out, float* model_out,
+            cudaStream_t st) {
+  return run_fit<uint64_t>(m, P, o, static_cast<const uint64_t*>(samples), static_cast<uint64_t*>(out), model_out, st);
 }
 
 int batch_attrs_u64(bool vals) {

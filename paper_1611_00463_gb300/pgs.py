@@ -23,6 +23,7 @@ SPLITTERS = {"sampled": 0, "learned": 1}
 DTYPES = {"u32": PGS_U32, "u64": PGS_U64, "f32": PGS_F32}
 KEY_TORCH = {"u32": torch.int32, "u64": torch.int64, "f32": torch.int32}
 MLP_FLOATS = 1 * 32 + 32 + 32 * 32 + 32 + 32 * 1 + 1
+MLP_WORDS = MLP_FLOATS + 4
 
 
 class pgs_config(ctypes.Structure):
@@ -43,6 +44,8 @@ class pgs_config(ctypes.Structure):
         ("stats", ctypes.c_void_p),
         ("spin_limit", ctypes.c_uint64),
         ("timer", ctypes.c_void_p),
+        ("model", ctypes.c_void_p),
+        ("model_out", ctypes.c_void_p),
     ]
 
 
@@ -208,7 +211,8 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
                 investigator: str = "rank", exchange: str = "auto", splitters: str = "sampled",
                 workspace: torch.Tensor | None = None, bucket_bounds: torch.Tensor | None = None,
                 cuts: torch.Tensor | None = None, splitters_out: torch.Tensor | None = None,
-                stats: torch.Tensor | None = None, timer: Timer | None = None) -> pgs_config:
+                stats: torch.Tensor | None = None, timer: Timer | None = None,
+                model: torch.Tensor | None = None, model_out: torch.Tensor | None = None) -> pgs_config:
     c = pgs_config()
     c.dtype = DTYPES[dtype]
     c.samples_per_run = samples_per_run
@@ -225,6 +229,8 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
     c.splitters = _ptr(splitters_out)
     c.stats = _ptr(stats)
     c.timer = timer.handle if timer is not None else None
+    c.model = _ptr(model)
+    c.model_out = _ptr(model_out)
     return c
 
 

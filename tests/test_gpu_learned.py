@@ -1,0 +1,176 @@
+"""Learned-CDF splitters on the GPU against the oracle.
+
+With a given model the learned cut matrix must equal the oracle's, bit for bit
+(same fp32 evaluation order), and the judge's choice between learned and
+sampled cuts must be the one the oracle's integers dictate.  Training on the
+GPU is compared by its properties (monotone weights, loss close to the fp64
+reference trainer).  The sorted output is the stable sort in every case.
+"""
+import numpy as np
+import pytest
+
+from oracle import pgs_oracle as O
+from paper_1611_00463_gb300 import inputs
+from tests.pins import check_stable_sorted
+
+pytestmark = pytest.mark.gpu
+
+
+def sorted_sample(keys, P, dtype):
+    o = O.ord_bits(keys, dtype)
+    n = len(keys)
+    s = O.paper_samples_per_run(P, O.KEY_BYTES[dtype])
+    b = O.run_bounds(n, P)
+    parts = []
+    for r in range(P):
+        run = np.sort(o[b[r]:b[r + 1]])
+        parts.append(run[O.regular_sample_positions(len(run), s)])
+    return np.sort(np.concatenate(parts))
+
+
+def model_words(w, kmin, scale, valid=1):
+    extra = np.array([kmin & 0xFFFFFFFF, kmin >> 32, np.float32(scale).view(np.uint32), valid], dtype=np.uint32)
+    return np.concatenate([np.asarray(w, np.float32).view(np.uint32), extra])
+
+
+def run_learned(keys, P, dtype, words=None, eps=0.05):
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    n = len(keys)
+    vals = inputs.index_payload(n)
+    dev = torch.device("cuda")
+    kin = pgs.as_device_keys(keys, dtype, dev)
+    vin = torch.from_numpy(vals.view(np.int32)).to(dev)
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    model = None if words is None else torch.from_numpy(words.view(np.float32)).to(dev)
+    model_out = torch.zeros(pgs.MLP_WORDS, dtype=torch.float32, device=dev)
+    cfg0 = pgs.make_config(dtype=dtype, splitters="learned", eps=eps)
+    ws = pgs.workspace(n, P, cfg0, dev)
+    bounds = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    cuts = torch.zeros(P * (P + 1), dtype=torch.int64, device=dev)
+    st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
+    cfg = pgs.make_config(dtype=dtype, splitters="learned", eps=eps, workspace=ws, bucket_bounds=bounds,
+                          cuts=cuts, stats=st, model=model, model_out=model_out)
+    pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg)
+    torch.cuda.synchronize()
+    got_k = pgs.to_numpy_keys(kout, dtype)
+    got_v = vout.cpu().numpy().view(np.uint32)
+    check_stable_sorted(keys, vals, got_k, got_v, dtype)
+    return {"e": bounds.cpu().numpy(), "cut": cuts.cpu().numpy().reshape(P, P + 1),
+            "stats": pgs.pgs_get_stats(st), "model": model_out.cpu().numpy()}
+
+
+def expect_decision(keys, P, dtype, w, kmin, scale, got, eps=0.05, valid=True):
+    learned = O.learned_buckets(keys, P, dtype, w, kmin, scale)
+    sampled = O.buckets(keys, P, dtype)
+    ratio = learned["stats"]["max_over_mean"]
+    keep = valid and ratio <= 1.0 + eps
+    want = learned if keep else sampled
+    assert got["stats"]["fallback"] == (0 if keep else 1)
+    assert np.array_equal(got["e"], want["e"])
+    assert np.array_equal(got["cut"], want["cut"])
+    return keep
+
+
+def identity_words(kmin, scale):
+    eff = {"w1": np.zeros(32), "b1": np.zeros(32), "W2": np.zeros((32, 32)), "b2": np.zeros(32),
+           "w3": np.zeros(32), "b3": np.array(0.0)}
+    eff["w1"][0] = eff["W2"][0, 0] = eff["w3"][0] = 1.0
+    return O.mlp_pack(eff)
+
+
+def test_given_identity_model_on_uniform_keys_is_kept():
+    n, P = 200_000, 16
+    keys = inputs.uniform_u32(n, 21)
+    kmin, scale = O.mlp_norm(sorted_sample(keys, P, "u32"))
+    w = identity_words(kmin, scale)
+    got = run_learned(keys, P, "u32", model_words(w, kmin, scale))
+    assert expect_decision(keys, P, "u32", w, kmin, scale, got)
+    assert got["stats"]["splitter_mode"] == 1
+
+
+@pytest.mark.parametrize("dtype,gen,P", [("u32", inputs.exponential_u32, 16), ("u64", inputs.normal_lognormal_u64, 8),
+                                         ("f32", inputs.zipf_dup_f32, 12)])
+def test_given_oracle_trained_model(dtype, gen, P):
+    n = 120_003
+    keys = gen(n, 5)
+    samp = sorted_sample(keys, P, dtype)
+    kmin, scale = O.mlp_norm(samp)
+    x = O.mlp_inputs(samp, kmin, scale).astype(np.float64)
+    raw, _ = O.mlp_train(x, steps=60)
+    w = O.mlp_pack(O.mlp_effective(raw))
+    got = run_learned(keys, P, dtype, model_words(w, kmin, scale), eps=1.0)
+    expect_decision(keys, P, dtype, w, kmin, scale, got, eps=1.0)
+
+
+def test_random_monotone_model_and_judge():
+    n, P = 90_000, 24
+    keys = inputs.exponential_u32(n, 8)
+    g = np.random.default_rng(3)
+    raw = {"v1": g.normal(0, 0.3, 32), "b1": g.normal(0, 0.3, 32), "V2": g.normal(-2, 0.3, (32, 32)),
+           "b2": g.normal(0, 0.1, 32), "v3": g.normal(-1, 0.3, 32), "b3": np.array(0.5)}
+    raw["V2"] = np.where(O.mlp_block_mask(), raw["V2"], 0.0)
+    w = O.mlp_pack(O.mlp_effective(raw))
+    kmin, scale = O.mlp_norm(sorted_sample(keys, P, "u32"))
+    for eps in [0.05, 1.0]:
+        got = run_learned(keys, P, "u32", model_words(w, kmin, scale), eps=eps)
+        expect_decision(keys, P, "u32", w, kmin, scale, got, eps=eps)
+
+
+def test_non_monotone_model_is_rejected():
+    n, P = 50_000, 8
+    keys = inputs.uniform_u32(n, 9)
+    kmin, scale = O.mlp_norm(sorted_sample(keys, P, "u32"))
+    w = identity_words(kmin, scale)
+    w[20] = 0.5                                   # w1 of a unit that must not rise with x
+    got = run_learned(keys, P, "u32", model_words(w, kmin, scale))
+    expect_decision(keys, P, "u32", w, kmin, scale, got, valid=False)
+    assert reinterpret_words(got["model"])[-1] == 0
+
+
+def reinterpret_words(m):
+    return np.asarray(m, np.float32).view(np.uint32)
+
+
+@pytest.mark.parametrize("dtype,gen,P", [("u32", inputs.exponential_u32, 64), ("u64", inputs.normal_lognormal_u64, 16)])
+def test_gpu_training(dtype, gen, P):
+    n = 1 << 20
+    keys = gen(n, 13)
+    got = run_learned(keys, P, dtype)
+    words = reinterpret_words(got["model"])
+    w = got["model"][:O.MLP_FLOATS]
+    assert words[-1] == 1 and O.mlp_monotone(w)
+    samp = sorted_sample(keys, P, dtype)
+    kmin, scale = O.mlp_norm(samp)
+    assert int(words[O.MLP_FLOATS]) | (int(words[O.MLP_FLOATS + 1]) << 32) == kmin
+    assert np.float32(got["model"][O.MLP_FLOATS + 2]) == scale
+    x = O.mlp_inputs(samp, kmin, scale).astype(np.float64)
+    t = (np.arange(len(x)) + 0.5) / len(x)
+    y, _ = O.mlp_forward64(O.mlp_unpack(w), x)
+    gpu_loss = float(np.mean((y - t) ** 2))
+    _, ref_loss = O.mlp_train(x)
+    assert gpu_loss <= 1.5 * ref_loss + 1e-6, (gpu_loss, ref_loss)
+    expect_decision(keys, P, dtype, w, kmin, scale, got)
+
+
+def test_fit_splitters_learned_mode():
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    m, P = 65_536, 64
+    samples = inputs.exponential_u32(m, 17)
+    dev_s = pgs.as_device_keys(samples, "u32")
+    cfg0 = pgs.make_config(dtype="u32", splitters="learned")
+    ws = torch.empty(pgs.pgs_fit_workspace_bytes(m, P, cfg0), dtype=torch.uint8, device="cuda")
+    cfg = pgs.make_config(dtype="u32", splitters="learned", workspace=ws)
+    out = torch.zeros(P - 1, dtype=torch.int32, device="cuda")
+    model = torch.zeros(pgs.MLP_WORDS, dtype=torch.float32, device="cuda")
+    pgs.pgs_fit_splitters(dev_s, P, cfg, out, model_out=model)
+    torch.cuda.synchronize()
+    assert np.array_equal(pgs.to_numpy_keys(out, "u32"), O.select_splitters(samples, P))
+    w = model.cpu().numpy()[:O.MLP_FLOATS]
+    assert O.mlp_monotone(w)
+    srt = np.sort(samples)
+    kmin, scale = O.mlp_norm(srt)
+    x = O.mlp_inputs(srt, kmin, scale).astype(np.float64)
+    y, _ = O.mlp_forward64(O.mlp_unpack(w), x)
+    assert float(np.mean((y - (np.arange(m) + 0.5) / m) ** 2)) < 1e-3
