@@ -38,7 +38,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pgs", choices=["pgs", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS) + ["batched"])
+    ap.add_argument("--splitters", default="sampled", choices=["sampled", "learned"])
+    ap.add_argument("--guaranteed", action="store_true", help="oversample so every bucket < (1+eps) n/P")
+    ap.add_argument("--instances", type=int, default=10000, help="batched workload: number of instances")
     ap.add_argument("--n", type=int, default=None, help="override the number of keys (smaller cases)")
     ap.add_argument("--P", type=int, default=None)
     ap.add_argument("--exchange", default="auto", choices=["auto", "scatter", "fused"])
@@ -175,6 +178,8 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == "batched":
+        return run_reference_batched(args)
     dtype, n, P, _, _ = workload_shape(args)
     sample_n = min(n, 1 << 23)
     value, dt, _ = time_oracle(args.workload, P, sample_n, args.steps, args.warmup)
@@ -192,6 +197,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_batched(args):
+    """The oracle on the first instances of the batched workload (bounded sample)."""
+    from oracle import pgs_oracle as O
+    sizes = inputs.batched_sizes(args.instances)
+    P = inputs.batched_partitions(sizes)
+    take, total = 0, 0
+    while take < len(sizes) and total + sizes[take] <= (1 << 23):
+        total += int(sizes[take])
+        take += 1
+    take = max(take, 1)
+    inst = [inputs.batched_instance_keys(i, int(sizes[i])) for i in range(take)]
+    n = sum(len(k) for k in inst)
+
+    def step():
+        for i, k in enumerate(inst):
+            O.stable_sort(k, np.arange(len(k), dtype=np.uint32), "u64")
+            O.buckets(k, int(P[i]), "u64")
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n / dt / 1e9
+    sample = f"first {take} instances of the batched workload ({n} keys): oracle stable sort + bucket vector, one thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched", "instances": args.instances},
+            "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def workload_shape(args):
     dtype, n0, P0, gen, seed = inputs.WORKLOADS[args.workload]
     n = args.n or n0
@@ -206,6 +245,8 @@ def config_block(args, dtype, n, P, stats):
         "n": n, "P": P, "key": dtype, "payload": "u32 index",
         "l2": "inputs larger than L2 (no flush between steps)",
         "exchange": args.exchange,
+        "splitters": args.splitters,
+        "guaranteed": bool(args.guaranteed),
     }
     if stats:
         c["passes"] = stats["passes"]
@@ -217,10 +258,114 @@ def config_block(args, dtype, n, P, stats):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_batched(args):
+    """The batched workload: ~10,000 uneven uint64 instances with uint32
+    payload in one CUDA-graph replay of the batched sort (tile shape chosen by
+    the tuner), against per-instance pgs_sort_copy launches."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1611_00463_gb300 import build as pbuild
+    from paper_1611_00463_gb300 import pgs
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        pbuild.build()
+    if world > 1:
+        dist.barrier()
+    pgs.load()
+    t_gen = time.time()
+    offsets, keys_np, P = inputs.batched(args.instances, seed=4 + 100 * rank)
+    t_gen = time.time() - t_gen
+    n = int(offsets[-1])
+    vals_np = np.arange(n, dtype=np.uint32)
+    kin = torch.from_numpy(keys_np.view(np.int64)).to(dev)
+    vin = torch.from_numpy(vals_np.view(np.int32)).to(dev)
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    bt = pgs.Batch(offsets, P, dtype="u64", with_vals=True, device=dev)
+    chosen, tune_ms = bt.tune(kout, vout)
+    st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
+    cfg = bt.config(stats=st)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bt.sort_copy(kin, vin, kout, vout, stream=s, cfg=cfg)
+    torch.cuda.synchronize(dev)
+    for _ in range(max(args.warmup, 0)):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    stats = pgs.pgs_get_stats(st)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cur = torch.cuda.current_stream(dev)
+    with ClockSampler(torch.cuda.current_device()) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(cur)
+        for _ in range(args.steps):
+            g.replay()
+        ev1.record(cur)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = n * world / (ms_step * 1e-3) / 1e9
+    # The same instances, one pgs_sort_copy call (its own launch sequence) each.
+    per = None
+    if rank == 0:
+        sizes = np.diff(offsets).astype(np.int64)
+        ws = pgs.workspace(int(sizes.max()), int(P.max()), pgs.make_config(dtype="u64"), dev)
+        cfgi = pgs.make_config(dtype="u64", workspace=ws)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for i in range(len(sizes)):
+            a, b = int(offsets[i]), int(offsets[i + 1])
+            pgs.pgs_sort_copy(kin[a:b], vin[a:b], kout[a:b], vout[a:b], int(P[i]), cfgi)
+        e1.record(cur)
+        torch.cuda.synchronize(dev)
+        pms = e0.elapsed_time(e1)
+        per = {"ms": pms, "value": n / (pms * 1e-3) / 1e9, "unit": "Gkeys/s",
+               "speedup_of_batched": pms / ms_step}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"batched: {args.instances} instances, {n} uint64 keys + uint32 payload, "
+                                   "lognormal sizes 1K..16M, per-instance distribution by seed, "
+                                   "P_i = clamp(2^floor(log2(n_i/2^16)), 1, 256); one CUDA-graph replay "
+                                   "of the batched sort per step, out of place",
+                       "n": n, "instances": args.instances, "P_sum": int(P.sum()),
+                       "tile_variant": chosen, "tune_ms": tune_ms, "generation_s": t_gen,
+                       "passes": stats["passes"], "l2": "inputs larger than L2 (no flush between steps)"},
+            "max_over_mean_bucket": stats["max_over_mean"],
+            "gpu_launches": stats["launches"] * args.steps,
+            "launches_per_step": stats["launches"],
+            "per_instance_launches": per,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
     import torch
     import torch.distributed as dist
@@ -246,13 +391,14 @@ def main():
     vin = torch.from_numpy(vals_np.view(np.int32)).to(dev)
     kout = torch.empty_like(kin)
     vout = torch.empty_like(vin)
-    cfg0 = pgs.make_config(dtype=dtype, exchange=args.exchange)
+    opts = dict(dtype=dtype, exchange=args.exchange, splitters=args.splitters, guaranteed=args.guaranteed)
+    cfg0 = pgs.make_config(**opts)
     ws = pgs.workspace(n, P, cfg0, dev)
     st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    timer = None if args.no_timer else pgs.Timer(capacity=256 * (args.steps + 1))
-    cfg_plain = pgs.make_config(dtype=dtype, exchange=args.exchange, workspace=ws, stats=st)
-    cfg_timed = pgs.make_config(dtype=dtype, exchange=args.exchange, workspace=ws, stats=st, timer=timer)
+    timer = None if args.no_timer else pgs.Timer(capacity=(1024 if args.splitters == "learned" else 256) * (args.steps + 1))
+    cfg_plain = pgs.make_config(workspace=ws, stats=st, **opts)
+    cfg_timed = pgs.make_config(workspace=ws, stats=st, timer=timer, **opts)
 
     for _ in range(max(args.warmup, 0)):
         pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_plain, stream)
@@ -315,14 +461,14 @@ def main():
         hk = torch.from_numpy(keys_np.view(np.int64 if dtype == "u64" else np.int32)).pin_memory()
         hv = torch.from_numpy(vals_np.view(np.int32)).pin_memory()
         for _ in range(1):
-            pgs.sort(hk, hv, P, dtype=dtype, exchange=args.exchange)
+            pgs.sort(hk, hv, P, **opts)
         torch.cuda.synchronize(dev)
         k_e2e = max(1, min(args.steps, 5))
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(k_e2e):
-            ko, vo, _ = pgs.sort(hk, hv, P, dtype=dtype, exchange=args.exchange)
+            ko, vo, _ = pgs.sort(hk, hv, P, **opts)
         torch.cuda.synchronize(dev)
         dt = (time.perf_counter() - t0) / k_e2e
         if world > 1:
@@ -351,6 +497,8 @@ def main():
             "roofline": roof,
             "hbm_frac_end_to_end": e2e_frac,
             "max_over_mean_bucket": stats["max_bucket"] / (n / stats["P"]),
+            "splitters": {"mode": args.splitters, "fallback": stats["fallback"],
+                          "learned_max_over_mean": stats["learned_over_mean"] if args.splitters == "learned" else None},
             "gpu_launches": stats["launches"] * args.steps,
             "launches_per_step": stats["launches"],
             "clocks": clocks.summary(),

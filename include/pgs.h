@@ -100,6 +100,8 @@ typedef struct pgs_launch_record {
 /* Opaque launch timer (host object holding CUDA events; no device memory). */
 typedef struct pgs_timer pgs_timer;
 
+#define PGS_TILE_VARIANTS 4
+
 /* Options.  A zeroed struct, or a NULL pointer, means all defaults. */
 typedef struct pgs_config {
   int32_t  dtype;             /* pgs_dtype, default PGS_U32 */
@@ -109,7 +111,9 @@ typedef struct pgs_config {
   int32_t  investigator;      /* pgs_investigator, default RANK */
   int32_t  exchange;          /* pgs_exchange, default AUTO */
   int32_t  splitter_mode;     /* pgs_splitter_mode, default SAMPLED */
-  int32_t  reserved0;
+  int32_t  tile_variant;      /* merge tile shape, 0..PGS_TILE_VARIANTS-1 (threads x outputs per thread:
+                                 0 = 256 x 9 (default), 1 = 128 x 9, 2 = 256 x 13, 3 = 128 x 17);
+                                 pgs_batch_tune picks one for a batch */
   void*    workspace;         /* device, 256-byte aligned, >= pgs_workspace_bytes(n, P, cfg) */
   uint64_t workspace_bytes;
   /* Optional device outputs, written when non-NULL: */
@@ -140,6 +144,8 @@ typedef struct pgs_stats {
   uint32_t passes;            /* full passes over the data the sort made */
   uint32_t launches;          /* kernels the call launched */
   float    max_over_mean;     /* largest bucket / its instance's mean bucket n_i / P_i */
+  float    learned_over_mean; /* LEARNED: the model's own largest bucket / mean, before the judge */
+  uint32_t reserved;
 } pgs_stats;
 
 /* Bytes of device workspace pgs_sort / pgs_sort_copy need for n keys on P
@@ -208,6 +214,19 @@ int pgs_batch_create(const uint64_t* offsets, uint32_t num, const uint32_t* P, i
 size_t pgs_batch_workspace_bytes(const pgs_batch* batch);
 int pgs_batch_upload(pgs_batch* batch, void* workspace, uint64_t workspace_bytes, void* stream);
 int pgs_sort_batched(pgs_batch* batch, void* keys, uint32_t* vals, void* stream, const pgs_config* cfg);
+/* Out-of-place form: reads keys_in/vals_in, writes keys_out/vals_out (the
+ * inputs are left unchanged, so a captured graph can be replayed on them). */
+int pgs_sort_batched_copy(pgs_batch* batch, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                          uint32_t* vals_out, void* stream, const pgs_config* cfg);
+/* Autotuner: times the whole batched sort once per merge tile shape on
+ * pseudo-random keys written into the caller's scratch buffers (device, one
+ * key and, for a batch with payload, one uint32 per key of the batch; their
+ * contents are overwritten), keeps the fastest shape in the batch (used by
+ * later calls whose cfg->tile_variant is 0) and returns it in *chosen (host,
+ * may be NULL) with the times in ms_out (host, PGS_TILE_VARIANTS floats, may
+ * be NULL).  Synchronises `stream`; call it outside any stream capture. */
+int pgs_batch_tune(pgs_batch* batch, void* scratch_keys, uint32_t* scratch_vals, void* stream,
+                   const pgs_config* cfg, uint32_t* chosen, float* ms_out);
 int pgs_batch_destroy(pgs_batch* batch);
 
 /* Step 3 of Section IV on a caller-given sample: sort m sample keys (device,

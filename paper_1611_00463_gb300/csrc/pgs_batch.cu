@@ -9,8 +9,10 @@
 namespace pgs {
 int batch_attrs_u32(bool vals);
 int batch_attrs_u64(bool vals);
-int batch_u32(const Shape&, const Options&, void*, uint32_t*, cudaStream_t);
-int batch_u64(const Shape&, const Options&, void*, uint32_t*, cudaStream_t);
+int batch_u32(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int batch_u64(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int fill_random_u32(void*, uint32_t*, uint64_t, uint64_t, cudaStream_t);
+int fill_random_u64(void*, uint32_t*, uint64_t, uint64_t, cudaStream_t);
 }  // namespace pgs
 
 using namespace pgs;
@@ -21,6 +23,7 @@ struct pgs_batch {
   std::vector<char> tables;   // the table region of the workspace, laid out by carve()
   size_t tables_bytes = 0;
   size_t ws_bytes = 0;
+  int variant = 0;            // merge tile shape chosen by pgs_batch_tune
 };
 
 extern "C" {
@@ -137,32 +140,78 @@ int pgs_batch_upload(pgs_batch* bt, void* workspace, uint64_t workspace_bytes, v
   return PGS_OK;
 }
 
-int pgs_sort_batched(pgs_batch* bt, void* keys, uint32_t* vals, void* stream, const pgs_config* cfg) {
+int pgs_sort_batched_copy(pgs_batch* bt, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                          uint32_t* vals_out, void* stream, const pgs_config* cfg) {
   if (!bt) return PGS_ERR_INVALID;
   Options o;
   int rc = read_options(cfg, &o);
   if (rc) return rc;
   if (o.dtype != bt->o.dtype) return PGS_ERR_INVALID;
   if (o.splitter_mode == PGS_SPLITTERS_LEARNED) return PGS_ERR_UNSUPPORTED;
-  if ((vals != nullptr) != bt->sh.vals) return PGS_ERR_INVALID;
+  if ((vals_in != nullptr) != bt->sh.vals || (vals_out != nullptr) != bt->sh.vals) return PGS_ERR_INVALID;
   if (bt->sh.n == 0) return PGS_OK;
-  if (!keys) return PGS_ERR_INVALID;
+  if (!keys_in || !keys_out) return PGS_ERR_INVALID;
   if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < bt->ws_bytes)
     return PGS_ERR_WORKSPACE;
-  // Batch options: the sampling and investigator settings fixed at create time,
-  // the per-call outputs of a single sort are not written.
+  // Batch options: the sampling settings fixed at create time; the per-call
+  // outputs of a single sort are not written for a batch.
   Options run = bt->o;
   run.workspace = o.workspace;
   run.workspace_bytes = o.workspace_bytes;
   run.stats = o.stats;
   run.timer = o.timer;
   run.investigator = o.investigator;
+  run.tile_variant = o.tile_variant ? o.tile_variant : bt->variant;
   run.bucket_bounds = nullptr;
   run.cuts = nullptr;
   run.splitters = nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (o.dtype == PGS_U64) return batch_u64(bt->sh, run, keys, vals, st);
-  return batch_u32(bt->sh, run, keys, vals, st);
+  if (o.dtype == PGS_U64) return batch_u64(bt->sh, run, keys_in, vals_in, keys_out, vals_out, st);
+  return batch_u32(bt->sh, run, keys_in, vals_in, keys_out, vals_out, st);
+}
+
+int pgs_sort_batched(pgs_batch* bt, void* keys, uint32_t* vals, void* stream, const pgs_config* cfg) {
+  return pgs_sort_batched_copy(bt, keys, vals, keys, vals, stream, cfg);
+}
+
+int pgs_batch_tune(pgs_batch* bt, void* scratch_keys, uint32_t* scratch_vals, void* stream, const pgs_config* cfg,
+                   uint32_t* chosen, float* ms_out) {
+  if (!bt) return PGS_ERR_INVALID;
+  if (bt->sh.n && !scratch_keys) return PGS_ERR_INVALID;
+  if ((scratch_vals != nullptr) != bt->sh.vals) return PGS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  PGS_CUDA(cudaEventCreate(&e0));
+  PGS_CUDA(cudaEventCreate(&e1));
+  float best = 0.0f;
+  int best_v = 0;
+  int rc = PGS_OK;
+  for (int v = 0; v < PGS_TILE_VARIANTS && rc == PGS_OK; ++v) {
+    pgs_config c = cfg ? *cfg : pgs_config{};
+    c.tile_variant = v;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && rc == PGS_OK; ++rep) {      // first run warms up
+      rc = bt->o.dtype == PGS_U64 ? fill_random_u64(scratch_keys, scratch_vals, bt->sh.n, 0x5EED + rep, st)
+                                  : fill_random_u32(scratch_keys, scratch_vals, bt->sh.n, 0x5EED + rep, st);
+      if (rc) break;
+      if (cudaEventRecord(e0, st) != cudaSuccess) { rc = PGS_ERR_CUDA; break; }
+      rc = pgs_sort_batched(bt, scratch_keys, scratch_vals, stream, &c);
+      if (rc) break;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PGS_ERR_CUDA;
+    }
+    if (ms_out) ms_out[v] = ms;
+    if (rc == PGS_OK && (v == 0 || ms < best)) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  bt->variant = best_v;
+  if (chosen) *chosen = (uint32_t)best_v;
+  return PGS_OK;
 }
 
 int pgs_batch_destroy(pgs_batch* bt) {

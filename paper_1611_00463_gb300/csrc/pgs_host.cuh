@@ -43,6 +43,7 @@ struct Options {
   pgs_timer* timer = nullptr;
   const float* model = nullptr;
   float* model_out = nullptr;
+  int tile_variant = 0;       // merge tile shape (see kMergeShapes)
 };
 
 // Validates and copies a (possibly NULL) pgs_config.  Returns PGS_OK or an error.
@@ -64,12 +65,14 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->timer = cfg->timer;
   o->model = cfg->model;
   o->model_out = cfg->model_out;
+  o->tile_variant = cfg->tile_variant;
   if (o->dtype < PGS_U32 || o->dtype > PGS_F32) return PGS_ERR_INVALID;
   if (!(o->eps > 0.0f) || o->eps > 1.0f) return PGS_ERR_INVALID;
   if (o->investigator < 0 || o->investigator > 2) return PGS_ERR_INVALID;
   if (o->exchange < 0 || o->exchange > 2) return PGS_ERR_INVALID;
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
   if (o->exchange == PGS_EXCHANGE_FUSED) return PGS_ERR_UNSUPPORTED;
+  if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;
   return PGS_OK;
 }
 
@@ -129,7 +132,7 @@ inline void finish_shape(Shape& sh) {
   uint64_t mp = std::max<uint64_t>(sh.R, sh.Q);
   if (sh.run_rounds > 0) mp = std::max<uint64_t>(mp, (uint64_t)sh.R * ceil_div(sh.maxlen, 2ull * kTile));
   sh.max_pairs = std::max<uint64_t>(mp, 1);
-  sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeTile) + sh.max_pairs + 1;
+  sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeMinTile) + sh.max_pairs + 1;
   sh.scan_len = std::max<uint64_t>(sh.max_pairs, sh.Q);
   sh.passes = 1 + sh.run_rounds + (sh.Pmax > 1 ? 1 + sh.bucket_rounds : 0);
 }
@@ -282,6 +285,7 @@ struct Ctx {
   cudaStream_t st = nullptr;
   pgs_timer* timer = nullptr;
   uint32_t launches = 0;
+  int variant = 0;            // merge tile shape
 };
 
 // Run `f` (which launches exactly one kernel on c.st), check the launch, count
@@ -328,15 +332,28 @@ inline int scan_u64(Ctx& c, const uint64_t* in, uint64_t* out, uint64_t m, uint6
                 [&] { k_scan_chunks<<<(unsigned)chunks, kScanNT, 0, c.st>>>(in, m, out, sums2); });
 }
 
+// Merge tile shapes the tuner chooses from (threads x outputs per thread);
+// variant 0 is the default.
+struct MergeShape { int nt, vt; };
+constexpr MergeShape kMergeShapes[PGS_TILE_VARIANTS] = {{256, 9}, {128, 9}, {256, 13}, {128, 17}};
+
+template <typename K, bool V, int NT, int VT>
+inline int set_merge_attr() {
+  PGS_CUDA(cudaFuncSetAttribute(k_merge_tile<K, V, NT, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Merge2Layout<K, V, NT, VT>::bytes));
+  return PGS_OK;
+}
+
 // Opt in to more than 48 KB of dynamic shared memory (set on every call: the
 // attribute belongs to the current device, and the call costs microseconds).
 template <typename K, bool V>
 inline int set_smem_attrs() {
   PGS_CUDA(cudaFuncSetAttribute(k_block_sort<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(BlockSortSmem<K>)));
-  PGS_CUDA(cudaFuncSetAttribute(k_merge_tile<K, V, kMergeNT, kMergeVT>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Merge2Layout<K, V, kMergeNT, kMergeVT>::bytes));
+  PGS_TRY((set_merge_attr<K, V, 256, 9>()));
+  PGS_TRY((set_merge_attr<K, V, 128, 9>()));
+  PGS_TRY((set_merge_attr<K, V, 256, 13>()));
+  PGS_TRY((set_merge_attr<K, V, 128, 17>()));
   PGS_CUDA(cudaFuncSetAttribute(k_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ScatterSmem<K>)));
   PGS_CUDA(cudaFuncSetAttribute(k_mlp_grad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -344,31 +361,37 @@ inline int set_smem_attrs() {
   return PGS_OK;
 }
 
+template <typename K, bool V, int NT, int VT>
+inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t tiles,
+                              const Buffers& b, const uint64_t* total, int f32_out, cudaStream_t st) {
+  k_merge_tile<K, V, NT, VT><<<(unsigned)tiles, NT, Merge2Layout<K, V, NT, VT>::bytes, st>>>(
+      ks, vs, kd, vd, b.split, total, f32_out, b.err);
+}
+
 // One pairwise merge round over pairs already described in b.pairs / b.tcount
-// (tile counts of kMergeTile).  `len` keys take part; every one of them is read
-// and written once.
+// (tile counts of the chosen tile shape).  `len` keys take part; every one of
+// them is read and written once.
 template <typename K, bool V>
 inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
                        uint64_t len, const Buffers& b, int f32_out, uint32_t step) {
+  const MergeShape ms = kMergeShapes[c.variant];
+  const uint32_t tile = (uint32_t)(ms.nt * ms.vt);
   PGS_TRY(scan_u64(c, b.tcount, b.tbegin, npairs, b.scan_sums, b.scan_sums2, step));
-  const uint64_t tiles_ub = ceil_div(len, kMergeTile) + npairs;
-  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, kMergeTile), [&] {
-    k_partition_split<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.split,
-                                                                    (uint32_t)kMergeTile);
+  const uint64_t tiles_ub = ceil_div(len, tile) + npairs;
+  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, tile), [&] {
+    k_partition_split<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.split, tile);
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
-  constexpr size_t smem = Merge2Layout<K, V, kMergeNT, kMergeVT>::bytes;
+  const uint64_t* total = b.tbegin + npairs;
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
-    k_merge_tile<K, V, kMergeNT, kMergeVT><<<(unsigned)tiles_ub, kMergeNT, smem, c.st>>>(
-        ks, vs, kd, vd, b.split, b.tbegin + npairs, f32_out, b.err);
+    switch (c.variant) {
+      case 1: launch_merge_tile<K, V, 128, 9>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+      case 2: launch_merge_tile<K, V, 256, 13>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+      case 3: launch_merge_tile<K, V, 128, 17>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+      default: launch_merge_tile<K, V, 256, 9>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+    }
   });
 }
-
-// ---------------------------------------------------------------------------
-// The sort: Section IV, steps 1-6, for every instance of a batch at once.
-// The batch tables must already be in the workspace (k_tables_single for a
-// single sort, or uploaded by the batch API).
-// ---------------------------------------------------------------------------
 
 // Learned splitters (single sort, P > 1): the model (trained on the sorted
 // sample `sorted` or the caller's), the per-run histogram of every key's
@@ -434,6 +457,7 @@ template <typename K, bool V>
 int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
                  Ctx& c, const Buffers& b) {
   cudaStream_t st = c.st;
+  c.variant = o.tile_variant;
   const Geo g = b.geo(sh);
   const uint64_t n = sh.n;
   const uint32_t R = sh.R;
@@ -462,7 +486,7 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
     const uint64_t np = cmax * R;
     PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
       k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, b.run_off, R, w, cmax,
-                                                      (uint32_t)kMergeTile);
+                                                      (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
     }));
     --left;
     PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, n, b, left == 0 ? f32 : 0, 1)));
@@ -487,7 +511,7 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       const uint32_t step = 1u << k;
       PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 3, 32 * (uint64_t)R, [&] {
         k_pairs_sample_lists<<<grid_for(R, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.samp_off, step,
-                                                               (uint32_t)kMergeTile);
+                                                               (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
       }));
       PGS_TRY((merge_round<K, false>(c, sa, nullptr, sb, nullptr, R, sh.S, b, 0, 3)));
       std::swap(sa, sb);
@@ -531,7 +555,7 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       const uint32_t step = 1u << k;
       PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * sh.Q, [&] {
         k_pairs_bucket_lists<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, sh.Q, step,
-                                                                   (uint32_t)kMergeTile);
+                                                                   (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
       }));
       --left;
       PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
@@ -552,8 +576,8 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
   return launch(c, PGS_KERNEL_STATS, 0, 8 * ((uint64_t)R + sh.I), [&] {
     k_stats<<<1, 256, 0, st>>>(g, b.e, n, (uint32_t)std::min<uint64_t>(sh.s, 0xFFFFFFFFu),
                                sh.learned ? PGS_SPLITTERS_LEARNED : PGS_SPLITTERS_SAMPLED, (uint32_t)sh.passes,
-                               launches, b.err, b.fallback, static_cast<DevStats*>(o.stats), o.bucket_bounds,
-                               b.max_ratio);
+                               launches, b.err, b.fallback, b.learned_ratio, static_cast<DevStats*>(o.stats),
+                               o.bucket_bounds, b.max_ratio);
   });
 }
 

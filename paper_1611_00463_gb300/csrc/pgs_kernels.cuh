@@ -16,9 +16,10 @@ namespace pgs {
 constexpr int kNT = 256;             // threads per CTA of the sort and merge kernels
 constexpr int kVT = 17;              // items per thread; odd, so blocked smem access is conflict free
 constexpr int kTile = kNT * kVT;     // 4352 keys per block-sort tile and per merge tile
-constexpr int kMergeNT = 256;        // threads per merge CTA
+constexpr int kMergeNT = 256;        // threads per merge CTA (default shape)
 constexpr int kMergeVT = 9;          // outputs per merge thread (odd: conflict-free staging)
 constexpr int kMergeTile = kMergeNT * kMergeVT;   // 2304 outputs per merge tile
+constexpr int kMergeMinTile = 128 * 9;            // smallest tile of the tunable shapes
 constexpr int kScanNT = 1024;
 constexpr int kScanVT = 8;
 constexpr int kScanChunk = kScanNT * kScanVT;
@@ -838,6 +839,20 @@ k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __re
   if (VALS) store_tile_vec<uint32_t, kScatterNT>(vdst + o, sm.vals, cnt);
 }
 
+// Pseudo-random keys (splitmix64 of the position and a seed) and index
+// payloads, for timing runs of the tuner.
+template <typename K>
+__global__ void k_fill_random(K* keys, uint32_t* vals, uint64_t n, uint64_t seed) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t z = (i + 1) * 0x9E3779B97F4A7C15ull + seed;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  keys[i] = (K)z;
+  if (vals) vals[i] = (uint32_t)i;
+}
+
 // ---------------------------------------------------------------------------
 // K9: load statistics (Table II: each processor's share after the sort).
 // ---------------------------------------------------------------------------
@@ -849,14 +864,16 @@ struct DevStats {                     // layout of pgs_stats
   uint32_t splitter_mode, fallback, error, passes;
   uint32_t launches;
   float max_over_mean;
+  float learned_over_mean;
+  uint32_t reserved;
 };
 
 // Bucket sizes e_{b+1} - e_b over all buckets of all instances: the largest,
 // the smallest, and the largest ratio to its instance's mean n_i / P_i.
 static __global__ void __launch_bounds__(256)
 k_stats(Geo g, const uint64_t* __restrict__ e, uint64_t n_total, uint32_t s, uint32_t mode, uint32_t passes,
-        uint32_t launches, const uint32_t* err_word, const uint32_t* fallback_word, DevStats* st,
-        uint64_t* user_bounds, float* max_ratio_out) {
+        uint32_t launches, const uint32_t* err_word, const uint32_t* fallback_word,
+        const float* learned_ratio, DevStats* st, uint64_t* user_bounds, float* max_ratio_out) {
   __shared__ uint64_t smax[256], smin[256];
   __shared__ float sratio[256];
   uint64_t mx = 0, mn = ~0ull;
@@ -898,6 +915,8 @@ k_stats(Geo g, const uint64_t* __restrict__ e, uint64_t n_total, uint32_t s, uin
       st->passes = passes;
       st->launches = launches;
       st->max_over_mean = sratio[0];
+      st->learned_over_mean = learned_ratio ? *learned_ratio : 0.0f;
+      st->reserved = 0;
     }
   }
 }

@@ -20,15 +20,23 @@ int batch_attrs_u32(bool vals) {
   return vals ? set_all_smem_attrs<uint32_t, true>() : set_all_smem_attrs<uint32_t, false>();
 }
 
-int batch_u32(const Shape& sh, const Options& o, void* keys, uint32_t* vals, cudaStream_t st) {
+int batch_u32(const Shape& sh, const Options& o, const void* kin, const uint32_t* vin, void* kout,
+             uint32_t* vout, cudaStream_t st) {
   Ctx c;
   c.st = st;
   c.timer = o.timer;
   Buffers b;
   carve(sh, o.workspace, &b);
-  auto k = static_cast<uint32_t*>(keys);
-  if (vals) return run_pipeline<uint32_t, true>(sh, o, k, vals, k, vals, c, b);
-  return run_pipeline<uint32_t, false>(sh, o, k, nullptr, k, nullptr, c, b);
+  auto ki = static_cast<const uint32_t*>(kin);
+  auto ko = static_cast<uint32_t*>(kout);
+  if (vin) return run_pipeline<uint32_t, true>(sh, o, ki, vin, ko, vout, c, b);
+  return run_pipeline<uint32_t, false>(sh, o, ki, nullptr, ko, nullptr, c, b);
+}
+
+int fill_random_u32(void* keys, uint32_t* vals, uint64_t n, uint64_t seed, cudaStream_t st) {
+  k_fill_random<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(static_cast<uint32_t*>(keys), vals, n, seed);
+  PGS_CUDA(cudaGetLastError());
+  return PGS_OK;
 }
 
 }  // namespace pgs

@@ -233,8 +233,12 @@ def batched(num: int = 10000, seed: int = 4, **size_kw):
     offsets = np.zeros(num + 1, dtype=np.uint64)
     offsets[1:] = np.cumsum(sizes).astype(np.uint64)
     keys = np.empty(int(offsets[-1]), dtype=np.uint64)
-    for i in range(num):
+
+    def work(i: int) -> None:
         keys[int(offsets[i]):int(offsets[i + 1])] = batched_instance_keys(i, int(sizes[i]))
+
+    with _cf.ThreadPoolExecutor(_threads()) as ex:
+        list(ex.map(work, range(num)))
     return offsets, keys, batched_partitions(sizes)
 
 

@@ -35,7 +35,7 @@ class pgs_config(ctypes.Structure):
         ("investigator", ctypes.c_int32),
         ("exchange", ctypes.c_int32),
         ("splitter_mode", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("tile_variant", ctypes.c_int32),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_uint64),
         ("bucket_bounds", ctypes.c_void_p),
@@ -62,6 +62,8 @@ class pgs_stats(ctypes.Structure):
         ("passes", ctypes.c_uint32),
         ("launches", ctypes.c_uint32),
         ("max_over_mean", ctypes.c_float),
+        ("learned_over_mean", ctypes.c_float),
+        ("reserved", ctypes.c_uint32),
     ]
 
     def as_dict(self) -> dict:
@@ -97,7 +99,12 @@ EXPORTS = {
     "pgs_sort_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p]),
     "pgs_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "pgs_sort_batched_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
+TILE_VARIANTS = 4
 
 KERNELS = ["block_sort", "merge", "partition", "pairs", "scan", "sample", "splitters", "cut_search",
            "investigator", "offsets", "scatter", "stats"]
@@ -212,7 +219,8 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
                 workspace: torch.Tensor | None = None, bucket_bounds: torch.Tensor | None = None,
                 cuts: torch.Tensor | None = None, splitters_out: torch.Tensor | None = None,
                 stats: torch.Tensor | None = None, timer: Timer | None = None,
-                model: torch.Tensor | None = None, model_out: torch.Tensor | None = None) -> pgs_config:
+                model: torch.Tensor | None = None, model_out: torch.Tensor | None = None,
+                tile_variant: int = 0) -> pgs_config:
     c = pgs_config()
     c.dtype = DTYPES[dtype]
     c.samples_per_run = samples_per_run
@@ -231,6 +239,7 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
     c.timer = timer.handle if timer is not None else None
     c.model = _ptr(model)
     c.model_out = _ptr(model_out)
+    c.tile_variant = tile_variant
     return c
 
 
@@ -316,6 +325,27 @@ class Batch:
         cfg = cfg if cfg is not None else self.config()
         _check(load().pgs_sort_batched(self.handle, _ptr(keys), _ptr(vals), _stream(stream), ctypes.byref(cfg)),
                "pgs_sort_batched")
+
+    def sort_copy(self, keys_in: torch.Tensor, vals_in: torch.Tensor | None, keys_out: torch.Tensor,
+                  vals_out: torch.Tensor | None, stream=None, cfg: pgs_config | None = None):
+        """Sort every instance of keys_in (and vals_in) into keys_out (and vals_out)."""
+        for t in (keys_in, keys_out):
+            if t.numel() != self.n:
+                raise ValueError("length mismatch")
+        cfg = cfg if cfg is not None else self.config()
+        _check(load().pgs_sort_batched_copy(self.handle, _ptr(keys_in), _ptr(vals_in), _ptr(keys_out),
+                                            _ptr(vals_out), _stream(stream), ctypes.byref(cfg)),
+               "pgs_sort_batched_copy")
+
+    def tune(self, scratch_keys: torch.Tensor, scratch_vals: torch.Tensor | None, stream=None):
+        """Time every merge tile shape on pseudo-random keys in the scratch
+        buffers and keep the fastest; returns (chosen, [ms per shape])."""
+        chosen = ctypes.c_uint32()
+        ms = (ctypes.c_float * TILE_VARIANTS)()
+        cfg = self.config()
+        _check(load().pgs_batch_tune(self.handle, _ptr(scratch_keys), _ptr(scratch_vals), _stream(stream),
+                                     ctypes.byref(cfg), ctypes.byref(chosen), ms), "pgs_batch_tune")
+        return chosen.value, list(ms)
 
     def close(self):
         if self.handle:

@@ -42,7 +42,7 @@ def test_binding_names_match_header():
 def test_struct_sizes_match_header(lib):
     from paper_1611_00463_gb300 import pgs
     # pgs_stats is copied byte for byte from the device block.
-    assert ctypes.sizeof(pgs.pgs_stats) == 56
+    assert ctypes.sizeof(pgs.pgs_stats) == 64
     assert [lib.pgs_batch_auto_partitions(n) for n in [1, 65535, 65536, 131071, 131072, 1 << 24, 1 << 30]] == \
         [1, 1, 1, 1, 2, 256, 256]
     assert ctypes.sizeof(pgs.pgs_config) == 32 + 8 * 10

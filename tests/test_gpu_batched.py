@@ -123,3 +123,35 @@ def test_single_sort_is_batch_of_one():
     single = gpu_sort(keys, vals, P, "u64")
     assert np.array_equal(got_k, single["keys"]) and np.array_equal(got_v, single["vals"])
     assert st["max_bucket"] == single["stats"]["max_bucket"]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_merge_tile_shape_gives_the_stable_sort(variant):
+    from tests.gpu_helpers import gpu_sort
+    n = 90_017
+    keys = inputs.zipf_dup_f32(n, 12)
+    vals = inputs.index_payload(n)
+    got = gpu_sort(keys, vals, 20, "f32", tile_variant=variant)
+    want_k, want_v = O.stable_sort(keys, vals, "f32")
+    assert np.array_equal(got["keys"], want_k) and np.array_equal(got["vals"], want_v)
+    assert np.array_equal(got["e"], O.buckets(keys, 20, "f32")["e"])
+
+
+def test_tuner_and_out_of_place_batch():
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    offsets, keys, vals = make_batch(30, seed=2, hi=200_000)
+    P = np.random.default_rng(1).integers(1, 16, size=30).astype(np.uint32)
+    bt = pgs.Batch(offsets, P, dtype="u64", with_vals=True)
+    sk = torch.empty(bt.n, dtype=torch.int64, device="cuda")
+    sv = torch.empty(bt.n, dtype=torch.int32, device="cuda")
+    chosen, ms = bt.tune(sk, sv)
+    assert 0 <= chosen < pgs.TILE_VARIANTS and all(m > 0 for m in ms) and ms[chosen] == min(ms)
+    kin = pgs.as_device_keys(keys, "u64")
+    vin = torch.from_numpy(vals.view(np.int32)).cuda()
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    bt.sort_copy(kin, vin, kout, vout)
+    torch.cuda.synchronize()
+    assert np.array_equal(pgs.to_numpy_keys(kin, "u64"), keys)          # input untouched
+    Peff = [max(1, min(int(P[i]), int(offsets[i + 1] - offsets[i]))) for i in range(30)]
+    check(offsets, keys, vals, pgs.to_numpy_keys(kout, "u64"), vout.cpu().numpy().view(np.uint32), Peff, "u64")
