@@ -60,8 +60,9 @@ typedef enum {
 typedef enum { PGS_INVESTIGATOR_RANK = 0, PGS_INVESTIGATOR_EQUAL = 1, PGS_INVESTIGATOR_OFF = 2 } pgs_investigator;
 
 /* Step 5 (Section IV-C): SCATTER copies every run segment to its bucket before
- * the merge; FUSED lets the merge read the segments where the runs left them.
- * AUTO lets the library pick (currently SCATTER). */
+ * the merge (one pass of its own); FUSED lets the first merge round of step 6
+ * read each pair of segments where the sorted runs left them and write the
+ * merged pair to its place in the bucket.  AUTO picks FUSED. */
 typedef enum { PGS_EXCHANGE_AUTO = 0, PGS_EXCHANGE_SCATTER = 1, PGS_EXCHANGE_FUSED = 2 } pgs_exchange;
 
 /* Splitter source.  SAMPLED: steps 2-3 of Section IV.  LEARNED: an MLP CDF

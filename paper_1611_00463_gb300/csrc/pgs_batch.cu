@@ -91,6 +91,7 @@ int pgs_batch_create(const uint64_t* offsets, uint32_t num, const uint32_t* P, i
   sh.S = S;
   sh.maxlen = maxlen;
   sh.s = 0;
+  sh.scatter = o.exchange == PGS_EXCHANGE_SCATTER;
   finish_shape(sh);
 
   std::vector<uint64_t> run_off(R + 1);

@@ -71,7 +71,6 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   if (o->investigator < 0 || o->investigator > 2) return PGS_ERR_INVALID;
   if (o->exchange < 0 || o->exchange > 2) return PGS_ERR_INVALID;
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
-  if (o->exchange == PGS_EXCHANGE_FUSED) return PGS_ERR_UNSUPPORTED;
   if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;
   return PGS_OK;
 }
@@ -105,6 +104,7 @@ struct Shape {
   int w = 4;                 // key bytes
   bool vals = false;
   bool learned = false;      // learned-CDF splitters (single sorts only)
+  bool scatter = false;      // step 5 as its own pass (else fused into step 6's first round)
   int run_rounds = 0;        // merge rounds growing block-sorted tiles into runs (step 1)
   int bucket_rounds = 0;     // merge rounds of steps 3 and 6: ceil(log2 Pmax)
   uint64_t max_pairs = 1;
@@ -134,7 +134,7 @@ inline void finish_shape(Shape& sh) {
   sh.max_pairs = std::max<uint64_t>(mp, 1);
   sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeMinTile) + sh.max_pairs + 1;
   sh.scan_len = std::max<uint64_t>(sh.max_pairs, sh.Q);
-  sh.passes = 1 + sh.run_rounds + (sh.Pmax > 1 ? 1 + sh.bucket_rounds : 0);
+  sh.passes = 1 + sh.run_rounds + (sh.Pmax > 1 ? (sh.scatter ? 1 : 0) + sh.bucket_rounds : 0);
 }
 
 // A single sort of n keys on P_req logical partitions.
@@ -153,6 +153,7 @@ inline Shape single_shape(uint64_t n, uint32_t P_req, bool vals, const Options& 
   sh.s = P > 1 ? samples_per_run(P, sh.w, o) : 0;
   sh.S = P > 1 ? (sh.s >= sh.maxlen ? n : (uint64_t)P * sh.s) : 0;
   sh.learned = o.splitter_mode == PGS_SPLITTERS_LEARNED && P > 1;
+  sh.scatter = o.exchange == PGS_EXCHANGE_SCATTER;
   finish_shape(sh);
   return sh;
 }
@@ -538,24 +539,39 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       k_bucket_sizes<<<grid_for(sh.Q, 256), 256, 0, st>>>(g, sh.Q, b.cut, b.sizes, b.seg_src);
     }));
     PGS_TRY(scan_u64(c, b.sizes, b.off, sh.Q, b.scan_sums, b.scan_sums2, 5));
-    // Step 5: the exchange, as an in-HBM scatter into bucket-major order.
-    const uint64_t stiles = ceil_div(n, kScatterTile);
-    PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 8 * stiles, [&] {
-      k_scatter_part<<<grid_for(stiles, 256), 256, 0, st>>>(b.off, sh.Q, n, b.first_seg);
-    }));
-    --left;
-    PGS_TRY(launch(c, PGS_KERNEL_SCATTER, 5, 2 * n * kv, [&] {
-      k_scatter<K, V><<<(unsigned)stiles, kScatterNT, sizeof(ScatterSmem<K>), st>>>(
-          cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, left == 0 ? f32 : 0);
-    }));
-    std::swap(cur_k, oth_k);
-    std::swap(cur_v, oth_v);
+    const uint32_t mtile = (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt);
+    int k0 = 0;
+    if (sh.scatter) {
+      // Step 5: the exchange, as an in-HBM scatter into bucket-major order.
+      const uint64_t stiles = ceil_div(n, kScatterTile);
+      PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 8 * stiles, [&] {
+        k_scatter_part<<<grid_for(stiles, 256), 256, 0, st>>>(b.off, sh.Q, n, b.first_seg);
+      }));
+      --left;
+      PGS_TRY(launch(c, PGS_KERNEL_SCATTER, 5, 2 * n * kv, [&] {
+        k_scatter<K, V><<<(unsigned)stiles, kScatterNT, sizeof(ScatterSmem<K>), st>>>(
+            cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, left == 0 ? f32 : 0);
+      }));
+      std::swap(cur_k, oth_k);
+      std::swap(cur_v, oth_v);
+    } else {
+      // Steps 5 and 6 fused: the first merge round of every bucket reads its
+      // two segments where the sorted runs hold them and writes the merged
+      // pair to its place in bucket-major order.
+      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 5, 48 * sh.Q, [&] {
+        k_pairs_fused<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, b.seg_src, sh.Q, mtile);
+      }));
+      --left;
+      PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
+      std::swap(cur_k, oth_k);
+      std::swap(cur_v, oth_v);
+      k0 = 1;
+    }
     // Step 6: every bucket merges its P segments with the Fig. 2 schedule.
-    for (int k = 0; k < sh.bucket_rounds; ++k) {
+    for (int k = k0; k < sh.bucket_rounds; ++k) {
       const uint32_t step = 1u << k;
       PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * sh.Q, [&] {
-        k_pairs_bucket_lists<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, sh.Q, step,
-                                                                   (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
+        k_pairs_bucket_lists<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, sh.Q, step, mtile);
       }));
       --left;
       PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));

@@ -28,8 +28,8 @@ constexpr int kScatterVT = 16;
 constexpr int kScatterTile = kScatterNT * kScatterVT;
 constexpr int kScatterWindow = 1024;  // bucket segments staged per scatter CTA
 
-struct Pair {                         // one pairwise merge: [lo, mid) + [mid, hi) -> [lo, hi)
-  uint64_t lo, mid, hi;
+struct Pair {                         // one pairwise merge: A = [a, a+na), B = [b, b+nb) -> [out, out+na+nb)
+  uint64_t a, na, b, nb, out;
 };
 
 // Batch geometry: device tables describing I sort instances laid end to end.
@@ -230,9 +230,10 @@ k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kou
 // Pair descriptors for one merge round, and the tile bookkeeping.
 // ---------------------------------------------------------------------------
 
+// Contiguous pair [lo, mid) + [mid, hi) -> [lo, hi).
 __device__ __forceinline__ void put_pair(Pair* pairs, uint64_t* tcount, uint64_t p, uint64_t lo, uint64_t mid,
                                          uint64_t hi, uint32_t tile) {
-  pairs[p] = Pair{lo, mid, hi};
+  pairs[p] = Pair{lo, mid - lo, mid, hi - mid, lo};
   tcount[p] = (hi - lo + tile - 1) / tile;
 }
 
@@ -292,6 +293,27 @@ static __global__ void k_pairs_bucket_lists(Pair* pairs, uint64_t* tcount, Geo g
   }
   put_pair(pairs, tcount, q, off[base + j], off[base + umin(j + step, P)], off[base + umin(j + 2 * step, P)],
            tile);
+}
+
+// Step 5 fused into the first round of step 6: segment j of bucket b (j even)
+// merges with segment j+1 straight from the sorted runs, where the exchange
+// would have copied them from, into the pair's place in bucket-major order.
+static __global__ void k_pairs_fused(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
+                                     const uint64_t* __restrict__ seg_src, uint64_t Q, uint32_t tile) {
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
+  const uint64_t P = g.P[i];
+  const uint64_t j = (q - g.seg[i]) % P;
+  if (j % 2 != 0) {
+    pairs[q] = Pair{0, 0, 0, 0, 0};
+    tcount[q] = 0;
+    return;
+  }
+  const uint64_t na = off[q + 1] - off[q];
+  const uint64_t nb = j + 1 < P ? off[q + 2] - off[q + 1] : 0;
+  pairs[q] = Pair{seg_src[q], na, j + 1 < P ? seg_src[q + 1] : 0, nb, off[q]};
+  tcount[q] = (na + nb + tile - 1) / tile;
 }
 
 // ---------------------------------------------------------------------------
@@ -362,6 +384,7 @@ __device__ __forceinline__ void store_tile_vec(T* g, const T* s, int cnt) {
 struct TileSplit {
   uint64_t a, b, out;     // first A element, first B element, first output element
   uint64_t a_end, b_end;  // end of the pair's A list and of its B list
+  uint64_t pair;          // index of the pair the tile belongs to
 };
 
 template <typename K>
@@ -377,10 +400,9 @@ __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restr
     if (tbegin[mid] <= i) lo = mid; else hi = mid;
   }
   const Pair pr = pairs[lo];
-  const uint64_t na = pr.mid - pr.lo, nb = pr.hi - pr.mid;
   const uint64_t d0 = (i - tbegin[lo]) * tile;
-  const uint64_t a0 = merge_path<K, uint64_t>(src + pr.lo, na, src + pr.mid, nb, d0);
-  split[i] = TileSplit{pr.lo + a0, pr.mid + (d0 - a0), pr.lo + d0, pr.mid, pr.hi};
+  const uint64_t a0 = merge_path<K, uint64_t>(src + pr.a, pr.na, src + pr.b, pr.nb, d0);
+  split[i] = TileSplit{pr.a + a0, pr.b + (d0 - a0), pr.out + d0, pr.a + pr.na, pr.b + pr.nb, lo};
 }
 
 template <typename K, bool VALS, int NT, int VT>
@@ -410,7 +432,7 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
       TileSplit nx{};
       if (tile + 1 < total) {
         nx = split[tile + 1];
-        same = nx.a_end == t.a_end && nx.b_end == t.b_end;
+        same = nx.pair == t.pair;
       }
       na = (uint32_t)((same ? nx.a : t.a_end) - t.a);
       nb = (uint32_t)((same ? nx.b : t.b_end) - t.b);

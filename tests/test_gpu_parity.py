@@ -83,6 +83,18 @@ def test_structured(kind):
     check_against_oracle(keys, inputs.index_payload(n), 12, "u32")
 
 
+@pytest.mark.parametrize("exchange", ["scatter", "fused"])
+@pytest.mark.parametrize("dtype,P", [("u64", 7), ("f32", 33), ("u32", 128)])
+def test_exchange_modes(exchange, dtype, P):
+    n = 3 * TILE + 1234
+    gen = {"u32": inputs.exponential_u32, "u64": inputs.normal_lognormal_u64, "f32": inputs.zipf_dup_f32}[dtype]
+    keys = gen(n, P)
+    got = check_against_oracle(keys, inputs.index_payload(n), P, dtype, exchange=exchange)
+    passes = got["stats"]["passes"]
+    other = _gpu(keys, inputs.index_payload(n), P, dtype, exchange="fused" if exchange == "scatter" else "scatter")
+    assert other["stats"]["passes"] == passes + (1 if exchange == "fused" else -1)
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_investigator_variants(variant):
     n = 60_000
