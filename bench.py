@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the number of keys (smaller cases)")
     ap.add_argument("--P", type=int, default=None)
     ap.add_argument("--exchange", default="auto", choices=["auto", "scatter", "fused"])
+    ap.add_argument("--merge-ways", type=int, default=0, choices=[0, 2, 4], help="tree levels per pass (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-timer", action="store_true", help="skip per-launch events (profiling runs)")
@@ -245,6 +246,7 @@ def config_block(args, dtype, n, P, stats):
         "n": n, "P": P, "key": dtype, "payload": "u32 index",
         "l2": "inputs larger than L2 (no flush between steps)",
         "exchange": args.exchange,
+        "merge_ways": args.merge_ways or 2,
         "splitters": args.splitters,
         "guaranteed": bool(args.guaranteed),
     }
@@ -391,7 +393,8 @@ def main():
     vin = torch.from_numpy(vals_np.view(np.int32)).to(dev)
     kout = torch.empty_like(kin)
     vout = torch.empty_like(vin)
-    opts = dict(dtype=dtype, exchange=args.exchange, splitters=args.splitters, guaranteed=args.guaranteed)
+    opts = dict(dtype=dtype, exchange=args.exchange, splitters=args.splitters, guaranteed=args.guaranteed,
+                merge_ways=args.merge_ways)
     cfg0 = pgs.make_config(**opts)
     ws = pgs.workspace(n, P, cfg0, dev)
     st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)

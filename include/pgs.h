@@ -130,6 +130,10 @@ typedef struct pgs_config {
                                  training one; rejected (sampled cuts kept) if its signs do not make
                                  it monotone */
   float*    model_out;        /* optional device buffer of PGS_MLP_WORDS words: the model used */
+  int32_t   merge_ways;       /* levels of the Fig. 2 merge tree per pass over the data: 2 (one level,
+                                 pairwise rounds, default; 0 means 2) or 4 (two levels per pass: fewer
+                                 passes, more shared-memory work per chunk) */
+  int32_t   reserved1;
 } pgs_config;
 
 /* Load statistics of one sort (Table II reports the per-processor share). */

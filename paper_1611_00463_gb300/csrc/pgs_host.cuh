@@ -44,6 +44,7 @@ struct Options {
   const float* model = nullptr;
   float* model_out = nullptr;
   int tile_variant = 0;       // merge tile shape (see kMergeShapes)
+  int merge_ways = 2;         // tree levels per pass: 2-way (one level) or 4-way (two levels)
 };
 
 // Validates and copies a (possibly NULL) pgs_config.  Returns PGS_OK or an error.
@@ -66,12 +67,14 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->model = cfg->model;
   o->model_out = cfg->model_out;
   o->tile_variant = cfg->tile_variant;
+  o->merge_ways = cfg->merge_ways == 0 ? 2 : cfg->merge_ways;
   if (o->dtype < PGS_U32 || o->dtype > PGS_F32) return PGS_ERR_INVALID;
   if (!(o->eps > 0.0f) || o->eps > 1.0f) return PGS_ERR_INVALID;
   if (o->investigator < 0 || o->investigator > 2) return PGS_ERR_INVALID;
   if (o->exchange < 0 || o->exchange > 2) return PGS_ERR_INVALID;
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
   if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;
+  if (o->merge_ways != 2 && o->merge_ways != 4) return PGS_ERR_INVALID;
   return PGS_OK;
 }
 
@@ -105,6 +108,9 @@ struct Shape {
   bool vals = false;
   bool learned = false;      // learned-CDF splitters (single sorts only)
   bool scatter = false;      // step 5 as its own pass (else fused into step 6's first round)
+  bool four = false;         // four-way rounds (two tree levels per pass)
+  uint64_t max_quads = 1;
+  uint64_t max_chunks = 1;
   int run_rounds = 0;        // merge rounds growing block-sorted tiles into runs (step 1)
   int bucket_rounds = 0;     // merge rounds of steps 3 and 6: ceil(log2 Pmax)
   uint64_t max_pairs = 1;
@@ -133,8 +139,14 @@ inline void finish_shape(Shape& sh) {
   if (sh.run_rounds > 0) mp = std::max<uint64_t>(mp, (uint64_t)sh.R * ceil_div(sh.maxlen, 2ull * kTile));
   sh.max_pairs = std::max<uint64_t>(mp, 1);
   sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeMinTile) + sh.max_pairs + 1;
-  sh.scan_len = std::max<uint64_t>(sh.max_pairs, sh.Q);
-  sh.passes = 1 + sh.run_rounds + (sh.Pmax > 1 ? (sh.scatter ? 1 : 0) + sh.bucket_rounds : 0);
+  sh.max_quads = std::max<uint64_t>(sh.Q, 1);
+  if (sh.run_rounds > 1) sh.max_quads = std::max<uint64_t>(sh.max_quads, (uint64_t)sh.R * ceil_div(sh.maxlen, 4ull * kTile));
+  sh.max_chunks = sh.max_quads + ceil_div(std::max<uint64_t>(sh.n, 1), kMerge4Cut) + 1;
+  sh.scan_len = std::max<uint64_t>(std::max<uint64_t>(sh.max_pairs, sh.Q), sh.max_quads);
+  auto passes_for = [&](int levels) { return sh.four ? levels / 2 + levels % 2 : levels; };
+  int bucket_passes = 0;
+  if (sh.Pmax > 1) bucket_passes = sh.scatter ? 1 + passes_for(sh.bucket_rounds) : 1 + passes_for(sh.bucket_rounds - 1);
+  sh.passes = 1 + passes_for(sh.run_rounds) + bucket_passes;
 }
 
 // A single sort of n keys on P_req logical partitions.
@@ -154,6 +166,7 @@ inline Shape single_shape(uint64_t n, uint32_t P_req, bool vals, const Options& 
   sh.S = P > 1 ? (sh.s >= sh.maxlen ? n : (uint64_t)P * sh.s) : 0;
   sh.learned = o.splitter_mode == PGS_SPLITTERS_LEARNED && P > 1;
   sh.scatter = o.exchange == PGS_EXCHANGE_SCATTER;
+  sh.four = o.merge_ways == 4;
   finish_shape(sh);
   return sh;
 }
@@ -166,6 +179,7 @@ struct Buffers {
   uint64_t *samp_counts, *samp_off;
   Pair* pairs; uint64_t *tcount, *tbegin;
   TileSplit* split;
+  Quad* quads; uint64_t *ccount, *coff; Cut4 *cuts_a, *cuts_b; Chunk4* chunks4;
   uint64_t *scan_sums, *scan_sums2;
   uint64_t* first_seg;
   // batch tables
@@ -212,6 +226,19 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->tcount = c.take<uint64_t>(sh.max_pairs);
   b->tbegin = c.take<uint64_t>(sh.max_pairs + 1);
   b->split = c.take<TileSplit>(sh.max_tiles);
+  if (sh.four) {
+    b->quads = c.take<Quad>(sh.max_quads);
+    b->ccount = c.take<uint64_t>(sh.max_quads);
+    b->coff = c.take<uint64_t>(sh.max_quads + 1);
+    b->cuts_a = c.take<Cut4>(sh.max_chunks);
+    b->cuts_b = c.take<Cut4>(sh.max_chunks);
+    b->chunks4 = c.take<Chunk4>(sh.max_chunks);
+  } else {
+    b->chunks4 = nullptr;
+    b->quads = nullptr;
+    b->ccount = b->coff = nullptr;
+    b->cuts_a = b->cuts_b = nullptr;
+  }
   const uint64_t chunks = ceil_div(sh.scan_len, kScanChunk);
   b->scan_sums = c.take<uint64_t>(chunks + 1);
   b->scan_sums2 = c.take<uint64_t>(chunks + 1);
@@ -355,6 +382,8 @@ inline int set_smem_attrs() {
   PGS_TRY((set_merge_attr<K, V, 128, 9>()));
   PGS_TRY((set_merge_attr<K, V, 256, 13>()));
   PGS_TRY((set_merge_attr<K, V, 128, 17>()));
+  PGS_CUDA(cudaFuncSetAttribute(k_merge4<K, V, kMerge4NT, kMerge4VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes));
   PGS_CUDA(cudaFuncSetAttribute(k_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ScatterSmem<K>)));
   PGS_CUDA(cudaFuncSetAttribute(k_mlp_grad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -391,6 +420,31 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
       case 3: launch_merge_tile<K, V, 128, 17>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
       default: launch_merge_tile<K, V, 256, 9>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
     }
+  });
+}
+
+// One four-way round over quads already described in b.quads / b.ccount:
+// cuts, their order by rank, then one CTA per chunk.
+template <typename K, bool V>
+inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t nquads,
+                        uint64_t len, const Buffers& b, int f32_out, uint32_t step) {
+  PGS_TRY(scan_u64(c, b.ccount, b.coff, nquads, b.scan_sums, b.scan_sums2, step));
+  const uint64_t chunks_ub = ceil_div(len, kMerge4Cut) + nquads;
+  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, kMerge4Cut), [&] {
+    k_cuts4<K><<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(ks, b.quads, b.coff, nquads, b.cuts_a, kMerge4Cut);
+  }));
+  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 96 * ceil_div(len, kMerge4Cut), [&] {
+    k_cuts4_sort<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_a, b.quads, b.coff, nquads, b.cuts_b,
+                                                             kMerge4Cut);
+  }));
+  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 128 * ceil_div(len, kMerge4Cut), [&] {
+    k_chunks4<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_b, b.quads, b.coff, nquads, b.chunks4);
+  }));
+  const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
+  constexpr size_t smem = Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes;
+  return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
+    k_merge4<K, V, kMerge4NT, kMerge4VT><<<(unsigned)chunks_ub, kMerge4NT, smem, c.st>>>(
+        ks, vs, kd, vd, b.chunks4, b.coff + nquads, f32_out, b.err);
   });
 }
 
@@ -480,19 +534,36 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
     k_block_sort<K, V><<<(unsigned)((uint64_t)R * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
         kin, vin, cur_k, cur_v, b.run_off, tiles_per_run, f32, left == 0 ? f32 : 0);
   }));
-  // ... then balanced pairwise merge rounds (Fig. 2) until each run is one list.
-  for (int k = 0; k < sh.run_rounds; ++k) {
-    const uint64_t w = (uint64_t)kTile << k;
-    const uint64_t cmax = ceil_div(sh.maxlen, 2 * w);
-    const uint64_t np = cmax * R;
-    PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
-      k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, b.run_off, R, w, cmax,
-                                                      (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
-    }));
-    --left;
-    PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, n, b, left == 0 ? f32 : 0, 1)));
-    std::swap(cur_k, oth_k);
-    std::swap(cur_v, oth_v);
+  // ... then the balanced merge tree (Fig. 2) until each run is one list: two
+  // levels per pass (four-way rounds) while two remain, else a pairwise round.
+  {
+    uint64_t w = kTile;
+    int levels = sh.run_rounds;
+    while (levels > 0) {
+      --left;
+      if (sh.four && levels >= 2) {
+        const uint64_t cmax = ceil_div(sh.maxlen, 4 * w);
+        const uint64_t nq = cmax * R;
+        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 80 * nq, [&] {
+          k_quads_runs<<<grid_for(nq, 256), 256, 0, st>>>(b.quads, b.ccount, b.run_off, R, w, cmax, kMerge4Cut);
+        }));
+        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, n, b, left == 0 ? f32 : 0, 1)));
+        w *= 4;
+        levels -= 2;
+      } else {
+        const uint64_t cmax = ceil_div(sh.maxlen, 2 * w);
+        const uint64_t np = cmax * R;
+        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
+          k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, b.run_off, R, w, cmax,
+                                                          (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
+        }));
+        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, n, b, left == 0 ? f32 : 0, 1)));
+        w *= 2;
+        levels -= 1;
+      }
+      std::swap(cur_k, oth_k);
+      std::swap(cur_v, oth_v);
+    }
   }
 
   if (sh.Pmax > 1) {
@@ -567,16 +638,33 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       std::swap(cur_v, oth_v);
       k0 = 1;
     }
-    // Step 6: every bucket merges its P segments with the Fig. 2 schedule.
-    for (int k = k0; k < sh.bucket_rounds; ++k) {
-      const uint32_t step = 1u << k;
-      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * sh.Q, [&] {
-        k_pairs_bucket_lists<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, sh.Q, step, mtile);
-      }));
-      --left;
-      PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
-      std::swap(cur_k, oth_k);
-      std::swap(cur_v, oth_v);
+    // Step 6: every bucket merges its P segments with the Fig. 2 schedule,
+    // two levels per pass while two remain.
+    {
+      int levels = sh.bucket_rounds - k0;
+      uint32_t step = 1u << k0;
+      while (levels > 0) {
+        --left;
+        if (sh.four && levels >= 2) {
+          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * sh.Q, [&] {
+            k_quads_buckets<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, sh.Q, step,
+                                                                 kMerge4Cut);
+          }));
+          PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
+          step *= 4;
+          levels -= 2;
+        } else {
+          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * sh.Q, [&] {
+            k_pairs_bucket_lists<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, sh.Q, step,
+                                                                       mtile);
+          }));
+          PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
+          step *= 2;
+          levels -= 1;
+        }
+        std::swap(cur_k, oth_k);
+        std::swap(cur_v, oth_v);
+      }
     }
   } else {
     PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)R, [&] {

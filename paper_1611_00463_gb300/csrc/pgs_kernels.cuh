@@ -20,6 +20,9 @@ constexpr int kMergeNT = 256;        // threads per merge CTA (default shape)
 constexpr int kMergeVT = 9;          // outputs per merge thread (odd: conflict-free staging)
 constexpr int kMergeTile = kMergeNT * kMergeVT;   // 2304 outputs per merge tile
 constexpr int kMergeMinTile = 128 * 9;            // smallest tile of the tunable shapes
+constexpr int kMerge4NT = 256;                    // four-way rounds: threads per CTA
+constexpr int kMerge4VT = 9;                      // outputs per thread at most; a chunk holds <= 2304
+constexpr int kMerge4Cut = kMerge4NT * kMerge4VT / 2;   // X and Y are cut every 1152 elements
 constexpr int kScanNT = 1024;
 constexpr int kScanVT = 8;
 constexpr int kScanChunk = kScanNT * kScanVT;
@@ -497,6 +500,330 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
         bk = bi < nb ? sb[bi] : key_max<K>();
       }
     }
+  }
+  __syncthreads();
+  store_tile_vec<K, NT>(kdst + s_out, s_kout, cnt);
+  if (VALS) store_tile_vec<uint32_t, NT>(vdst + s_out, s_vout, cnt);
+}
+
+// ---------------------------------------------------------------------------
+// Four-way merge round: two levels of the Fig. 2 tree in one pass over HBM.
+// Lists A, B, C, D (in stable order) merge into X = merge(A, B), Y = merge(C,
+// D), then merge(X, Y).  The output is cut into chunks at every T-th element
+// of X and of Y (the way step 4 cuts runs at splitters): an X cut at X
+// position m takes the merge-path split of (A, B) at m, and its value's
+// lower bounds in C and D (equal keys of C and D come after it); a Y cut
+// takes the split of (C, D) and upper bounds in A and B.  Sorted by stable
+// rank, consecutive cuts bound a chunk with at most T elements of X and at
+// most T of Y, split exactly; a CTA merges the chunk's four pieces in shared
+// memory (A+B and C+D, then X+Y) and stores it.
+// ---------------------------------------------------------------------------
+
+struct Quad {                 // four lists in stable order -> [out, out + sum n)
+  uint64_t s[4];              // first element of each list
+  uint64_t n[4];              // list lengths
+  uint64_t out;
+};
+
+struct Cut4 {                 // a chunk boundary: its stable rank in the quad, the four list positions
+  uint64_t rank;
+  uint64_t p[4];
+  uint64_t quad;
+};
+
+__device__ __forceinline__ uint64_t quad_cuts(const Quad& q, uint32_t T) {
+  const uint64_t nx = q.n[0] + q.n[1], ny = q.n[2] + q.n[3];
+  if (nx + ny == 0) return 0;
+  const uint64_t cx = nx ? (nx + T - 1) / T - 1 : 0;
+  const uint64_t cy = ny ? (ny + T - 1) / T - 1 : 0;
+  return 1 + cx + cy;                                   // the start, X cuts, Y cuts
+}
+
+__device__ __forceinline__ void put_quad(Quad* quads, uint64_t* ccount, uint64_t p, const uint64_t b[5],
+                                         uint64_t out, uint32_t T) {
+  Quad q;
+  for (int i = 0; i < 4; ++i) {
+    q.s[i] = b[i];
+    q.n[i] = b[i + 1] - b[i];
+  }
+  q.out = out;
+  quads[p] = q;
+  ccount[p] = quad_cuts(q, T);
+}
+
+// Run formation: blocks [j 4w + i w, j 4w + (i+1) w) of every run, i = 0..3.
+static __global__ void k_quads_runs(Quad* quads, uint64_t* ccount, const uint64_t* __restrict__ run_off, uint32_t R,
+                                    uint64_t w, uint64_t cmax, uint32_t T) {
+  uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (p >= (uint64_t)R * cmax) return;
+  const uint64_t r = p / cmax, j = p % cmax;
+  const uint64_t rs = run_off[r], re = run_off[r + 1];
+  uint64_t b[5];
+  for (int i = 0; i < 5; ++i) b[i] = umin(rs + j * 4 * w + i * w, re);
+  put_quad(quads, ccount, p, b, b[0], T);
+}
+
+// Bucket merge: groups of `step` segments; group g of a bucket starts at
+// segment 4 g step (slot = global segment index; other slots empty).
+static __global__ void k_quads_buckets(Quad* quads, uint64_t* ccount, Geo g, const uint64_t* __restrict__ off,
+                                       uint64_t Q, uint32_t step, uint32_t T) {
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
+  const uint64_t P = g.P[i];
+  const uint64_t local = q - g.seg[i];
+  const uint64_t bk = local / P, j = local % P;
+  const uint64_t base = g.seg[i] + bk * P;
+  uint64_t b[5];
+  if (j % (4ull * step) != 0) {
+    for (int k = 0; k < 5; ++k) b[k] = off[base + P];
+  } else {
+    for (int k = 0; k < 5; ++k) b[k] = off[base + umin(j + (uint64_t)k * step, P)];
+  }
+  put_quad(quads, ccount, q, b, b[0], T);
+}
+
+template <typename K>
+__device__ __forceinline__ uint64_t lower_bound_g(const K* x, uint64_t n, K v) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] < v) lo = mid + 1; else hi = mid; }
+  return lo;
+}
+template <typename K>
+__device__ __forceinline__ uint64_t upper_bound_g(const K* x, uint64_t n, K v) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] <= v) lo = mid + 1; else hi = mid; }
+  return lo;
+}
+
+// One thread per cut (unsorted): local index 0 is the quad start, 1..cx the
+// X cuts at X positions T, 2T, ..., then the Y cuts.
+template <typename K>
+__global__ void k_cuts4(const K* __restrict__ src, const Quad* __restrict__ quads, const uint64_t* __restrict__ coff,
+                        uint64_t nquads, Cut4* cuts, uint32_t T) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= coff[nquads]) return;
+  const uint64_t qi = last_le<uint64_t>(coff, (uint32_t)nquads, t);
+  const Quad q = quads[qi];
+  const uint64_t l = t - coff[qi];
+  const uint64_t nx = q.n[0] + q.n[1], ny = q.n[2] + q.n[3];
+  const uint64_t cx = nx ? (nx + T - 1) / T - 1 : 0;
+  const K* A = src + q.s[0];
+  const K* B = src + q.s[1];
+  const K* C = src + q.s[2];
+  const K* D = src + q.s[3];
+  Cut4 c;
+  c.quad = qi;
+  if (l == 0) {
+    c.rank = 0;
+    c.p[0] = c.p[1] = c.p[2] = c.p[3] = 0;
+  } else if (l <= cx) {
+    const uint64_t m = l * T;
+    const uint64_t a = merge_path<K, uint64_t>(A, q.n[0], B, q.n[1], m);
+    const uint64_t b = m - a;
+    const bool from_a = a < q.n[0] && (b >= q.n[1] || A[a] <= B[b]);
+    const K v = from_a ? A[a] : B[b];
+    c.p[0] = a;
+    c.p[1] = b;
+    c.p[2] = lower_bound_g<K>(C, q.n[2], v);
+    c.p[3] = lower_bound_g<K>(D, q.n[3], v);
+    c.rank = m + c.p[2] + c.p[3];
+  } else {
+    const uint64_t m = (l - cx) * T;
+    const uint64_t cc = merge_path<K, uint64_t>(C, q.n[2], D, q.n[3], m);
+    const uint64_t d = m - cc;
+    const bool from_c = cc < q.n[2] && (d >= q.n[3] || C[cc] <= D[d]);
+    const K v = from_c ? C[cc] : D[d];
+    c.p[2] = cc;
+    c.p[3] = d;
+    c.p[0] = upper_bound_g<K>(A, q.n[0], v);
+    c.p[1] = upper_bound_g<K>(B, q.n[1], v);
+    c.rank = m + c.p[0] + c.p[1];
+  }
+  cuts[t] = c;
+}
+
+// Sort the cuts of every quad by rank: X cuts and Y cuts are each in rank
+// order already, so a cut's place is its own index plus the number of the
+// other side's cuts of smaller rank (ranks are distinct: they are the stable
+// ranks of distinct elements).
+static __global__ void k_cuts4_sort(const Cut4* __restrict__ in, const Quad* __restrict__ quads,
+                                    const uint64_t* __restrict__ coff, uint64_t nquads, Cut4* out, uint32_t T) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= coff[nquads]) return;
+  const Cut4 c = in[t];
+  const uint64_t qi = c.quad;
+  const uint64_t base = coff[qi];
+  const uint64_t l = t - base;
+  if (l == 0) {
+    out[base] = c;
+    return;
+  }
+  const Quad q = quads[qi];
+  const uint64_t nx = q.n[0] + q.n[1];
+  const uint64_t cx = nx ? (nx + T - 1) / T - 1 : 0;
+  const uint64_t ncut = coff[qi + 1] - base;
+  const uint64_t cy = ncut - 1 - cx;
+  // Other side: X cuts at [base+1, base+1+cx), Y cuts at [base+1+cx, base+ncut).
+  const bool is_x = l <= cx;
+  const Cut4* other = in + base + 1 + (is_x ? cx : 0);
+  const uint64_t no = is_x ? cy : cx;
+  uint64_t lo = 0, hi = no;                            // other cuts with rank < c.rank
+  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (other[mid].rank < c.rank) lo = mid + 1; else hi = mid; }
+  const uint64_t own = is_x ? l - 1 : l - 1 - cx;
+  out[base + 1 + own + lo] = c;
+}
+
+struct Chunk4 {               // one chunk of a four-way round: the four source ranges and the output start
+  uint64_t s[4];
+  uint32_t n[4];
+  uint64_t out;
+};
+
+// Chunk t spans sorted cuts t and t+1 (or the quad's end).
+static __global__ void k_chunks4(const Cut4* __restrict__ cuts, const Quad* __restrict__ quads,
+                                 const uint64_t* __restrict__ coff, uint64_t nquads, Chunk4* chunks) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= coff[nquads]) return;
+  const Cut4 lo = cuts[t];
+  const Quad q = quads[lo.quad];
+  const bool last = t + 1 >= coff[lo.quad + 1];
+  Chunk4 c;
+  for (int i = 0; i < 4; ++i) {
+    const uint64_t hi = last ? q.n[i] : cuts[t + 1].p[i];
+    c.s[i] = q.s[i] + lo.p[i];
+    c.n[i] = (uint32_t)(hi - lo.p[i]);
+  }
+  c.out = q.out + lo.rank;
+  chunks[t] = c;
+}
+
+template <typename K, bool VALS, int NT, int VT>
+struct Merge4Layout {
+  static constexpr int M = NT * VT;                                   // largest chunk (2 T)
+  static constexpr size_t kin = 16;
+  static constexpr size_t vin = kin + (size_t)M * sizeof(K) + 128;
+  static constexpr size_t kmid = vin + (VALS ? (size_t)M * 4 + 128 : 0);
+  static constexpr size_t vmid = kmid + (size_t)M * sizeof(K);
+  static constexpr size_t bytes = vmid + (VALS ? (size_t)M * 4 : 0);
+  static_assert(M % 4 == 0, "16-byte aligned staging");
+};
+
+// Merge VT outputs of merge(a[0..na), b[0..nb)) starting at output `diag` into
+// out[diag..]; payloads follow their keys (source payload arrays va, vb).
+template <typename K, bool VALS, int VT>
+__device__ __forceinline__ void merge_into(const K* a, const uint32_t* va, int na, const K* b, const uint32_t* vb,
+                                           int nb, int diag, int count, K* out, uint32_t* vout, int f32_out) {
+  if (count <= 0) return;
+  int ai = merge_path<K, int>(a, na, b, nb, diag);
+  int bi = diag - ai;
+  K ak = ai < na ? a[ai] : key_max<K>();
+  K bk = bi < nb ? b[bi] : key_max<K>();
+#pragma unroll
+  for (int j = 0; j < VT; ++j) {
+    if (j < count) {
+      const bool take_a = (bi >= nb) || (ai < na && ak <= bk);
+      out[diag + j] = from_order<K>(take_a ? ak : bk, f32_out);
+      if (VALS) vout[diag + j] = take_a ? va[ai] : vb[bi];
+      if (take_a) {
+        ++ai;
+        ak = ai < na ? a[ai] : key_max<K>();
+      } else {
+        ++bi;
+        bk = bi < nb ? b[bi] : key_max<K>();
+      }
+    }
+  }
+}
+
+template <typename K, bool VALS, int NT, int VT>
+__global__ void __launch_bounds__(NT)
+k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
+         uint32_t* __restrict__ vdst, const Chunk4* __restrict__ chunks, const uint64_t* __restrict__ total,
+         int f32_out, uint32_t* err) {
+  using L = Merge4Layout<K, VALS, NT, VT>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  char* s_kin = reinterpret_cast<char*>(smem_raw + L::kin);
+  char* s_vin = reinterpret_cast<char*>(smem_raw + L::vin);
+  K* s_kmid = reinterpret_cast<K*>(smem_raw + L::kmid);
+  uint32_t* s_vmid = reinterpret_cast<uint32_t*>(smem_raw + L::vmid);
+  __shared__ uint64_t s_lo[4], s_cnt[4], s_out;
+  __shared__ uint32_t s_off_k[4], s_off_v[4];
+  const uint64_t t = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    if (t < *total) {
+      const Chunk4 ch = chunks[t];
+      uint32_t kbytes = 0, vbytes = 0;
+      Span16 ks[4], vs[4];
+      for (int i = 0; i < 4; ++i) {
+        s_lo[i] = ch.s[i];
+        s_cnt[i] = ch.n[i];
+        ks[i] = widen16(ksrc + s_lo[i], (uint32_t)s_cnt[i]);
+        s_off_k[i] = kbytes + ks[i].skip * (uint32_t)sizeof(K);
+        kbytes += ks[i].bytes;
+        if (VALS) {
+          vs[i] = widen16(vsrc + s_lo[i], (uint32_t)s_cnt[i]);
+          s_off_v[i] = vbytes + vs[i].skip * 4u;
+          vbytes += vs[i].bytes;
+        }
+      }
+      s_out = ch.out;
+      mbar_init(bar, 1);
+      fence_barrier_init();
+      mbar_arrive_expect_tx(bar, kbytes + vbytes);
+      uint32_t ko = 0, vo = 0;
+      for (int i = 0; i < 4; ++i) {
+        if (ks[i].bytes) bulk_load(s_kin + ko, ks[i].base, ks[i].bytes, bar);
+        ko += ks[i].bytes;
+        if (VALS) {
+          if (vs[i].bytes) bulk_load(s_vin + vo, vs[i].base, vs[i].bytes, bar);
+          vo += vs[i].bytes;
+        }
+      }
+    } else {
+      for (int i = 0; i < 4; ++i) s_cnt[i] = 0;
+    }
+  }
+  __syncthreads();
+  const int na = (int)s_cnt[0], nb = (int)s_cnt[1], nc = (int)s_cnt[2], nd = (int)s_cnt[3];
+  const int nx = na + nb, ny = nc + nd, cnt = nx + ny;
+  if (cnt == 0) return;
+  if (!mbar_wait(bar, 0)) {
+    if (tid == 0) atomicOr(err, kErrWaitTimeout);
+    mbar_wait(bar, 0);
+    return;
+  }
+  const K* A = reinterpret_cast<const K*>(s_kin + s_off_k[0]);
+  const K* B = reinterpret_cast<const K*>(s_kin + s_off_k[1]);
+  const K* C = reinterpret_cast<const K*>(s_kin + s_off_k[2]);
+  const K* D = reinterpret_cast<const K*>(s_kin + s_off_k[3]);
+  const uint32_t* vA = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[0]) : nullptr;
+  const uint32_t* vB = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[1]) : nullptr;
+  const uint32_t* vC = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[2]) : nullptr;
+  const uint32_t* vD = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[3]) : nullptr;
+  // Every thread takes an equal share of the chunk (odd, so blocked staging
+  // writes stay conflict free), whatever the chunk's size.
+  const int per = ((cnt + NT - 1) / NT) | 1;
+  // Level 1: X = merge(A, B) into mid[0, nx), Y = merge(C, D) into mid[nx, cnt).
+  {
+    const int d0 = min(tid * per, cnt), d1 = min(d0 + per, cnt);
+    if (d0 < nx) merge_into<K, VALS, VT>(A, vA, na, B, vB, nb, d0, min(d1, nx) - d0, s_kmid, s_vmid, 0);
+    if (d1 > nx) {
+      const int y0 = max(d0, nx) - nx;
+      merge_into<K, VALS, VT>(C, vC, nc, D, vD, nd, y0, d1 - max(d0, nx), s_kmid + nx,
+                              VALS ? s_vmid + nx : nullptr, 0);
+    }
+  }
+  __syncthreads();
+  // Level 2: merge(X, Y) into the (now free) input staging.
+  K* s_kout = reinterpret_cast<K*>(s_kin);
+  uint32_t* s_vout = reinterpret_cast<uint32_t*>(s_vin);
+  {
+    const int d0 = min(tid * per, cnt);
+    merge_into<K, VALS, VT>(s_kmid, s_vmid, nx, s_kmid + nx, VALS ? s_vmid + nx : nullptr, ny, d0,
+                            min(per, cnt - d0), s_kout, s_vout, f32_out);
   }
   __syncthreads();
   store_tile_vec<K, NT>(kdst + s_out, s_kout, cnt);

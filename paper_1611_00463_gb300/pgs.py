@@ -46,6 +46,8 @@ class pgs_config(ctypes.Structure):
         ("timer", ctypes.c_void_p),
         ("model", ctypes.c_void_p),
         ("model_out", ctypes.c_void_p),
+        ("merge_ways", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
     ]
 
 
@@ -220,7 +222,7 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
                 cuts: torch.Tensor | None = None, splitters_out: torch.Tensor | None = None,
                 stats: torch.Tensor | None = None, timer: Timer | None = None,
                 model: torch.Tensor | None = None, model_out: torch.Tensor | None = None,
-                tile_variant: int = 0) -> pgs_config:
+                tile_variant: int = 0, merge_ways: int = 0) -> pgs_config:
     c = pgs_config()
     c.dtype = DTYPES[dtype]
     c.samples_per_run = samples_per_run
@@ -240,6 +242,7 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
     c.model = _ptr(model)
     c.model_out = _ptr(model_out)
     c.tile_variant = tile_variant
+    c.merge_ways = merge_ways
     return c
 
 

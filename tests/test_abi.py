@@ -45,7 +45,7 @@ def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(pgs.pgs_stats) == 64
     assert [lib.pgs_batch_auto_partitions(n) for n in [1, 65535, 65536, 131071, 131072, 1 << 24, 1 << 30]] == \
         [1, 1, 1, 1, 2, 256, 256]
-    assert ctypes.sizeof(pgs.pgs_config) == 32 + 8 * 10
+    assert ctypes.sizeof(pgs.pgs_config) == 32 + 8 * 11
     assert ctypes.sizeof(pgs.pgs_launch_record) == 24
     assert [lib.pgs_kernel_name(i).decode() for i in range(len(pgs.KERNELS))] == pgs.KERNELS
 
