@@ -125,11 +125,16 @@ def dist_env():
     return world, rank, local
 
 
-def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("pgs_kernels.cuh",):
-        with open(os.path.join(ROOT, "paper_1611_00463_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+def kernel_source_hash(kernel: str = "k_merge_tile") -> str:
+    """Hash of one kernel's source text (its template header to its closing
+    brace) plus the PTX helpers it uses, so committed counters are used only
+    for the kernel they were taken on."""
+    src = open(os.path.join(ROOT, "paper_1611_00463_gb300", "csrc", "pgs_kernels.cuh")).read()
+    start = src.index(kernel + "(")
+    start = src.rfind("template", 0, start)
+    end = src.index("\n}\n", start) + 3
+    h = hashlib.sha256(src[start:end].encode())
+    h.update(open(os.path.join(ROOT, "paper_1611_00463_gb300", "csrc", "pgs_ptx.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -139,13 +144,14 @@ def profiled_traffic(kernel: str, workload: str, n: int):
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     if not os.path.exists(path):
         return None
+    src_kernel = {"merge": "k_merge_tile", "block_sort": "k_block_sort"}.get(kernel, kernel)
     vals = {}
     for ln in open(path):
         if ":" in ln and not ln.startswith("#"):
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
     try:
-        if vals.get("source_hash") != kernel_source_hash():
+        if vals.get("source_hash") != kernel_source_hash(src_kernel):
             return None
         per_key = float(vals["dram_bytes_per_launch"]) / float(vals["keys_per_launch"])
         return per_key * n
