@@ -113,7 +113,7 @@ typedef struct pgs_config {
   int32_t  exchange;          /* pgs_exchange, default AUTO */
   int32_t  splitter_mode;     /* pgs_splitter_mode, default SAMPLED */
   int32_t  tile_variant;      /* merge tile shape, 0..PGS_TILE_VARIANTS-1 (threads x outputs per thread:
-                                 0 = 256 x 9 (default), 1 = 128 x 9, 2 = 256 x 13, 3 = 128 x 17);
+                                 0 = 128 x 17 (default), 1 = 256 x 13, 2 = 128 x 9, 3 = 64 x 17);
                                  pgs_batch_tune picks one for a batch */
   void*    workspace;         /* device, 256-byte aligned, >= pgs_workspace_bytes(n, P, cfg) */
   uint64_t workspace_bytes;

@@ -363,7 +363,7 @@ inline int scan_u64(Ctx& c, const uint64_t* in, uint64_t* out, uint64_t m, uint6
 // Merge tile shapes the tuner chooses from (threads x outputs per thread);
 // variant 0 is the default.
 struct MergeShape { int nt, vt; };
-constexpr MergeShape kMergeShapes[PGS_TILE_VARIANTS] = {{256, 9}, {128, 9}, {256, 13}, {128, 17}};
+constexpr MergeShape kMergeShapes[PGS_TILE_VARIANTS] = {{128, 17}, {256, 13}, {128, 9}, {64, 17}};
 
 template <typename K, bool V, int NT, int VT>
 inline int set_merge_attr() {
@@ -378,10 +378,10 @@ template <typename K, bool V>
 inline int set_smem_attrs() {
   PGS_CUDA(cudaFuncSetAttribute(k_block_sort<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(BlockSortSmem<K>)));
-  PGS_TRY((set_merge_attr<K, V, 256, 9>()));
-  PGS_TRY((set_merge_attr<K, V, 128, 9>()));
-  PGS_TRY((set_merge_attr<K, V, 256, 13>()));
-  PGS_TRY((set_merge_attr<K, V, 128, 17>()));
+  PGS_TRY((set_merge_attr<K, V, kMergeShapes[0].nt, kMergeShapes[0].vt>()));
+  PGS_TRY((set_merge_attr<K, V, kMergeShapes[1].nt, kMergeShapes[1].vt>()));
+  PGS_TRY((set_merge_attr<K, V, kMergeShapes[2].nt, kMergeShapes[2].vt>()));
+  PGS_TRY((set_merge_attr<K, V, kMergeShapes[3].nt, kMergeShapes[3].vt>()));
   PGS_CUDA(cudaFuncSetAttribute(k_merge4<K, V, kMerge4NT, kMerge4VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes));
   PGS_CUDA(cudaFuncSetAttribute(k_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -415,10 +415,12 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
   const uint64_t* total = b.tbegin + npairs;
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     switch (c.variant) {
-      case 1: launch_merge_tile<K, V, 128, 9>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
-      case 2: launch_merge_tile<K, V, 256, 13>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
-      case 3: launch_merge_tile<K, V, 128, 17>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
-      default: launch_merge_tile<K, V, 256, 9>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+#define PGS_MERGE_SHAPE(i) kMergeShapes[i].nt, kMergeShapes[i].vt
+      case 1: launch_merge_tile<K, V, PGS_MERGE_SHAPE(1)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+      case 2: launch_merge_tile<K, V, PGS_MERGE_SHAPE(2)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+      case 3: launch_merge_tile<K, V, PGS_MERGE_SHAPE(3)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+      default: launch_merge_tile<K, V, PGS_MERGE_SHAPE(0)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+#undef PGS_MERGE_SHAPE
     }
   });
 }
