@@ -111,27 +111,25 @@ __device__ __forceinline__ I merge_path(const K* a, I na, const K* b, I nb, I di
   return lo;
 }
 
-// Merge up to `count` items of two sorted ranges of one smem array, A = [ai, a_end)
-// and B = [bi, b_end), into registers.  pos[] receives the smem index of each item.
+// Merge VT items of two sorted ranges of one smem array, A = [ai, a_end) and
+// B = [bi, b_end), into registers (ties take A, so the merge is stable);
+// pos[] receives the smem index of each item.  One shared-memory read per
+// item: the next key of whichever list advanced.  That read may land one slot
+// past a range's end; the caller keeps that slot inside the array, and the
+// index tests, not the key read there, decide.
 template <typename K, int VT>
 __device__ __forceinline__ void serial_merge(const K* s, int ai, int a_end, int bi, int b_end,
-                                             int count, K (&key)[VT], int (&pos)[VT]) {
-  K ak = ai < a_end ? s[ai] : key_max<K>();
-  K bk = bi < b_end ? s[bi] : key_max<K>();
+                                             K (&key)[VT], int (&pos)[VT]) {
+  K ak = s[ai];
+  K bk = s[bi];
 #pragma unroll
   for (int j = 0; j < VT; ++j) {
-    if (j < count) {
-      bool take_a = (bi >= b_end) || (ai < a_end && ak <= bk);
-      key[j] = take_a ? ak : bk;
-      pos[j] = take_a ? ai : bi;
-      if (take_a) {
-        ++ai;
-        ak = ai < a_end ? s[ai] : key_max<K>();
-      } else {
-        ++bi;
-        bk = bi < b_end ? s[bi] : key_max<K>();
-      }
-    }
+    const bool take_b = (bi < b_end) && ((ai >= a_end) || (bk < ak));
+    key[j] = take_b ? bk : ak;
+    pos[j] = take_b ? bi : ai;
+    if (take_b) ++bi; else ++ai;
+    const K nx = s[take_b ? bi : ai];
+    if (take_b) bk = nx; else ak = nx;
   }
 }
 
@@ -145,8 +143,8 @@ __device__ __forceinline__ void serial_merge(const K* s, int ai, int a_end, int 
 
 template <typename K>
 struct BlockSortSmem {
-  K keys[kTile];
-  uint16_t ids[kTile];
+  K keys[kTile + 1];      // + one slot the serial merge may read past the last list
+  uint16_t ids[kTile + 8];
   uint32_t vals[kTile];
 };
 
@@ -170,6 +168,7 @@ k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kou
     sm.keys[idx] = idx < cnt ? to_order<K>(kin[g0 + idx], f32_in) : key_max<K>();
     if (VALS) sm.vals[idx] = idx < cnt ? vin[g0 + idx] : 0u;
   }
+  if (tid == 0) sm.keys[kTile] = key_max<K>();
   __syncthreads();
 
   K key[kVT];
@@ -190,22 +189,26 @@ k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kou
       }
     }
   }
-  // Pairwise merge rounds (Fig. 2): coop threads share one merged list.
+  // Pairwise merge rounds (Fig. 2): coop threads share one merged list.  While
+  // a list pair lies inside one warp (coop <= 32) a warp barrier is enough: a
+  // thread only reads slots of its own group, besides the one slot past its
+  // B list, whose key is never used.
+#pragma unroll 1
   for (int coop = 2; coop <= kNT; coop *= 2) {
-    __syncthreads();
+    if (coop <= 64) __syncwarp(); else __syncthreads();    // last round's reads stayed in coop/2 threads
 #pragma unroll
     for (int j = 0; j < kVT; ++j) {
       sm.keys[tid * kVT + j] = key[j];
       sm.ids[tid * kVT + j] = (uint16_t)pos[j];
     }
-    __syncthreads();
+    if (coop <= 32) __syncwarp(); else __syncthreads();
     const int half = (coop / 2) * kVT;
     const int start = (tid & ~(coop - 1)) * kVT;
     const int diag = (tid & (coop - 1)) * kVT;
     const int a = merge_path<K, int>(sm.keys + start, half, sm.keys + start + half, half, diag);
     int spos[kVT];
     serial_merge<K, kVT>(sm.keys, start + a, start + half, start + half + (diag - a), start + 2 * half,
-                         kVT, key, spos);
+                         key, spos);
 #pragma unroll
     for (int j = 0; j < kVT; ++j) pos[j] = sm.ids[spos[j]];
   }
