@@ -482,23 +482,23 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
   const int mine = min(VT, cnt - diag);
   int ai = merge_path<K, int>(sa, na, sb, nb, diag);
   int bi = diag - ai;
-  K ak = ai < na ? sa[ai] : key_max<K>();
-  K bk = bi < nb ? sb[bi] : key_max<K>();
+  // One shared-memory read per output for the key (the list that advanced) and
+  // one for the payload.  A key read may land one slot past A's end (inside
+  // B's copy) or past B's end (inside the 64-byte slack of the key buffer);
+  // the index tests decide, never that key.
+  K ak = sa[ai];
+  K bk = sb[bi];
   K ok[VT];
   uint32_t ov[VT];
 #pragma unroll
   for (int j = 0; j < VT; ++j) {
     if (j < mine) {
-      const bool take_a = (bi >= nb) || (ai < na && ak <= bk);
-      ok[j] = from_order<K>(take_a ? ak : bk, f32_out);
-      if (VALS) ov[j] = take_a ? sva[ai] : svb[bi];
-      if (take_a) {
-        ++ai;
-        ak = ai < na ? sa[ai] : key_max<K>();
-      } else {
-        ++bi;
-        bk = bi < nb ? sb[bi] : key_max<K>();
-      }
+      const bool take_b = (bi < nb) && ((ai >= na) || (bk < ak));
+      ok[j] = from_order<K>(take_b ? bk : ak, f32_out);
+      if (VALS) ov[j] = *(take_b ? svb + bi : sva + ai);
+      if (take_b) ++bi; else ++ai;
+      const K nx = *(take_b ? sb + bi : sa + ai);
+      if (take_b) bk = nx; else ak = nx;
     }
   }
   __syncthreads();                                      // every thread is done reading the inputs
