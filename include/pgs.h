@@ -145,7 +145,8 @@ typedef struct pgs_stats {
   uint64_t min_bucket;        /* min_b (e_{b+1} - e_b) */
   uint32_t splitter_mode;     /* mode that produced the buckets */
   uint32_t fallback;          /* LEARNED: 1 if the sampled splitters replaced the model's */
-  uint32_t error;             /* device-side error word; 0 = none */
+  uint32_t error;             /* device-side error word; 0 = none, bit 0 = a bounded wait expired,
+                                 bit 1 = a merge tile did not fit its buffer (skipped) */
   uint32_t passes;            /* full passes over the data the sort made */
   uint32_t launches;          /* kernels the call launched */
   float    max_over_mean;     /* largest bucket / its instance's mean bucket n_i / P_i */
@@ -257,7 +258,8 @@ int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
                       const pgs_config* cfg, void* splitters_out, float* model_out);
 
 /* Copy a device pgs_stats to host memory; synchronises `stream` and returns
- * PGS_ERR_TIMEOUT if the device error word reports an expired wait. */
+ * PGS_ERR_TIMEOUT if the device error word reports an expired wait, PGS_ERR_CUDA
+ * if it reports any other device-side inconsistency. */
 int pgs_get_stats(const void* stats_dev, pgs_stats* host_out, void* stream);
 
 /* Launch timer.  pgs_timer_create makes a host object with room for

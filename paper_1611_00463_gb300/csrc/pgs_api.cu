@@ -111,7 +111,8 @@ int pgs_get_stats(const void* stats_dev, pgs_stats* host_out, void* stream) {
   if (cudaMemcpyAsync(host_out, stats_dev, sizeof(pgs_stats), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PGS_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PGS_ERR_CUDA;
-  if (host_out->error) return PGS_ERR_TIMEOUT;
+  if (host_out->error & kErrWaitTimeout) return PGS_ERR_TIMEOUT;
+  if (host_out->error) return PGS_ERR_CUDA;
   return PGS_OK;
 }
 

@@ -440,7 +440,8 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
                                                              kMerge4Cut);
   }));
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 128 * ceil_div(len, kMerge4Cut), [&] {
-    k_chunks4<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_b, b.quads, b.coff, nquads, b.chunks4);
+    k_chunks4<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_b, b.quads, b.coff, nquads, b.chunks4,
+                                                          2 * kMerge4Cut, b.err);
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
   constexpr size_t smem = Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes;

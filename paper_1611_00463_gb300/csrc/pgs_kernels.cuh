@@ -435,8 +435,14 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
         nx = split[tile + 1];
         same = nx.pair == t.pair;
       }
-      na = (uint32_t)((same ? nx.a : t.a_end) - t.a);
-      nb = (uint32_t)((same ? nx.b : t.b_end) - t.b);
+      const uint64_t a_hi = same ? nx.a : t.a_end, b_hi = same ? nx.b : t.b_end;
+      if (a_hi < t.a || b_hi < t.b || (a_hi - t.a) + (b_hi - t.b) > (uint64_t)L::T) {
+        atomicOr(err, kErrBadTile);                     // inconsistent split: skip the tile, never copy
+        t = TileSplit{};
+      } else {
+        na = (uint32_t)(a_hi - t.a);
+        nb = (uint32_t)(b_hi - t.b);
+      }
       const Span16 ka = widen16(ksrc + t.a, na), kb = widen16(ksrc + t.b, nb);
       Span16 va{nullptr, 0, 0}, vb{nullptr, 0, 0};
       if (VALS) {
@@ -690,19 +696,30 @@ struct Chunk4 {               // one chunk of a four-way round: the four source 
   uint64_t out;
 };
 
-// Chunk t spans sorted cuts t and t+1 (or the quad's end).
+// Chunk t spans sorted cuts t and t+1 (or the quad's end).  A chunk whose
+// pieces would not be ranges of their lists or would not fit max_chunk
+// elements (impossible for sorted lists) is emptied and flagged.
 static __global__ void k_chunks4(const Cut4* __restrict__ cuts, const Quad* __restrict__ quads,
-                                 const uint64_t* __restrict__ coff, uint64_t nquads, Chunk4* chunks) {
+                                 const uint64_t* __restrict__ coff, uint64_t nquads, Chunk4* chunks,
+                                 uint32_t max_chunk, uint32_t* err) {
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= coff[nquads]) return;
   const Cut4 lo = cuts[t];
   const Quad q = quads[lo.quad];
   const bool last = t + 1 >= coff[lo.quad + 1];
   Chunk4 c;
+  uint64_t sum = 0;
+  bool bad = false;
   for (int i = 0; i < 4; ++i) {
     const uint64_t hi = last ? q.n[i] : cuts[t + 1].p[i];
+    bad = bad || hi < lo.p[i] || hi > q.n[i];
     c.s[i] = q.s[i] + lo.p[i];
     c.n[i] = (uint32_t)(hi - lo.p[i]);
+    sum += hi - lo.p[i];
+  }
+  if (bad || sum > max_chunk) {
+    atomicOr(err, kErrBadTile);
+    for (int i = 0; i < 4; ++i) { c.s[i] = q.s[i]; c.n[i] = 0; }
   }
   c.out = q.out + lo.rank;
   chunks[t] = c;

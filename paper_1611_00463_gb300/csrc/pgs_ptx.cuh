@@ -8,6 +8,7 @@ namespace pgs {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: far above any legitimate wait
 constexpr uint32_t kErrWaitTimeout = 1u;           // error word bit: a bounded wait expired
+constexpr uint32_t kErrBadTile = 2u;               // error word bit: a merge tile did not fit its buffer
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
