@@ -173,6 +173,28 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out,
                   uint32_t* vals_out, uint64_t n, uint32_t P, void* stream,
                   const pgs_config* cfg);
 
+/* Bytes of device workspace pgs_sort_host needs: pgs_workspace_bytes plus the
+ * device copies of input and output.  Returns 0 for an invalid request. */
+size_t pgs_host_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg);
+
+/* Sort host-resident keys (and payloads) out of place through the device: the
+ * same sort as pgs_sort_copy, with the copies inside the call.
+ *   keys_in/vals_in, keys_out/vals_out: host memory (pinned memory moves at the
+ *   link's full rate; pageable memory works, slower); vals both NULL or both
+ *   non-NULL; inputs and outputs must not overlap.  Device pointers are
+ *   PGS_ERR_INVALID.  cfg->workspace (device, on the GPU that sorts) must hold
+ *   pgs_host_workspace_bytes(n, P, cfg).
+ *   The input is copied in up to 8 groups of whole runs on a stream of the
+ *   call's own, and step 1 of a group starts as soon as its copy has landed,
+ *   while later groups are still copying; the sorted output is copied back on
+ *   `stream` after step 6.  Asynchronous on `stream` for pinned memory:
+ *   synchronise it before reading the outputs.  The paper has no counterpart
+ *   (its data starts in each machine's memory); this is the host-to-host form
+ *   of pgs_sort_copy. */
+int pgs_sort_host(const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                  uint32_t* vals_out, uint64_t n, uint32_t P, void* stream,
+                  const pgs_config* cfg);
+
 /* pgs_sort without a workspace, for callers that cannot allocate device
  * memory (an allocator or memory-pool callback, a plug-in whose host owns all
  * device allocations, a path that must never wait on the driver's allocator).

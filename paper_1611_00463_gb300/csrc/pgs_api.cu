@@ -9,6 +9,8 @@
 namespace pgs {
 int sort_u32(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
 int sort_u64(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int sort_host_u32(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
+int sort_host_u64(const Shape&, const Options&, const void*, const uint32_t*, void*, uint32_t*, cudaStream_t);
 int fit_u32(uint64_t, uint32_t, const Options&, const void*, void*, float*, cudaStream_t);
 int fit_u64(uint64_t, uint32_t, const Options&, const void*, void*, float*, cudaStream_t);
 
@@ -26,6 +28,16 @@ int use_device_of(const void* ptr) {
   if (cudaGetDevice(&cur) != cudaSuccess) return PGS_ERR_CUDA;
   if (cur != a.device && cudaSetDevice(a.device) != cudaSuccess) return PGS_ERR_CUDA;
   return PGS_OK;
+}
+
+// Host memory (pinned or pageable), not a device allocation.
+bool is_host_pointer(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
 bool ranges_overlap(const void* a, const void* b, uint64_t bytes) {
@@ -77,6 +89,41 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out, 
 
 int pgs_sort(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream, const pgs_config* cfg) {
   return pgs_sort_copy(keys, vals, keys, vals, n, P, stream, cfg);
+}
+
+size_t pgs_host_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg) {
+  Options o;
+  if (read_options(cfg, &o) != PGS_OK || P == 0) return 0;
+  Shape p = single_shape(n, P, true, o);
+  if (p.Pmax > kMaxP) return 0;
+  return host_layout(p).total;
+}
+
+int pgs_sort_host(const void* keys_in, const uint32_t* vals_in, void* keys_out, uint32_t* vals_out, uint64_t n,
+                  uint32_t P, void* stream, const pgs_config* cfg) {
+  Options o;
+  int rc = read_options(cfg, &o);
+  if (rc) return rc;
+  if (P == 0) return PGS_ERR_INVALID;
+  if ((vals_in == nullptr) != (vals_out == nullptr)) return PGS_ERR_INVALID;
+  if (n == 0) return PGS_OK;
+  if (!keys_in || !keys_out) return PGS_ERR_INVALID;
+  if (n >= (1ull << 40)) return PGS_ERR_UNSUPPORTED;
+  const int w = key_bytes(o.dtype);
+  if (!is_host_pointer(keys_in) || !is_host_pointer(keys_out)) return PGS_ERR_INVALID;
+  if (vals_in && (!is_host_pointer(vals_in) || !is_host_pointer(vals_out))) return PGS_ERR_INVALID;
+  if (ranges_overlap(keys_in, keys_out, n * (uint64_t)w)) return PGS_ERR_INVALID;
+  if (vals_in && ranges_overlap(vals_in, vals_out, n * 4ull)) return PGS_ERR_INVALID;
+  Shape p = single_shape(n, P, vals_in != nullptr, o);
+  if (p.Pmax > kMaxP) return PGS_ERR_UNSUPPORTED;
+  const size_t need = host_layout(p).total;
+  if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
+    return PGS_ERR_WORKSPACE;
+  rc = use_device_of(o.workspace);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (o.dtype == PGS_U64) return sort_host_u64(p, o, keys_in, vals_in, keys_out, vals_out, st);
+  return sort_host_u32(p, o, keys_in, vals_in, keys_out, vals_out, st);
 }
 
 size_t pgs_fit_workspace_bytes(uint64_t m, uint32_t P, const pgs_config* cfg) {

@@ -509,11 +509,24 @@ int set_all_smem_attrs() {
   return set_smem_attrs<K, false>();          // the sample sort runs keys only
 }
 
+// Run r's first key, computed as the device computes it (run_start).
+inline uint64_t host_run_start(uint64_t r, uint64_t n, uint64_t P) { return (r * n) / P; }
+
+// Host-buffer sorts: the input reaches the device in groups of whole runs on a
+// copy stream; group g's copy records ev[g], and its step-1 work waits for
+// that event only, so later groups copy while earlier ones sort.
+constexpr uint32_t kHostGroups = 8;
+struct HostGroups {
+  uint32_t groups = 0;                 // 0: the input is already on the device
+  uint32_t r0[kHostGroups + 1] = {};   // runs [r0[g], r0[g+1]) form group g
+  cudaEvent_t ev[kHostGroups] = {};
+};
+
 // The launch sequence itself (no attribute or allocation calls, so it can be
 // captured into a CUDA graph once set_all_smem_attrs has run on the device).
 template <typename K, bool V>
 int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
-                 Ctx& c, const Buffers& b) {
+                 Ctx& c, const Buffers& b, const HostGroups* hg = nullptr) {
   cudaStream_t st = c.st;
   c.variant = o.tile_variant;
   const Geo g = b.geo(sh);
@@ -533,39 +546,57 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
 
   // Step 1: local sort of every run.  Block sort of kTile tiles ...
   const uint32_t tiles_per_run = (uint32_t)std::max<uint64_t>(1, ceil_div(sh.maxlen, kTile));
-  PGS_TRY(launch(c, PGS_KERNEL_BLOCK_SORT, 1, 2 * n * kv, [&] {
-    k_block_sort<K, V><<<(unsigned)((uint64_t)R * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
-        kin, vin, cur_k, cur_v, b.run_off, tiles_per_run, f32, left == 0 ? f32 : 0);
-  }));
-  // ... then the balanced merge tree (Fig. 2) until each run is one list: two
-  // levels per pass (four-way rounds) while two remain, else a pairwise round.
-  {
+  // Runs [r0, r0 + Rg) holding len keys; every group goes through the same rounds.
+  auto sort_runs = [&](uint32_t r0, uint32_t Rg, uint64_t len) -> int {
+    const uint64_t* ro = b.run_off + r0;
+    PGS_TRY(launch(c, PGS_KERNEL_BLOCK_SORT, 1, 2 * len * kv, [&] {
+      k_block_sort<K, V><<<(unsigned)((uint64_t)Rg * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
+          kin, vin, cur_k, cur_v, ro, tiles_per_run, f32, left == 0 ? f32 : 0);
+    }));
+    // ... then the balanced merge tree (Fig. 2) until each run is one list: two
+    // levels per pass (four-way rounds) while two remain, else a pairwise round.
     uint64_t w = kTile;
     int levels = sh.run_rounds;
     while (levels > 0) {
       --left;
       if (sh.four && levels >= 2) {
         const uint64_t cmax = ceil_div(sh.maxlen, 4 * w);
-        const uint64_t nq = cmax * R;
+        const uint64_t nq = cmax * Rg;
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 80 * nq, [&] {
-          k_quads_runs<<<grid_for(nq, 256), 256, 0, st>>>(b.quads, b.ccount, b.run_off, R, w, cmax, kMerge4Cut);
+          k_quads_runs<<<grid_for(nq, 256), 256, 0, st>>>(b.quads, b.ccount, ro, Rg, w, cmax, kMerge4Cut);
         }));
-        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, n, b, left == 0 ? f32 : 0, 1)));
+        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, len, b, left == 0 ? f32 : 0, 1)));
         w *= 4;
         levels -= 2;
       } else {
         const uint64_t cmax = ceil_div(sh.maxlen, 2 * w);
-        const uint64_t np = cmax * R;
+        const uint64_t np = cmax * Rg;
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
-          k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, b.run_off, R, w, cmax,
+          k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, ro, Rg, w, cmax,
                                                           (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
         }));
-        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, n, b, left == 0 ? f32 : 0, 1)));
+        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, len, b, left == 0 ? f32 : 0, 1)));
         w *= 2;
         levels -= 1;
       }
       std::swap(cur_k, oth_k);
       std::swap(cur_v, oth_v);
+    }
+    return PGS_OK;
+  };
+  if (hg == nullptr || hg->groups == 0) {
+    PGS_TRY(sort_runs(0, R, n));
+  } else {
+    K* const ck = cur_k;
+    K* const okk = oth_k;
+    uint32_t* const cv = cur_v;
+    uint32_t* const ov = oth_v;
+    const int left0 = left;
+    for (uint32_t gi = 0; gi < hg->groups; ++gi) {
+      cur_k = ck; oth_k = okk; cur_v = cv; oth_v = ov; left = left0;
+      const uint32_t r0 = hg->r0[gi], r1 = hg->r0[gi + 1];
+      PGS_CUDA(cudaStreamWaitEvent(st, hg->ev[gi], 0));
+      PGS_TRY(sort_runs(r0, r1 - r0, host_run_start(r1, n, R) - host_run_start(r0, n, R)));
     }
   }
 
@@ -704,6 +735,88 @@ int run_sort(const Shape& sh, const Options& o, const K* kin, const uint32_t* vi
                                                           b.run_inst, sh.n, P, sh.s);
   }));
   return run_pipeline<K, V>(sh, o, kin, vin, kout, vout, c, b);
+}
+
+// ---------------------------------------------------------------------------
+// pgs_sort_host: a single sort of host-resident keys and payloads.  The device
+// copies of input and output follow the sort's own buffers in the workspace.
+// ---------------------------------------------------------------------------
+
+struct HostLayout {
+  size_t kin = 0, vin = 0, kout = 0, vout = 0, total = 0;
+};
+
+inline HostLayout host_layout(const Shape& sh) {
+  Buffers b;
+  const size_t used = carve(sh, nullptr, &b);
+  auto al = [](size_t x) { return (x + kAlign - 1) / kAlign * kAlign; };
+  const size_t kb = (size_t)sh.n * sh.w, vb = sh.vals ? (size_t)sh.n * 4 : 0;
+  HostLayout L;
+  L.kin = al(used);
+  L.vin = al(L.kin + kb);
+  L.kout = al(L.vin + vb);
+  L.vout = al(L.kout + kb);
+  L.total = L.vout + vb;
+  return L;
+}
+
+// Copy stream and events of one host-buffer sort, released when the call
+// returns (the runtime frees them once their pending work has finished).
+struct HostCopies {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t start = nullptr;
+  HostGroups hg;
+  ~HostCopies() {
+    for (uint32_t g = 0; g < kHostGroups; ++g)
+      if (hg.ev[g]) cudaEventDestroy(hg.ev[g]);
+    if (start) cudaEventDestroy(start);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+template <typename K, bool V>
+int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t* hv, K* hko, uint32_t* hvo,
+                  cudaStream_t st) {
+  PGS_TRY((set_all_smem_attrs<K, V>()));
+  Ctx c;
+  c.st = st;
+  c.timer = o.timer;
+  Buffers b;
+  carve(sh, o.workspace, &b);
+  const HostLayout L = host_layout(sh);
+  char* ws = static_cast<char*>(o.workspace);
+  K* dki = reinterpret_cast<K*>(ws + L.kin);
+  K* dko = reinterpret_cast<K*>(ws + L.kout);
+  uint32_t* dvi = V ? reinterpret_cast<uint32_t*>(ws + L.vin) : nullptr;
+  uint32_t* dvo = V ? reinterpret_cast<uint32_t*>(ws + L.vout) : nullptr;
+  const uint64_t n = sh.n;
+  const uint32_t R = sh.R;
+  HostCopies hc;
+  HostGroups& hg = hc.hg;
+  hg.groups = std::min<uint32_t>(kHostGroups, R);
+  for (uint32_t g = 0; g <= hg.groups; ++g) hg.r0[g] = (uint32_t)(((uint64_t)g * R) / hg.groups);
+  PGS_CUDA(cudaStreamCreateWithFlags(&hc.cs, cudaStreamNonBlocking));
+  PGS_CUDA(cudaEventCreateWithFlags(&hc.start, cudaEventDisableTiming));
+  for (uint32_t g = 0; g < hg.groups; ++g) PGS_CUDA(cudaEventCreateWithFlags(&hg.ev[g], cudaEventDisableTiming));
+  // The copies may overwrite the workspace only after earlier work on `st`.
+  PGS_CUDA(cudaEventRecord(hc.start, st));
+  PGS_CUDA(cudaStreamWaitEvent(hc.cs, hc.start, 0));
+  for (uint32_t g = 0; g < hg.groups; ++g) {
+    const uint64_t e0 = host_run_start(hg.r0[g], n, R), e1 = host_run_start(hg.r0[g + 1], n, R);
+    if (e1 > e0) {
+      PGS_CUDA(cudaMemcpyAsync(dki + e0, hk + e0, (e1 - e0) * sizeof(K), cudaMemcpyHostToDevice, hc.cs));
+      if (V) PGS_CUDA(cudaMemcpyAsync(dvi + e0, hv + e0, (e1 - e0) * 4, cudaMemcpyHostToDevice, hc.cs));
+    }
+    PGS_CUDA(cudaEventRecord(hg.ev[g], hc.cs));
+  }
+  PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 0, 16 * (uint64_t)(R + 1), [&] {
+    k_tables_single<<<grid_for(R + 1, 256), 256, 0, st>>>(b.koff, b.Pt, b.R0, b.mat, b.seg, b.st, b.run_off,
+                                                          b.run_inst, n, R, sh.s);
+  }));
+  PGS_TRY((run_pipeline<K, V>(sh, o, dki, dvi, dko, dvo, c, b, &hg)));
+  PGS_CUDA(cudaMemcpyAsync(hko, dko, n * sizeof(K), cudaMemcpyDeviceToHost, st));
+  if (V) PGS_CUDA(cudaMemcpyAsync(hvo, dvo, n * 4, cudaMemcpyDeviceToHost, st));
+  return PGS_OK;
 }
 
 // ---------------------------------------------------------------------------

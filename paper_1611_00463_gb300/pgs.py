@@ -80,6 +80,9 @@ EXPORTS = {
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "pgs_sort_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_host_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
+    "pgs_sort_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "pgs_fit_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
     "pgs_fit_splitters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -171,6 +174,14 @@ def _ptr(t: torch.Tensor | None) -> int | None:
         raise ValueError("tensors passed to the CUDA sort must live on a CUDA device")
     if not t.is_contiguous():
         raise ValueError("tensors must be contiguous")
+    return t.data_ptr()
+
+
+def _host_ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("pgs_sort_host takes contiguous host tensors")
     return t.data_ptr()
 
 
@@ -272,6 +283,21 @@ def pgs_sort(keys: torch.Tensor, vals: torch.Tensor | None, P: int, cfg: pgs_con
     if vals is not None and vals.numel() != n:
         raise ValueError("length mismatch")
     _check(load().pgs_sort(_ptr(keys), _ptr(vals), n, P, _stream(stream), ctypes.byref(cfg)), "pgs_sort")
+
+
+def pgs_host_workspace_bytes(n: int, P: int, cfg: pgs_config | None = None) -> int:
+    return load().pgs_host_workspace_bytes(n, P, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def pgs_sort_host(keys_in: torch.Tensor, vals_in: torch.Tensor | None, keys_out: torch.Tensor,
+                  vals_out: torch.Tensor | None, P: int, cfg: pgs_config, stream=None) -> None:
+    """Host tensors in and out (pinned for full copy rate); the copies run
+    inside the library, overlapped with step 1.  Asynchronous on `stream`."""
+    n = keys_in.numel()
+    if keys_out.numel() != n or (vals_in is not None and (vals_in.numel() != n or vals_out.numel() != n)):
+        raise ValueError("length mismatch")
+    _check(load().pgs_sort_host(_host_ptr(keys_in), _host_ptr(vals_in), _host_ptr(keys_out), _host_ptr(vals_out),
+                                n, P, _stream(stream), ctypes.byref(cfg)), "pgs_sort_host")
 
 
 STATIC_MAX_KEYS = 1 << 16
@@ -399,34 +425,41 @@ def to_numpy_keys(t: torch.Tensor, dtype: str):
     return a.view(np.uint64 if dtype == "u64" else np.uint32)
 
 
-def sort(keys: torch.Tensor, vals: torch.Tensor | None, P: int, dtype: str = "u32", **opts):
-    """Sort a device (or pinned host) key/payload pair out of place; returns
-    (keys, vals, info) where info holds the bucket bounds and stats tensors.
+def sort(keys: torch.Tensor, vals: torch.Tensor | None, P: int, dtype: str = "u32", out=None, device=None,
+         **opts):
+    """Sort a key/payload pair out of place; returns (keys, vals, info), info
+    holding the bucket bounds and stats tensors (on the device).
 
-    Host tensors are copied to the device, sorted by the library and copied
-    back into fresh pinned host tensors."""
+    Device tensors go through pgs_sort_copy.  Host tensors go through
+    pgs_sort_host (copies inside the library); `out` = (keys_out, vals_out)
+    host tensors to fill, else fresh pinned ones are allocated.  The call
+    returns once host outputs are complete."""
     host = not keys.is_cuda
-    dev = torch.device("cuda") if host else keys.device
-    kin = keys.to(dev, non_blocking=True) if host else keys
-    vin = (vals.to(dev, non_blocking=True) if host else vals) if vals is not None else None
-    n = kin.numel()
+    dev = torch.device(device or "cuda") if host else keys.device
+    n = keys.numel()
     cfg = make_config(dtype=dtype, **opts)
     Peff = max(1, min(P, n)) if n else 1
-    ws = workspace(n, P, cfg, device=dev)
     bounds = torch.empty(Peff + 1, dtype=torch.int64, device=dev)
     st = torch.zeros(STATS_BYTES, dtype=torch.uint8, device=dev)
-    cfg = make_config(dtype=dtype, workspace=ws, bucket_bounds=bounds, stats=st, **opts)
-    kout = torch.empty_like(kin)
-    vout = torch.empty_like(vin) if vin is not None else None
-    pgs_sort_copy(kin, vin, kout, vout, P, cfg)
     info = {"bucket_bounds": bounds, "stats": st}
     if host:
-        ko = torch.empty(kout.shape, dtype=kout.dtype, pin_memory=True)
-        ko.copy_(kout, non_blocking=True)
-        vo = None
-        if vout is not None:
-            vo = torch.empty(vout.shape, dtype=vout.dtype, pin_memory=True)
-            vo.copy_(vout, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        nbytes = pgs_host_workspace_bytes(n, P, cfg)
+        if nbytes == 0:
+            raise PgsError(PGS_ERR_INVALID, "pgs_host_workspace_bytes")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        cfg = make_config(dtype=dtype, workspace=ws, bucket_bounds=bounds, stats=st, **opts)
+        if out is not None:
+            ko, vo = out
+        else:
+            ko = torch.empty(keys.shape, dtype=keys.dtype, pin_memory=True)
+            vo = torch.empty(vals.shape, dtype=vals.dtype, pin_memory=True) if vals is not None else None
+        with torch.cuda.device(dev):
+            pgs_sort_host(keys, vals, ko, vo, P, cfg)
+            torch.cuda.current_stream().synchronize()
         return ko, vo, info
+    ws = workspace(n, P, cfg, device=dev)
+    cfg = make_config(dtype=dtype, workspace=ws, bucket_bounds=bounds, stats=st, **opts)
+    kout = torch.empty_like(keys)
+    vout = torch.empty_like(vals) if vals is not None else None
+    pgs_sort_copy(keys, vals, kout, vout, P, cfg)
     return kout, vout, info

@@ -1,0 +1,97 @@
+"""pgs_sort_host (host buffers in and out, copies inside the call) against the oracle.
+
+The sorted keys and payloads must equal the oracle's stable sort bit for bit
+and the bucket vector must equal the oracle's step 1-4 computation, for run
+groups of every shape (fewer runs than copy groups, ragged groups, one run),
+pinned and pageable host memory, keys only and with payloads.
+"""
+import numpy as np
+import pytest
+
+from oracle import pgs_oracle as O
+from paper_1611_00463_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TILE = 17 * 256
+
+
+def host_tensor(a, dtype, pinned):
+    import torch
+    view = np.ascontiguousarray(a).view(np.int64 if dtype == "u64" else np.int32)
+    t = torch.from_numpy(view.copy())
+    return t.pin_memory() if pinned else t
+
+
+def run_host(keys, vals, P, dtype, pinned=True, **opts):
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    hk = host_tensor(keys, dtype, pinned)
+    hv = host_tensor(vals, "u32", pinned) if vals is not None else None
+    ko, vo, info = pgs.sort(hk, hv, P, dtype=dtype, **opts)
+    torch.cuda.synchronize()
+    got_k = ko.numpy().view(np.uint64 if dtype == "u64" else np.uint32)
+    got_v = vo.numpy().view(np.uint32) if vo is not None else None
+    e = info["bucket_bounds"].cpu().numpy()
+    return got_k, got_v, e, hk, hv
+
+
+def check(keys, vals, P, dtype, **kw):
+    got_k, got_v, e, hk, hv = run_host(keys, vals, P, dtype, **kw)
+    want_k, want_v = O.stable_sort(keys, vals, dtype)
+    assert np.array_equal(got_k, want_k), "keys differ"
+    if vals is not None:
+        assert np.array_equal(got_v, want_v), "payload differs"
+    assert np.array_equal(e, O.buckets(keys, P, dtype)["e"]), "bucket bounds differ"
+    # inputs are left unchanged
+    assert np.array_equal(hk.numpy().view(got_k.dtype), np.ascontiguousarray(keys).view(got_k.dtype))
+
+
+@pytest.mark.parametrize("dtype,n,P", [("u64", 300_007, 128), ("u32", 3 * TILE + 77, 3), ("f32", 200_003, 16),
+                                       ("u32", 50_000, 1), ("u64", 7, 64), ("u32", 1, 5), ("f32", 123_457, 11)])
+def test_host_sort_matches_oracle(dtype, n, P):
+    gen = {"u32": inputs.exponential_u32, "u64": inputs.normal_lognormal_u64, "f32": inputs.zipf_dup_f32}[dtype]
+    keys = gen(n, n % 89 + 1)
+    check(keys, inputs.index_payload(n), P, dtype)
+
+
+def test_host_sort_pageable_memory_and_keys_only():
+    n, P = 150_001, 24
+    keys = inputs.normal_lognormal_u64(n, 5)
+    check(keys, inputs.index_payload(n), P, "u64", pinned=False)
+    got_k, got_v, e, _, _ = run_host(keys, None, P, "u64")
+    assert got_v is None
+    assert np.array_equal(got_k, O.stable_sort(keys, None, "u64")[0])
+
+
+def test_host_sort_equals_device_sort():
+    from tests.gpu_helpers import gpu_sort
+    n, P = 400_000, 40
+    keys = inputs.zipf_dup_f32(n, 8)
+    vals = inputs.index_payload(n)
+    dev = gpu_sort(keys, vals, P, "f32")
+    got_k, got_v, e, _, _ = run_host(keys, vals, P, "f32")
+    assert np.array_equal(got_k, dev["keys"]) and np.array_equal(got_v, dev["vals"])
+    assert np.array_equal(e, dev["e"])
+
+
+def test_host_sort_rejects_device_buffers_and_small_workspace():
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    n, P = 10_000, 4
+    hk = torch.zeros(n, dtype=torch.int32).pin_memory()
+    ko = torch.zeros(n, dtype=torch.int32).pin_memory()
+    dk = torch.zeros(n, dtype=torch.int32, device="cuda")
+    cfg0 = pgs.make_config()
+    ws = torch.empty(pgs.pgs_host_workspace_bytes(n, P, cfg0), dtype=torch.uint8, device="cuda")
+    cfg = pgs.make_config(workspace=ws)
+    rc = pgs.load().pgs_sort_host(dk.data_ptr(), None, ko.data_ptr(), None, n, P, pgs._stream(None),
+                                  pgs.ctypes.byref(cfg))
+    assert rc == pgs.PGS_ERR_INVALID
+    with pytest.raises(ValueError):
+        pgs.pgs_sort_host(dk, None, ko, None, P, cfg)
+    small = pgs.make_config(workspace=torch.empty(1024, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(pgs.PgsError) as ei:
+        pgs.pgs_sort_host(hk, None, ko, None, P, small)
+    assert ei.value.status == pgs.PGS_ERR_WORKSPACE
+    assert pgs.pgs_host_workspace_bytes(n, P, cfg0) > pgs.pgs_workspace_bytes(n, P, cfg0)
