@@ -490,8 +490,8 @@ def main():
         e2e = {"value": n * world / dt / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3,
                "api": "pgs_sort_host through paper_1611_00463_gb300.pgs.sort: pinned host keys/payloads in and "
-                      "out, host-to-device copies in run groups overlapped with step 1, device-to-host copy "
-                      "after step 6, all inside the call"}
+                      "out, host-to-device copies in run groups overlapped with step 1, device-to-host copies "
+                      "in bucket groups overlapped with step 6, all inside the call"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

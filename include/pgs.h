@@ -186,11 +186,14 @@ size_t pgs_host_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg);
  *   pgs_host_workspace_bytes(n, P, cfg).
  *   The input is copied in up to 8 groups of whole runs on a stream of the
  *   call's own, and step 1 of a group starts as soon as its copy has landed,
- *   while later groups are still copying; the sorted output is copied back on
- *   `stream` after step 6.  Asynchronous on `stream` for pinned memory:
- *   synchronise it before reading the outputs.  The paper has no counterpart
- *   (its data starts in each machine's memory); this is the host-to-host form
- *   of pgs_sort_copy. */
+ *   while later groups are still copying.  Once step 5 has fixed the bucket
+ *   bounds the call reads them back (the host waits for steps 1-5 there), then
+ *   runs the remaining merge rounds of step 6 in up to 8 groups of buckets and
+ *   copies each group's sorted keys back while the next group merges.  With
+ *   P = 1 the output is copied back after step 1.  The rest is asynchronous on
+ *   `stream` for pinned memory: synchronise it before reading the outputs.
+ *   The paper has no counterpart (its data starts in each machine's memory);
+ *   this is the host-to-host form of pgs_sort_copy. */
 int pgs_sort_host(const void* keys_in, const uint32_t* vals_in, void* keys_out,
                   uint32_t* vals_out, uint64_t n, uint32_t P, void* stream,
                   const pgs_config* cfg);

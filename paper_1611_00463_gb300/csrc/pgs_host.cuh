@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "pgs.h"
 #include "pgs_kernels.cuh"
@@ -515,11 +516,20 @@ inline uint64_t host_run_start(uint64_t r, uint64_t n, uint64_t P) { return (r *
 // Host-buffer sorts: the input reaches the device in groups of whole runs on a
 // copy stream; group g's copy records ev[g], and its step-1 work waits for
 // that event only, so later groups copy while earlier ones sort.
+// The output leaves the same way: step 6 runs bucket group by bucket group
+// (their bounds read back once step 4 has fixed them), and group g's keys are
+// copied to the host while group g + 1 merges.
 constexpr uint32_t kHostGroups = 8;
 struct HostGroups {
   uint32_t groups = 0;                 // 0: the input is already on the device
   uint32_t r0[kHostGroups + 1] = {};   // runs [r0[g], r0[g+1]) form group g
   cudaEvent_t ev[kHostGroups] = {};
+  uint32_t out_groups = 0;             // 0: the caller copies the output
+  cudaStream_t cs = nullptr;           // copy stream
+  void* hk_out = nullptr;              // host outputs
+  uint32_t* hv_out = nullptr;
+  cudaEvent_t ev_out[kHostGroups] = {};
+  cudaEvent_t done = nullptr;          // recorded on cs after the last output copy
 };
 
 // The launch sequence itself (no attribute or allocation calls, so it can be
@@ -645,7 +655,6 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
     }));
     PGS_TRY(scan_u64(c, b.sizes, b.off, sh.Q, b.scan_sums, b.scan_sums2, 5));
     const uint32_t mtile = (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt);
-    int k0 = 0;
     if (sh.scatter) {
       // Step 5: the exchange, as an in-HBM scatter into bucket-major order.
       const uint64_t stiles = ceil_div(n, kScatterTile);
@@ -659,12 +668,15 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       }));
       std::swap(cur_k, oth_k);
       std::swap(cur_v, oth_v);
-    } else {
+    }
+    int k0 = 0;
+    if (!sh.scatter) {
       // Steps 5 and 6 fused: the first merge round of every bucket reads its
-      // two segments where the sorted runs hold them and writes the merged
-      // pair to its place in bucket-major order.
+      // two segments where the sorted runs hold them and writes the merged pair
+      // to its place in bucket-major order (all buckets at once: the runs'
+      // buffer is free only after every bucket has read its segments).
       PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 5, 48 * sh.Q, [&] {
-        k_pairs_fused<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, b.seg_src, sh.Q, mtile);
+        k_pairs_fused<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, b.seg_src, 0, sh.Q, mtile);
       }));
       --left;
       PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
@@ -672,33 +684,66 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       std::swap(cur_v, oth_v);
       k0 = 1;
     }
-    // Step 6: every bucket merges its P segments with the Fig. 2 schedule,
-    // two levels per pass while two remain.
-    {
+    // Step 6 for the buckets of segment slots [q0, q0 + Qg), len keys, already
+    // in bucket-major order: every bucket merges its P segments with the Fig. 2
+    // schedule, two levels per pass while two remain.
+    auto merge_buckets = [&](uint64_t q0, uint64_t Qg, uint64_t len) -> int {
       int levels = sh.bucket_rounds - k0;
       uint32_t step = 1u << k0;
       while (levels > 0) {
         --left;
         if (sh.four && levels >= 2) {
-          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * sh.Q, [&] {
-            k_quads_buckets<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, sh.Q, step,
-                                                                 kMerge4Cut);
+          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * Qg, [&] {
+            k_quads_buckets<<<grid_for(Qg, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, q0, Qg, step,
+                                                               kMerge4Cut);
           }));
-          PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
+          PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, left == 0 ? f32 : 0, 6)));
           step *= 4;
           levels -= 2;
         } else {
-          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * sh.Q, [&] {
-            k_pairs_bucket_lists<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, sh.Q, step,
-                                                                       mtile);
+          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * Qg, [&] {
+            k_pairs_bucket_lists<<<grid_for(Qg, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, q0, Qg, step,
+                                                                     mtile);
           }));
-          PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
+          PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, left == 0 ? f32 : 0, 6)));
           step *= 2;
           levels -= 1;
         }
         std::swap(cur_k, oth_k);
         std::swap(cur_v, oth_v);
       }
+      return PGS_OK;
+    };
+    if (hg == nullptr || hg->out_groups == 0) {
+      PGS_TRY(merge_buckets(0, sh.Q, n));
+    } else {
+      // Host-buffer sort of one instance: the bucket bounds come back once
+      // (the host waits for steps 1-5 here), then the remaining rounds run
+      // bucket group by bucket group; a group's range is final when its last
+      // round ends, and no later group writes inside it.
+      std::vector<uint64_t> e(R + 1);
+      PGS_CUDA(cudaMemcpyAsync(e.data(), b.e, (R + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+      PGS_CUDA(cudaStreamSynchronize(st));
+      K* const ck = cur_k;
+      K* const okk = oth_k;
+      uint32_t* const cv = cur_v;
+      uint32_t* const ov = oth_v;
+      const int left0 = left;
+      for (uint32_t gi = 0; gi < hg->out_groups; ++gi) {
+        cur_k = ck; oth_k = okk; cur_v = cv; oth_v = ov; left = left0;
+        const uint64_t b0 = ((uint64_t)gi * R) / hg->out_groups, b1 = ((uint64_t)(gi + 1) * R) / hg->out_groups;
+        const uint64_t lo = e[b0], hi = e[b1];
+        if (b1 > b0) PGS_TRY(merge_buckets(b0 * R, (b1 - b0) * R, hi - lo));
+        PGS_CUDA(cudaEventRecord(hg->ev_out[gi], st));
+        PGS_CUDA(cudaStreamWaitEvent(hg->cs, hg->ev_out[gi], 0));
+        if (hi > lo) {
+          PGS_CUDA(cudaMemcpyAsync(static_cast<K*>(hg->hk_out) + lo, kout + lo, (hi - lo) * sizeof(K),
+                                   cudaMemcpyDeviceToHost, hg->cs));
+          if (V) PGS_CUDA(cudaMemcpyAsync(hg->hv_out + lo, vout + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost, hg->cs));
+        }
+      }
+      PGS_CUDA(cudaEventRecord(hg->done, hg->cs));
+      PGS_CUDA(cudaStreamWaitEvent(st, hg->done, 0));
     }
   } else {
     PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)R, [&] {
@@ -767,8 +812,11 @@ struct HostCopies {
   cudaEvent_t start = nullptr;
   HostGroups hg;
   ~HostCopies() {
-    for (uint32_t g = 0; g < kHostGroups; ++g)
+    for (uint32_t g = 0; g < kHostGroups; ++g) {
       if (hg.ev[g]) cudaEventDestroy(hg.ev[g]);
+      if (hg.ev_out[g]) cudaEventDestroy(hg.ev_out[g]);
+    }
+    if (hg.done) cudaEventDestroy(hg.done);
     if (start) cudaEventDestroy(start);
     if (cs) cudaStreamDestroy(cs);
   }
@@ -795,9 +843,16 @@ int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t
   HostGroups& hg = hc.hg;
   hg.groups = std::min<uint32_t>(kHostGroups, R);
   for (uint32_t g = 0; g <= hg.groups; ++g) hg.r0[g] = (uint32_t)(((uint64_t)g * R) / hg.groups);
+  hg.out_groups = R > 1 ? std::min<uint32_t>(kHostGroups, R) : 0;   // P = 1 has no step 6
   PGS_CUDA(cudaStreamCreateWithFlags(&hc.cs, cudaStreamNonBlocking));
   PGS_CUDA(cudaEventCreateWithFlags(&hc.start, cudaEventDisableTiming));
   for (uint32_t g = 0; g < hg.groups; ++g) PGS_CUDA(cudaEventCreateWithFlags(&hg.ev[g], cudaEventDisableTiming));
+  for (uint32_t g = 0; g < hg.out_groups; ++g)
+    PGS_CUDA(cudaEventCreateWithFlags(&hg.ev_out[g], cudaEventDisableTiming));
+  PGS_CUDA(cudaEventCreateWithFlags(&hg.done, cudaEventDisableTiming));
+  hg.cs = hc.cs;
+  hg.hk_out = hko;
+  hg.hv_out = hvo;
   // The copies may overwrite the workspace only after earlier work on `st`.
   PGS_CUDA(cudaEventRecord(hc.start, st));
   PGS_CUDA(cudaStreamWaitEvent(hc.cs, hc.start, 0));
@@ -814,8 +869,10 @@ int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t
                                                           b.run_inst, n, R, sh.s);
   }));
   PGS_TRY((run_pipeline<K, V>(sh, o, dki, dvi, dko, dvo, c, b, &hg)));
-  PGS_CUDA(cudaMemcpyAsync(hko, dko, n * sizeof(K), cudaMemcpyDeviceToHost, st));
-  if (V) PGS_CUDA(cudaMemcpyAsync(hvo, dvo, n * 4, cudaMemcpyDeviceToHost, st));
+  if (hg.out_groups == 0) {                              // no bucket groups: one copy at the end
+    PGS_CUDA(cudaMemcpyAsync(hko, dko, n * sizeof(K), cudaMemcpyDeviceToHost, st));
+    if (V) PGS_CUDA(cudaMemcpyAsync(hvo, dvo, n * 4, cudaMemcpyDeviceToHost, st));
+  }
   return PGS_OK;
 }
 

@@ -280,10 +280,12 @@ static __global__ void k_pairs_sample_lists(Pair* pairs, uint64_t* tcount, Geo g
            samp_off[r0 + min(j + 2 * step, P)], tile);
 }
 
+// Slots [q0, q0 + Q) take part (whole buckets); slot q0 + t writes pair t.
 static __global__ void k_pairs_bucket_lists(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
-                                            uint64_t Q, uint32_t step, uint32_t tile) {
-  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (q >= Q) return;
+                                            uint64_t q0, uint64_t Q, uint32_t step, uint32_t tile) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= Q) return;
+  const uint64_t q = q0 + t;
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
   const uint64_t P = g.P[i];
   const uint64_t local = q - g.seg[i];
@@ -291,32 +293,34 @@ static __global__ void k_pairs_bucket_lists(Pair* pairs, uint64_t* tcount, Geo g
   const uint64_t base = g.seg[i] + b * P;           // first segment of bucket b
   if (j % (2 * step) != 0) {
     const uint64_t end = off[base + P];
-    put_pair(pairs, tcount, q, end, end, end, tile);
+    put_pair(pairs, tcount, t, end, end, end, tile);
     return;
   }
-  put_pair(pairs, tcount, q, off[base + j], off[base + umin(j + step, P)], off[base + umin(j + 2 * step, P)],
+  put_pair(pairs, tcount, t, off[base + j], off[base + umin(j + step, P)], off[base + umin(j + 2 * step, P)],
            tile);
 }
 
 // Step 5 fused into the first round of step 6: segment j of bucket b (j even)
 // merges with segment j+1 straight from the sorted runs, where the exchange
 // would have copied them from, into the pair's place in bucket-major order.
+// Slots [q0, q0 + Q) take part (whole buckets); slot q0 + t writes pair t.
 static __global__ void k_pairs_fused(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
-                                     const uint64_t* __restrict__ seg_src, uint64_t Q, uint32_t tile) {
-  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (q >= Q) return;
+                                     const uint64_t* __restrict__ seg_src, uint64_t q0, uint64_t Q, uint32_t tile) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= Q) return;
+  const uint64_t q = q0 + t;
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
   const uint64_t P = g.P[i];
   const uint64_t j = (q - g.seg[i]) % P;
   if (j % 2 != 0) {
-    pairs[q] = Pair{0, 0, 0, 0, 0};
-    tcount[q] = 0;
+    pairs[t] = Pair{0, 0, 0, 0, 0};
+    tcount[t] = 0;
     return;
   }
   const uint64_t na = off[q + 1] - off[q];
   const uint64_t nb = j + 1 < P ? off[q + 2] - off[q + 1] : 0;
-  pairs[q] = Pair{seg_src[q], na, j + 1 < P ? seg_src[q + 1] : 0, nb, off[q]};
-  tcount[q] = (na + nb + tile - 1) / tile;
+  pairs[t] = Pair{seg_src[q], na, j + 1 < P ? seg_src[q + 1] : 0, nb, off[q]};
+  tcount[t] = (na + nb + tile - 1) / tile;
 }
 
 // ---------------------------------------------------------------------------
@@ -582,9 +586,10 @@ static __global__ void k_quads_runs(Quad* quads, uint64_t* ccount, const uint64_
 // Bucket merge: groups of `step` segments; group g of a bucket starts at
 // segment 4 g step (slot = global segment index; other slots empty).
 static __global__ void k_quads_buckets(Quad* quads, uint64_t* ccount, Geo g, const uint64_t* __restrict__ off,
-                                       uint64_t Q, uint32_t step, uint32_t T) {
-  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (q >= Q) return;
+                                       uint64_t q0, uint64_t Q, uint32_t step, uint32_t T) {
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= Q) return;
+  const uint64_t q = q0 + t;
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
   const uint64_t P = g.P[i];
   const uint64_t local = q - g.seg[i];
@@ -596,7 +601,7 @@ static __global__ void k_quads_buckets(Quad* quads, uint64_t* ccount, Geo g, con
   } else {
     for (int k = 0; k < 5; ++k) b[k] = off[base + umin(j + (uint64_t)k * step, P)];
   }
-  put_quad(quads, ccount, q, b, b[0], T);
+  put_quad(quads, ccount, t, b, b[0], T);
 }
 
 template <typename K>

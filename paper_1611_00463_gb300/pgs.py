@@ -292,7 +292,8 @@ def pgs_host_workspace_bytes(n: int, P: int, cfg: pgs_config | None = None) -> i
 def pgs_sort_host(keys_in: torch.Tensor, vals_in: torch.Tensor | None, keys_out: torch.Tensor,
                   vals_out: torch.Tensor | None, P: int, cfg: pgs_config, stream=None) -> None:
     """Host tensors in and out (pinned for full copy rate); the copies run
-    inside the library, overlapped with step 1.  Asynchronous on `stream`."""
+    inside the library, overlapped with steps 1 and 6.  The call waits for
+    steps 1-5; the rest is asynchronous on `stream`."""
     n = keys_in.numel()
     if keys_out.numel() != n or (vals_in is not None and (vals_in.numel() != n or vals_out.numel() != n)):
         raise ValueError("length mismatch")
