@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--P", type=int, default=None)
     ap.add_argument("--exchange", default="auto", choices=["auto", "scatter", "fused"])
     ap.add_argument("--merge-ways", type=int, default=0, choices=[0, 2, 4], help="tree levels per pass (0 = default)")
+    ap.add_argument("--tile-variant", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="merge tile shape (0 = default; see pgs_config.tile_variant)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-timer", action="store_true", help="skip per-launch events (profiling runs)")
@@ -253,6 +255,7 @@ def config_block(args, dtype, n, P, stats):
         "l2": "inputs larger than L2 (no flush between steps)",
         "exchange": args.exchange,
         "merge_ways": args.merge_ways or 2,
+        "tile_variant": getattr(args, "tile_variant", 0),
         "splitters": args.splitters,
         "guaranteed": bool(args.guaranteed),
     }
@@ -400,7 +403,7 @@ def main():
     kout = torch.empty_like(kin)
     vout = torch.empty_like(vin)
     opts = dict(dtype=dtype, exchange=args.exchange, splitters=args.splitters, guaranteed=args.guaranteed,
-                merge_ways=args.merge_ways)
+                merge_ways=args.merge_ways, tile_variant=args.tile_variant)
     cfg0 = pgs.make_config(**opts)
     ws = pgs.workspace(n, P, cfg0, dev)
     st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
