@@ -627,7 +627,7 @@ __global__ void k_cuts4(const K* __restrict__ src, const Quad* __restrict__ quad
   const uint64_t qi = last_le<uint64_t>(coff, (uint32_t)nquads, t);
   const Quad q = quads[qi];
   const uint64_t l = t - coff[qi];
-  const uint64_t nx = q.n[0] + q.n[1], ny = q.n[2] + q.n[3];
+  const uint64_t nx = q.n[0] + q.n[1];
   const uint64_t cx = nx ? (nx + T - 1) / T - 1 : 0;
   const K* A = src + q.s[0];
   const K* B = src + q.s[1];
