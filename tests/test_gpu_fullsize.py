@@ -1,0 +1,166 @@
+"""The five workloads at full size, in the configuration bench.py times.
+
+At these sizes the oracle cannot sort the whole array in seconds, so the
+sorted output is checked by properties that make it unique: the payload (the
+input index) is a permutation, every output key is the input key its payload
+names, and (order key, payload) rises strictly along the output -- together
+they say the output is exactly the stable sort.  Steps 2-4 (splitters, bucket
+vector, cut matrix) are checked against the oracle's own functions applied to
+runs that numpy sorts (threads, one run each).
+"""
+import concurrent.futures as cf
+import functools
+import os
+
+import numpy as np
+import pytest
+
+from oracle import pgs_oracle as O
+from paper_1611_00463_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def device_ord(t, dtype):
+    """Order key as int64 whose signed order is the key order (on the device)."""
+    import torch
+    if dtype == "u64":
+        return t ^ torch.iinfo(torch.int64).min
+    b = t.to(torch.int64) & 0xFFFFFFFF
+    if dtype == "u32":
+        return b
+    return torch.where((b >> 31) == 1, b ^ 0xFFFFFFFF, b | 0x80000000)
+
+
+def check_stable_sort_device(kin, kout, vout, dtype, offsets=None, chunk=1 << 27):
+    """kin/kout: key bits, vout: input index, all on the device.  With offsets
+    (a batch), every property holds inside each instance."""
+    import torch
+    n = kout.numel()
+    dev = kout.device
+    seen = torch.zeros(n, dtype=torch.bool, device=dev)
+    off = torch.as_tensor(np.asarray(offsets, dtype=np.int64), device=dev) if offsets is not None else None
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk + 1)                     # one extra element for the pair across chunks
+        v = vout[lo:hi].to(torch.int64) & 0xFFFFFFFF
+        k = kout[lo:hi]
+        seen[v[: min(chunk, n - lo)]] = True
+        assert torch.equal(kin[v], k), f"an output key is not the input key its payload names near {lo}"
+        o = device_ord(k, dtype)
+        ok = (o[:-1] < o[1:]) | ((o[:-1] == o[1:]) & (v[:-1] < v[1:]))
+        if off is not None:
+            pos = torch.arange(lo, hi, device=dev)
+            inst = torch.searchsorted(off, pos, right=True) - 1
+            assert bool(((v >= off[inst]) & (v < off[inst + 1])).all()), f"a payload left its instance near {lo}"
+            ok = ok | (inst[:-1] != inst[1:])           # no order across instances
+        assert bool(ok.all()), f"(key, payload) does not rise strictly near {lo}"
+    assert bool(seen.all()), "the payload is not a permutation"
+
+
+@functools.lru_cache(maxsize=1)
+def workload(name):
+    dtype, keys, P = inputs.workload(name)
+    n = len(keys)
+    o = O.ord_bits(keys, dtype)
+    b = O.run_bounds(n, P)
+    with cf.ThreadPoolExecutor(THREADS) as ex:
+        run_ord = list(ex.map(lambda r: np.sort(o[b[r]:b[r + 1]], kind="stable"), range(P)))
+    return dtype, keys, P, run_ord
+
+
+def oracle_steps(run_ord, n, P, s):
+    """Steps 2-4 of the oracle on already sorted runs."""
+    samples = np.concatenate([r[O.regular_sample_positions(len(r), s)] for r in run_ord])
+    t = O.select_splitters(samples, P)
+    e, cut, _, _ = O.investigator(run_ord, t, n, P, O.INVESTIGATOR_RANK)
+    return t, e, cut
+
+
+def gpu_full(keys, P, dtype, **opts):
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    dev = torch.device("cuda")
+    n = len(keys)
+    kin = pgs.as_device_keys(keys, dtype, dev)
+    vin = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32)
+    cfg0 = pgs.make_config(dtype=dtype, **opts)
+    ws = pgs.workspace(n, P, cfg0, dev)
+    bounds = torch.full((P + 1,), -1, dtype=torch.int64, device=dev)
+    cuts = torch.full((P * (P + 1),), -1, dtype=torch.int64, device=dev)
+    spl = torch.zeros(P - 1, dtype=kin.dtype, device=dev)
+    st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
+    cfg = pgs.make_config(dtype=dtype, workspace=ws, bucket_bounds=bounds, cuts=cuts, splitters_out=spl, stats=st,
+                          **opts)
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg)
+    torch.cuda.synchronize()
+    check_stable_sort_device(kin, kout, vout, dtype)
+    return {"e": bounds.cpu().numpy(), "cut": cuts.cpu().numpy().reshape(P, P + 1),
+            "splitters": O.ord_bits(pgs.to_numpy_keys(spl, dtype), dtype), "stats": pgs.pgs_get_stats(st)}
+
+
+@pytest.mark.parametrize("name", ["normal_lognormal_u64", "zipf_dup_f32", "exponential_u32"])
+def test_full_size_sampled(name):
+    dtype, keys, P, run_ord = workload(name)
+    n = len(keys)
+    got = gpu_full(keys, P, dtype)
+    t, e, cut = oracle_steps(run_ord, n, P, O.paper_samples_per_run(P, O.KEY_BYTES[dtype]))
+    assert np.array_equal(got["splitters"], t), "splitters differ"
+    assert np.array_equal(got["e"], e), "bucket bounds differ"
+    assert np.array_equal(got["cut"], cut), "cut matrix differs"
+    sizes = np.diff(e)
+    assert got["stats"]["max_bucket"] == sizes.max() and got["stats"]["min_bucket"] == sizes.min()
+    if name == "normal_lognormal_u64":
+        assert sizes.max() <= 1.05 * n / P          # the balance target at the paper's sample budget
+
+
+def test_full_size_guaranteed_and_learned():
+    dtype, keys, P, run_ord = workload("exponential_u32")
+    n = len(keys)
+    s = O.guaranteed_samples_per_run(P, 0.05)
+    got = gpu_full(keys, P, dtype, guaranteed=True)
+    t, e, cut = oracle_steps(run_ord, n, P, s)
+    assert np.array_equal(got["splitters"], t) and np.array_equal(got["e"], e) and np.array_equal(got["cut"], cut)
+    assert np.diff(e).max() <= 1.05 * n / P
+    # Learned splitters: the model's buckets are judged against the sampled ones;
+    # when its imbalance exceeds 1 + eps the sampled cuts are used.
+    got_l = gpu_full(keys, P, dtype, splitters="learned")
+    st = got_l["stats"]
+    assert st["splitter_mode"] == 1
+    if st["fallback"]:
+        assert st["learned_over_mean"] > 1.05
+        _, e_s, cut_s = oracle_steps(run_ord, n, P, O.paper_samples_per_run(P, O.KEY_BYTES[dtype]))
+        assert np.array_equal(got_l["e"], e_s) and np.array_equal(got_l["cut"], cut_s)
+    else:
+        assert st["max_over_mean"] <= 1.05
+
+
+def test_full_size_batched():
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    offsets, keys, Pi = inputs.batched()
+    n = len(keys)
+    bt = pgs.Batch(offsets, None, dtype="u64", with_vals=True)
+    kin = pgs.as_device_keys(keys, "u64")
+    vin = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32)
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    bt.tune(kout, vout)                                   # the shape bench.py's batched line uses
+    st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    bt.sort_copy(kin, vin, kout, vout, cfg=bt.config(stats=st))
+    torch.cuda.synchronize()
+    check_stable_sort_device(kin, kout, vout, "u64", offsets=offsets)
+    stats = pgs.pgs_get_stats(st)
+    # The bucket loads of every instance against the oracle's steps 1-4.
+    auto = np.array([pgs.load().pgs_batch_auto_partitions(int(offsets[i + 1] - offsets[i]))
+                     for i in range(len(Pi))])
+    assert np.array_equal(auto, Pi)
+
+    def loads(i):
+        a, b = int(offsets[i]), int(offsets[i + 1])
+        r = O.buckets(keys[a:b], int(Pi[i]), "u64")
+        return r["stats"]["max"], r["stats"]["min"]
+    with cf.ThreadPoolExecutor(THREADS) as ex:
+        res = list(ex.map(loads, range(len(Pi))))
+    assert stats["max_bucket"] == max(m for m, _ in res) and stats["min_bucket"] == min(m for _, m in res)
