@@ -489,12 +489,47 @@ def main():
             t = torch.tensor([dt], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
+        # Steady state: two calls in flight, each on its own stream with its own
+        # workspace and output buffers, so one call's copy to the device overlaps
+        # the previous call's merge and copy back (the copy engines of the two
+        # directions run at once).  Every step still moves its own input in and
+        # its own result out inside the timed region.
+        hws = pgs.pgs_host_workspace_bytes(n, P, pgs.make_config(**opts))
+        lanes = []
+        for _ in range(2):
+            lanes.append((torch.cuda.Stream(dev), torch.empty(hws, dtype=torch.uint8, device=dev),
+                          torch.empty_like(hk).pin_memory(), torch.empty_like(hv).pin_memory()))
+        cfgs = [pgs.make_config(workspace=ln[1], **opts) for ln in lanes]
+
+        def call(k):
+            s_, _, ko_, vo_ = lanes[k % 2]
+            pgs.pgs_sort_host(hk, hv, ko_, vo_, P, cfgs[k % 2], stream=s_)
+        for k in range(2):
+            call(k)
+        torch.cuda.synchronize(dev)
+        k_pipe = max(2, min(args.steps, 10))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(k_pipe):
+            call(k)
+        torch.cuda.synchronize(dev)
+        dt_pipe = (time.perf_counter() - t0) / k_pipe
+        if world > 1:
+            t = torch.tensor([dt_pipe], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt_pipe = float(t.item())
+        same = all(torch.equal(ln[2], ko) and torch.equal(ln[3], vo) for ln in lanes)
+        del lanes, cfgs
         nbytes = n * (kin.element_size() + 4)
-        e2e = {"value": n * world / dt / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3,
-               "api": "pgs_sort_host through paper_1611_00463_gb300.pgs.sort: pinned host keys/payloads in and "
-                      "out, host-to-device copies in run groups overlapped with step 1, device-to-host copies "
-                      "in bucket groups overlapped with step 6, all inside the call"}
+        e2e = {"value": n * world / dt_pipe / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": dt_pipe * 1e3, "in_flight": 2,
+               "outputs_equal_single_call": same,
+               "single_call": {"value": n * world / dt / 1e9, "ms": dt * 1e3},
+               "api": "pgs_sort_host (C ABI, host buffers): pinned host keys/payloads in and out, "
+                      "host-to-device copies in run groups overlapped with step 1, device-to-host copies "
+                      "in bucket groups overlapped with step 6, all inside the call; two calls in flight "
+                      "on two streams with their own workspaces and output buffers"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
