@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--merge-ways", type=int, default=0, choices=[0, 2, 4], help="tree levels per pass (0 = default)")
     ap.add_argument("--tile-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="merge tile shape (0 = default; see pgs_config.tile_variant)")
+    ap.add_argument("--samples-per-run", type=int, default=0, help="regular samples per run (0 = the paper's budget)")
+    ap.add_argument("--sweep-samples", action="store_true",
+                    help="time the sort at the paper's sample sizes 0.004X .. 1.4X (X = 256 KB / P) instead")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-timer", action="store_true", help="skip per-launch events (profiling runs)")
@@ -255,6 +258,7 @@ def config_block(args, dtype, n, P, stats):
         "l2": "inputs larger than L2 (no flush between steps)",
         "exchange": args.exchange,
         "merge_ways": args.merge_ways or 2,
+        "samples_per_run_option": getattr(args, "samples_per_run", 0) or "paper budget",
         "tile_variant": getattr(args, "tile_variant", 0),
         "splitters": args.splitters,
         "guaranteed": bool(args.guaranteed),
@@ -370,8 +374,76 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+SWEEP_FRACTIONS = [0.004, 0.04, 0.4, 1.0, 1.004, 1.04, 1.4]   # the sample sizes of Fig. 9 and 10
+
+
+def run_sweep(args):
+    """The sort at the paper's sample sizes f X, X = 256 KB / P of keys per run
+    (Section V, Fig. 9 and 10): time per sort, per-step times, and the smallest
+    and largest bucket, one point per size, in one JSON line."""
+    import torch
+    from paper_1611_00463_gb300 import build as pbuild
+    from paper_1611_00463_gb300 import pgs
+    pbuild.build()
+    pgs.load()
+    dev = torch.device("cuda", 0)
+    dtype, n, P, gen, seed = workload_shape(args)
+    keys_np = gen(n, seed)
+    kin = pgs.as_device_keys(keys_np, dtype, dev)
+    vin = torch.from_numpy(inputs.index_payload(n).view(np.int32)).to(dev)
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    w = kin.element_size()
+    X = 262144 // (P * w)
+    stream = torch.cuda.current_stream(dev)
+    points = []
+    with ClockSampler(0) as clocks:
+        for f in SWEEP_FRACTIONS:
+            s_run = max(1, int(f * X))
+            opts = dict(dtype=dtype, exchange=args.exchange, merge_ways=args.merge_ways,
+                        tile_variant=args.tile_variant, samples_per_run=s_run)
+            ws = pgs.workspace(n, P, pgs.make_config(**opts), dev)
+            st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
+            cfg = pgs.make_config(workspace=ws, stats=st, **opts)
+            for _ in range(max(args.warmup, 0)):
+                pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg, stream)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1) / args.steps
+            timer = pgs.Timer(capacity=512)
+            pgs.pgs_sort_copy(kin, vin, kout, vout, P, pgs.make_config(workspace=ws, stats=st, timer=timer, **opts),
+                              stream)
+            torch.cuda.synchronize(dev)
+            recs, _ = timer.read()
+            step_ms = {}
+            for r in recs:
+                step_ms[str(r["step"])] = step_ms.get(str(r["step"]), 0.0) + r["ms"]
+            stv = pgs.pgs_get_stats(st, stream)
+            mean = n / stv["P"]
+            points.append({"fraction_of_X": f, "samples_per_run": s_run, "ms_per_sort": ms,
+                           "Gkeys_per_s": n / (ms * 1e-3) / 1e9, "max_bucket": stv["max_bucket"],
+                           "min_bucket": stv["min_bucket"], "max_over_mean": stv["max_bucket"] / mean,
+                           "min_over_mean": stv["min_bucket"] / mean,
+                           "load_difference": stv["max_bucket"] - stv["min_bucket"],
+                           "per_step_ms": step_ms})
+            del ws
+    line = {"sweep": "samples_per_run", "workload": args.workload, "n": n, "P": P, "key": dtype,
+            "X_keys_per_run": X, "steps": args.steps, "warmup": args.warmup, "points": points,
+            "clocks": clocks.summary(),
+            "note": "X = 256 KB / P of keys per run (Section V); per_step_ms keys are the steps of Section IV "
+                    "(1 local sort, 2 sampling, 3 splitters, 4 cut search + investigator, 5 offsets/exchange, "
+                    "6 bucket merge) from one extra timed sort"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.sweep_samples:
+        return run_sweep(args)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -403,7 +475,7 @@ def main():
     kout = torch.empty_like(kin)
     vout = torch.empty_like(vin)
     opts = dict(dtype=dtype, exchange=args.exchange, splitters=args.splitters, guaranteed=args.guaranteed,
-                merge_ways=args.merge_ways, tile_variant=args.tile_variant)
+                merge_ways=args.merge_ways, tile_variant=args.tile_variant, samples_per_run=args.samples_per_run)
     cfg0 = pgs.make_config(**opts)
     ws = pgs.workspace(n, P, cfg0, dev)
     st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)

@@ -95,3 +95,32 @@ def test_host_sort_rejects_device_buffers_and_small_workspace():
         pgs.pgs_sort_host(hk, None, ko, None, P, small)
     assert ei.value.status == pgs.PGS_ERR_WORKSPACE
     assert pgs.pgs_host_workspace_bytes(n, P, cfg0) > pgs.pgs_workspace_bytes(n, P, cfg0)
+
+
+def test_host_sorts_in_flight_on_two_streams():
+    """Consecutive calls on two streams with their own workspaces overlap on the
+    GPU (one call's copy in during the other's merges); each result is exact."""
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    n, P = 600_011, 32
+    sets = [inputs.normal_lognormal_u64(n, 30 + i) for i in range(4)]
+    vals = inputs.index_payload(n)
+    hv = host_tensor(vals, "u32", True)
+    cfg0 = pgs.make_config(dtype="u64")
+    lanes = []
+    for _ in range(2):
+        ws = torch.empty(pgs.pgs_host_workspace_bytes(n, P, cfg0), dtype=torch.uint8, device="cuda")
+        lanes.append((torch.cuda.Stream(), pgs.make_config(dtype="u64", workspace=ws), ws))
+    outs = []
+    for i, keys in enumerate(sets):
+        s, cfg, _ = lanes[i % 2]
+        hk = host_tensor(keys, "u64", True)
+        ko = torch.empty_like(hk).pin_memory()
+        vo = torch.empty_like(hv).pin_memory()
+        pgs.pgs_sort_host(hk, hv, ko, vo, P, cfg, stream=s)
+        outs.append((hk, ko, vo))
+    torch.cuda.synchronize()
+    for keys, (_, ko, vo) in zip(sets, outs):
+        want_k, want_v = O.stable_sort(keys, vals, "u64")
+        assert np.array_equal(ko.numpy().view(np.uint64), want_k)
+        assert np.array_equal(vo.numpy().view(np.uint32), want_v)

@@ -204,3 +204,16 @@ def test_four_way_and_pairwise_rounds_agree(dtype, n, P):
     four = check_against_oracle(keys, vals, P, dtype, merge_ways=4)
     two = check_against_oracle(keys, vals, P, dtype, merge_ways=2)
     assert four["stats"]["passes"] <= two["stats"]["passes"]
+
+
+@pytest.mark.parametrize("f", [0.004, 0.04, 0.4, 1.0, 1.004, 1.04, 1.4])
+def test_sample_size_sweep_points(f):
+    """The sample sizes of the paper's sweep (Section V, Fig. 9 and 10):
+    f X keys per run, X = 256 KB / P."""
+    P = 128
+    n = P * 3001 + 17
+    keys = inputs.normal_lognormal_u64(n, seed=11)
+    s = max(1, int(f * (262144 // (P * 8))))
+    check_against_oracle(keys, inputs.index_payload(n), P, "u64", s=s)
+    zipf = inputs.zipf_dup_f32(n, seed=12)
+    check_against_oracle(zipf, inputs.index_payload(n), P, "f32", s=max(1, int(f * (262144 // (P * 4)))))
