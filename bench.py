@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="pgs", choices=["pgs", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(inputs.WORKLOADS) + ["batched"])
     ap.add_argument("--splitters", default="sampled", choices=["sampled", "learned"])
+    ap.add_argument("--investigator", default="rank", choices=["rank", "equal", "off", "local"],
+                    help="step 4 rule for duplicated splitters (local = the per-run division, not stable)")
     ap.add_argument("--guaranteed", action="store_true", help="oversample so every bucket < (1+eps) n/P")
     ap.add_argument("--instances", type=int, default=10000, help="batched workload: number of instances")
     ap.add_argument("--n", type=int, default=None, help="override the number of keys (smaller cases)")
@@ -261,6 +263,7 @@ def config_block(args, dtype, n, P, stats):
         "samples_per_run_option": getattr(args, "samples_per_run", 0) or "paper budget",
         "tile_variant": getattr(args, "tile_variant", 0),
         "splitters": args.splitters,
+        "investigator": getattr(args, "investigator", "rank"),
         "guaranteed": bool(args.guaranteed),
     }
     if stats:
@@ -475,7 +478,8 @@ def main():
     kout = torch.empty_like(kin)
     vout = torch.empty_like(vin)
     opts = dict(dtype=dtype, exchange=args.exchange, splitters=args.splitters, guaranteed=args.guaranteed,
-                merge_ways=args.merge_ways, tile_variant=args.tile_variant, samples_per_run=args.samples_per_run)
+                merge_ways=args.merge_ways, tile_variant=args.tile_variant, samples_per_run=args.samples_per_run,
+                investigator=args.investigator)
     cfg0 = pgs.make_config(**opts)
     ws = pgs.workspace(n, P, cfg0, dev)
     st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)

@@ -55,9 +55,19 @@ typedef enum {
  *          their value into k equal parts, e_{j+i} = L + floor(G (i+1) / k);
  *          a non-duplicated splitter is cut by plain binary search (upper bound)
  *  OFF   : plain upper bound e_b = L_b + G_b, the failure mode of Fig. 5(b).
- * Every variant divides a value's range by global stable rank, so the output is
- * the same stable sort; only the bucket sizes differ. */
-typedef enum { PGS_INVESTIGATOR_RANK = 0, PGS_INVESTIGATOR_EQUAL = 1, PGS_INVESTIGATOR_OFF = 2 } pgs_investigator;
+ * These three divide a value's range by global stable rank, so the output is
+ * the same stable sort; only the bucket sizes differ.
+ *  LOCAL : the rule as the text words it: every run divides its own range of
+ *          a duplicated value, cut[r][j+i] = lb[r][j] + floor(cnt[r][j] (i+1) / k)
+ *          for a group of k equal splitters, upper bound otherwise; e_b is the
+ *          sum of the runs' cuts.  The keys come out sorted, but equal keys are
+ *          ordered by bucket, then run (not by input position: not stable). */
+typedef enum {
+  PGS_INVESTIGATOR_RANK = 0,
+  PGS_INVESTIGATOR_EQUAL = 1,
+  PGS_INVESTIGATOR_OFF = 2,
+  PGS_INVESTIGATOR_LOCAL = 3
+} pgs_investigator;
 
 /* Step 5 (Section IV-C): SCATTER copies every run segment to its bucket before
  * the merge (one pass of its own); FUSED lets the first merge round of step 6

@@ -42,6 +42,7 @@ KEY_BYTES = {"u32": 4, "u64": 8, "f32": 4}
 INVESTIGATOR_RANK = 0      # default: cut at rank floor(bN/P) clamped into [L_b, L_b+G_b]
 INVESTIGATOR_EQUAL = 1     # a group of k equal splitters splits the value's range into k equal parts
 INVESTIGATOR_OFF = 2       # plain binary search (upper bound), the failure mode of Fig. 5(b)
+INVESTIGATOR_LOCAL = 3     # the text's literal rule: every run divides its own range of the value
 
 SAMPLE_BUFFER_BYTES = 262144   # the 256 KB read buffer of Section IV-B
 
@@ -214,7 +215,17 @@ def investigator(run_ord: list[np.ndarray], t: np.ndarray, n: int, P: int,
 
     Each run gives bucket b its elements of stable rank [e_b, e_{b+1}):
     cut[r,b] = lb[r,b] + clamp(e_b - L_b - pre[r,b], 0, cnt[r,b]), with
-    cut[r,0] = 0 and cut[r,P] = n_r.  Returns (e, cut, lb, cnt).
+    cut[r,0] = 0 and cut[r,P] = n_r.
+
+    * LOCAL, the rule as Section IV-B words it ("during searching for each
+      splitter on local data entries"): every run divides its own range of a
+      duplicated value, so for a group of k equal splitters starting at b,
+      cut[r, b+i] = lb[r,b] + floor(cnt[r,b] (i+1) / k), i = 0..k-1, and a
+      splitter that is not duplicated cuts at the upper bound; e is then the sum
+      of the cuts over runs.  Keys end sorted, but equal keys are ordered by
+      bucket, then run, not by input position (not stable).
+
+    Returns (e, cut, lb, cnt).
     """
     R = len(run_ord)
     lb = np.zeros((R, P + 1), dtype=np.int64)
@@ -225,6 +236,19 @@ def investigator(run_ord: list[np.ndarray], t: np.ndarray, n: int, P: int,
     L = lb.sum(axis=0)
     G = cnt.sum(axis=0)
     pre = np.cumsum(cnt, axis=0) - cnt
+
+    if variant == INVESTIGATOR_LOCAL:
+        cut = np.zeros((R, P + 1), dtype=np.int64)
+        cut[:, P] = [len(x) for x in run_ord]
+        b = 1
+        while b < P:
+            k = 1
+            while b + k < P and t[b + k - 1] == t[b - 1]:
+                k += 1
+            for i in range(k):
+                cut[:, b + i] = lb[:, b] + (cnt[:, b] * (i + 1)) // k
+            b += k
+        return cut.sum(axis=0), cut, lb, cnt
 
     e = np.zeros(P + 1, dtype=np.int64)
     e[P] = n
@@ -291,8 +315,9 @@ def sample_sort(keys: np.ndarray, vals: np.ndarray | None, P: int, dtype: str,
     5. every segment is written at its receive offset (the exchange);
     6. each receiver merges its P segments with the Fig. 2 schedule.
 
-    Returns every intermediate result and the final keys/vals, which must equal
-    ``stable_sort`` for every investigator variant.
+    Returns every intermediate result and the final keys/vals, which equal
+    ``stable_sort`` for the RANK, EQUAL and OFF variants; with LOCAL the keys
+    equal it and equal keys are ordered by bucket, then run.
     """
     n = len(keys)
     P = effective_partitions(n, P)

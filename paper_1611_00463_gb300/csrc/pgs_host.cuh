@@ -71,7 +71,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->merge_ways = cfg->merge_ways == 0 ? 2 : cfg->merge_ways;
   if (o->dtype < PGS_U32 || o->dtype > PGS_F32) return PGS_ERR_INVALID;
   if (!(o->eps > 0.0f) || o->eps > 1.0f) return PGS_ERR_INVALID;
-  if (o->investigator < 0 || o->investigator > 2) return PGS_ERR_INVALID;
+  if (o->investigator < 0 || o->investigator > 3) return PGS_ERR_INVALID;
   if (o->exchange < 0 || o->exchange > 2) return PGS_ERR_INVALID;
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
   if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;

@@ -1064,7 +1064,40 @@ k_investigator(const uint64_t* __restrict__ lb, const uint64_t* __restrict__ cnt
   const uint64_t* lbi = lb + g.mat[i];
   const uint64_t* cnti = cnt + g.mat[i];
   uint64_t* cuti = cut + g.mat[i];
-  __shared__ uint64_t sh_L, sh_e;
+  __shared__ uint64_t sh_L, sh_e, sh_g0, sh_k;
+  // Group of equal splitters containing t_b: slots [g0, g0 + k) of 1..P-1.
+  auto group = [&](uint64_t& g0, uint64_t& k) {
+    const K* ti = t + r0;
+    const K v = ti[b];
+    uint64_t lo = 1, hi = P;
+    while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (ti[m] < v) lo = m + 1; else hi = m; }
+    g0 = lo;
+    hi = P;
+    while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (ti[m] <= v) lo = m + 1; else hi = m; }
+    k = lo - g0;
+  };
+  if (variant == 3) {
+    // The text's literal rule: every run divides its own range of a duplicated
+    // value into k equal parts; e_b is the sum of the runs' cuts.
+    if (threadIdx.x == 0) {
+      uint64_t g0, k;
+      group(g0, k);
+      sh_g0 = g0;
+      sh_k = k;
+    }
+    __syncthreads();
+    const uint64_t j = b - sh_g0, k = sh_k;
+    uint64_t part = 0;
+    for (uint64_t r = threadIdx.x; r < P; r += blockDim.x) {
+      const uint64_t c = lbi[r * W + b] + (cnti[r * W + b] * (j + 1)) / k;
+      cuti[r * W + b] = c;
+      part += c;
+    }
+    uint64_t total;
+    block_exclusive_scan(part, &total);
+    if (threadIdx.x == 0) e[r0 + i + b] = total;
+    return;
+  }
   uint64_t ls = 0, gs = 0;
   for (uint64_t r = threadIdx.x; r < P; r += blockDim.x) {
     ls += lbi[r * W + b];
@@ -1081,16 +1114,9 @@ k_investigator(const uint64_t* __restrict__ lb, const uint64_t* __restrict__ cnt
     } else if (variant == 2) {
       eb = Lb + Gb;
     } else {
-      // Group of equal splitters containing t_b: [g0, g1) in splitter slots 1..P-1.
-      const K* ti = t + r0;
-      const K v = ti[b];
-      uint64_t lo = 1, hi = P;
-      while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (ti[m] < v) lo = m + 1; else hi = m; }
-      const uint64_t g0 = lo;
-      hi = P;
-      while (lo < hi) { uint64_t m = (lo + hi) >> 1; if (ti[m] <= v) lo = m + 1; else hi = m; }
-      const uint64_t k = lo - g0, j = b - g0;
-      eb = Lb + (Gb * (j + 1)) / k;
+      uint64_t g0, k;
+      group(g0, k);
+      eb = Lb + (Gb * (b - g0 + 1)) / k;
     }
     sh_L = Lb;
     sh_e = eb;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpgs.so")
 
 PGS_U32, PGS_U64, PGS_F32 = 0, 1, 2
 PGS_OK, PGS_ERR_INVALID, PGS_ERR_WORKSPACE, PGS_ERR_CUDA, PGS_ERR_TIMEOUT, PGS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
-INVESTIGATOR = {"rank": 0, "equal": 1, "off": 2}
+INVESTIGATOR = {"rank": 0, "equal": 1, "off": 2, "local": 3}
 EXCHANGE = {"auto": 0, "scatter": 1, "fused": 2}
 SPLITTERS = {"sampled": 0, "learned": 1}
 DTYPES = {"u32": PGS_U32, "u64": PGS_U64, "f32": PGS_F32}

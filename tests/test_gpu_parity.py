@@ -217,3 +217,19 @@ def test_sample_size_sweep_points(f):
     check_against_oracle(keys, inputs.index_payload(n), P, "u64", s=s)
     zipf = inputs.zipf_dup_f32(n, seed=12)
     check_against_oracle(zipf, inputs.index_payload(n), P, "f32", s=max(1, int(f * (262144 // (P * 4)))))
+
+
+@pytest.mark.parametrize("dtype,n,P,s", [("f32", 40_009, 16, None), ("f32", 3 * TILE + 5, 64, 4), ("u64", 30_011, 7, 8),
+                                         ("u32", 20_000, 40, 3)])
+def test_local_investigator_matches_oracle_pipeline(dtype, n, P, s):
+    """The paper-literal per-run division (not stable): keys, payloads, bucket
+    vector and cut matrix equal the oracle's six steps with the same rule."""
+    gen = {"f32": inputs.zipf_dup_f32, "u64": inputs.zipf_dup_u64, "u32": lambda m, seed: inputs.structured_u32("few", m)}
+    keys = gen[dtype](n, 21)
+    vals = inputs.index_payload(n)
+    kw = {} if s is None else {"samples_per_run": s}
+    got = _gpu(keys, vals, P, dtype, investigator="local", **kw)
+    ref = O.sample_sort(keys, vals, P, dtype, samples_per_run=s, variant=O.INVESTIGATOR_LOCAL)
+    assert np.array_equal(got["keys"], ref["keys"]) and np.array_equal(got["vals"], ref["vals"])
+    assert np.array_equal(got["e"], ref["e"]) and np.array_equal(got["cut"], ref["cut"])
+    assert np.array_equal(got["keys"], O.stable_sort(keys, vals, dtype)[0])

@@ -269,3 +269,63 @@ def test_exchange_offsets_tile_the_output():
             covered[dst[r, b]:dst[r, b] + size[r, b]] += 1
             assert e[b] <= dst[r, b] and dst[r, b] + size[r, b] <= e[b + 1]
     assert np.all(covered == 1)
+
+
+def test_fig5c_local_rule_divides_every_run():
+    # The text's literal rule: each processor divides its own range of the
+    # duplicated value equally among the four duplicated splitters.
+    a = 5
+    keys = np.full(40, a, dtype=np.uint32)
+    keys[0] = 1
+    keys[39] = 9
+    loc = O.buckets(keys, 5, "u32", samples_per_run=8, variant=O.INVESTIGATOR_LOCAL)
+    assert list(loc["splitters"]) == [a, a, a, a]
+    # Runs of 8 keys: run 0 holds 1 + seven a, runs 1-3 eight a, run 4 seven a + 9.
+    cnt_a = [7, 8, 8, 8, 7]
+    lb_a = [1, 0, 0, 0, 0]
+    for r in range(5):
+        want = [0] + [lb_a[r] + (cnt_a[r] * (i + 1)) // 4 for i in range(4)] + [8]
+        assert list(loc["cut"][r]) == want
+    assert list(loc["e"]) == list(loc["cut"].sum(axis=0))
+    assert list(loc["e"]) == [0, 1 + 1 + 2 + 2 + 2 + 1, 1 + 3 + 4 + 4 + 4 + 3, 1 + 5 + 6 + 6 + 6 + 5,
+                              1 + 38, 40]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_local_rule_sorts_keys_and_stays_within_rounding_of_equal(seed):
+    rng = np.random.default_rng(seed)
+    n, P = int(rng.integers(50, 400)), int(rng.integers(2, 12))
+    keys = rng.choice(np.array([3, 7, 7, 7, 7, 11, 20], np.uint32), size=n)
+    vals = np.arange(n, dtype=np.uint32)
+    s = int(rng.integers(1, 9))
+    loc = O.sample_sort(keys, vals, P, "u32", samples_per_run=s, variant=O.INVESTIGATOR_LOCAL)
+    want_k, _ = O.stable_sort(keys, vals, "u32")
+    assert np.array_equal(loc["keys"], want_k)
+    assert np.array_equal(np.sort(loc["vals"]), vals)
+    assert np.array_equal(keys[loc["vals"]], loc["keys"])
+    eq = O.buckets(keys, P, "u32", samples_per_run=s, variant=O.INVESTIGATOR_EQUAL)
+    # Per-run floors against the floor of the sum: e_LOCAL <= e_EQUAL < e_LOCAL + R.
+    R = loc["P"]
+    assert np.all(loc["e"] <= eq["e"]) and np.all(eq["e"] - loc["e"] < R)
+    # Inside each bucket, keys from run r precede equal keys from run r' > r.
+    for b in range(R):
+        seg = loc["vals"][loc["e"][b]:loc["e"][b + 1]]
+        run_of = np.searchsorted(loc["bounds"], seg, side="right") - 1
+        kk = keys[seg]
+        for i in range(len(seg) - 1):
+            if kk[i] == kk[i + 1]:
+                assert (run_of[i], seg[i]) < (run_of[i + 1], seg[i + 1])
+
+
+def test_local_rule_is_not_stable():
+    # Three runs of three 7s under two duplicated splitters: each run sends
+    # floor(3/2) = 1 of its 7s to bucket 0 and the other 2 to bucket 1, so run
+    # 1's first 7 comes before run 0's second.
+    keys = np.full(9, 7, np.uint32)
+    vals = np.arange(9, dtype=np.uint32)
+    loc = O.sample_sort(keys, vals, 3, "u32", samples_per_run=3, variant=O.INVESTIGATOR_LOCAL)
+    assert list(loc["splitters"]) == [7, 7]
+    assert [list(r) for r in loc["cut"]] == [[0, 1, 3, 3]] * 3
+    assert list(loc["e"]) == [0, 3, 9, 9]
+    assert list(loc["vals"]) == [0, 3, 6, 1, 2, 4, 5, 7, 8]
+    assert list(O.stable_sort(keys, vals, "u32")[1]) == list(range(9))
