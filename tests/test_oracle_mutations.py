@@ -35,6 +35,10 @@ MUTATIONS = {
     "ceil_run_split": ("(r * n) // P for r in range(P + 1)", "(r * n + P - 1) // P for r in range(P + 1)"),
     "budget_counts_payload": ("SAMPLE_BUFFER_BYTES // (P * key_bytes)",
                               "SAMPLE_BUFFER_BYTES // (P * (key_bytes + 4))"),
+    "local_divides_global_count": ("cut[:, b + i] = lb[:, b] + (cnt[:, b] * (i + 1)) // k",
+                                   "cut[:, b + i] = lb[:, b] + (G[b] * (i + 1)) // k"),
+    "local_one_part_too_many": ("cut[:, b + i] = lb[:, b] + (cnt[:, b] * (i + 1)) // k",
+                                "cut[:, b + i] = lb[:, b] + (cnt[:, b] * (i + 1)) // (k + 1)"),
 }
 
 
@@ -103,6 +107,14 @@ def run_pins(O):
     keys = np.random.default_rng(4).permutation(48).astype(np.uint32) * 3
     res = O.buckets(keys, 6, "u32", samples_per_run=8)
     assert list(res["splitters"]) == list(np.sort(keys)[[8 * b - 1 for b in range(1, 6)]])
+    # Fig. 5(c) with the per-run rule: every run splits its own copies of the
+    # duplicated value into four equal parts.
+    keys = np.full(40, 5, np.uint32)
+    keys[0], keys[39] = 1, 9
+    res = O.buckets(keys, 5, "u32", samples_per_run=8, variant=O.INVESTIGATOR_LOCAL)
+    cnt_a, lb_a = [7, 8, 8, 8, 7], [1, 0, 0, 0, 0]
+    for r in range(5):
+        assert list(res["cut"][r]) == [0] + [lb_a[r] + (cnt_a[r] * (i + 1)) // 4 for i in range(4)] + [8]
     # The full pipeline against the stable-sort properties.
     for name, n, P in [("zipf_dup_f32", 3001, 16), ("normal_lognormal_u64", 2000, 8)]:
         dtype, keys, _ = inputs.workload(name, n=n)
