@@ -572,3 +572,35 @@ def learned_buckets(keys: np.ndarray, P: int, dtype: str, w: np.ndarray, kmin: i
         cut[r, 1:] = np.cumsum(hist)
     e = cut.sum(axis=0)
     return {"P": P, "cut": cut, "e": e, "stats": load_stats(e)}
+
+
+# ---------------------------------------------------------------------------
+# Lookups on the sorted output (Section IV-C: the library lets users binary
+# search the sorted data and find every entry's previous processor and index).
+# ---------------------------------------------------------------------------
+
+def search(sorted_keys: np.ndarray, queries: np.ndarray, dtype: str, side: str = "left") -> np.ndarray:
+    """Position of every query in the sorted keys, by key order: "left" gives
+    the number of keys ordered before the query (lower bound), "right" the
+    number ordered before or equal to it (upper bound)."""
+    return np.searchsorted(ord_bits(sorted_keys, dtype), ord_bits(queries, dtype), side=side).astype(np.int64)
+
+
+def bucket_of(pos: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """The bucket (processor) whose output range [e_b, e_{b+1}) holds position
+    pos; a position equal to n (past the last key) maps to P, and an empty
+    bucket holds no position."""
+    P = len(e) - 1
+    b = np.searchsorted(e, pos, side="right") - 1
+    return np.where(pos >= e[P], P, b).astype(np.int64)
+
+
+def provenance(vals: np.ndarray, n: int, P: int):
+    """Previous processor and index of every entry whose payload is its input
+    position: run r = the one with run_bounds[r] <= v < run_bounds[r+1]; the
+    index inside it is v - run_bounds[r] (step 6 keeps this provenance)."""
+    P = effective_partitions(n, P)
+    bounds = run_bounds(n, P)
+    v = vals.astype(np.int64)
+    r = np.searchsorted(bounds, v, side="right") - 1
+    return r.astype(np.int64), (v - bounds[r]).astype(np.int64)
