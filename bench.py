@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--tile-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="merge tile shape (0 = default; see pgs_config.tile_variant)")
     ap.add_argument("--samples-per-run", type=int, default=0, help="regular samples per run (0 = the paper's budget)")
+    ap.add_argument("--search-queries", type=int, default=0,
+                    help="time pgs_search of this many queries on the sorted workload instead")
     ap.add_argument("--sweep-samples", action="store_true",
                     help="time the sort at the paper's sample sizes 0.004X .. 1.4X (X = 256 KB / P) instead")
     ap.add_argument("--no-e2e", action="store_true")
@@ -443,10 +445,81 @@ def run_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def run_search(args):
+    """pgs_search on the sorted workload: M queries (half of them keys of the
+    array, half fresh draws of the same generator), lower bound plus bucket,
+    CUDA-event time over the steps; checked against the oracle on a sample."""
+    import torch
+    from paper_1611_00463_gb300 import build as pbuild
+    from paper_1611_00463_gb300 import pgs
+    from oracle import pgs_oracle as O
+    pbuild.build()
+    pgs.load()
+    dev = torch.device("cuda", 0)
+    dtype, n, P, gen, seed = workload_shape(args)
+    keys_np = gen(n, seed)
+    kin = pgs.as_device_keys(keys_np, dtype, dev)
+    kout = torch.empty_like(kin)
+    cfg0 = pgs.make_config(dtype=dtype)
+    ws = pgs.workspace(n, P, cfg0, dev)
+    e = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    pgs.pgs_sort_copy(kin, None, kout, None, P, pgs.make_config(dtype=dtype, workspace=ws, bucket_bounds=e))
+    torch.cuda.synchronize(dev)
+    del ws
+    M = args.search_queries
+    g = np.random.default_rng(seed + 99)
+    hit_idx = torch.from_numpy(g.integers(0, n, size=M // 2)).to(dev)
+    fresh = pgs.as_device_keys(gen(M - M // 2, seed + 100), dtype, dev)
+    q = torch.cat([kout[hit_idx], fresh])
+    q = q[torch.from_numpy(g.permutation(M)).to(dev)].contiguous()
+    pos = torch.empty(M, dtype=torch.int64, device=dev)
+    bkt = torch.empty(M, dtype=torch.int32, device=dev)
+    sws = torch.empty(max(1, pgs.pgs_search_workspace_bytes(n, dtype)), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    # The plain bisection once, for comparison with the indexed search timed below.
+    t_plain = []
+    for k in range(max(args.warmup, 0) + 2):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pgs.pgs_search(kout, q, pos, dtype=dtype, bucket_bounds=e, bucket_out=bkt, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_plain.append(ev0.elapsed_time(ev1))
+    for _ in range(max(args.warmup, 0)):
+        pgs.pgs_search(kout, q, pos, dtype=dtype, bucket_bounds=e, bucket_out=bkt, workspace=sws, stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            pgs.pgs_search(kout, q, pos, dtype=dtype, bucket_bounds=e, bucket_out=bkt, workspace=sws, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # Oracle check on a sample of the queries (the sorted array is the CUDA sort's output).
+    samp = torch.from_numpy(g.integers(0, M, size=min(M, 1 << 16))).to(dev)
+    sorted_np = pgs.to_numpy_keys(kout, dtype)
+    q_np = pgs.to_numpy_keys(q[samp].contiguous(), dtype)
+    want = O.search(sorted_np, q_np, dtype, "left")
+    ok = bool(np.array_equal(pos[samp].cpu().numpy(), want) and
+              np.array_equal(bkt[samp].cpu().numpy(), O.bucket_of(want, e.cpu().numpy())))
+    line = {"mode": "search", "metric": "Gqueries/s (pgs_search lower bound + bucket on the sorted workload)",
+            "value": M / (ms * 1e-3) / 1e9, "unit": "Gqueries/s", "ms_per_step": ms, "queries": M, "n": n, "P": P,
+            "key": dtype, "workload": args.workload, "steps": args.steps, "warmup": args.warmup,
+            "sample_checked_against_oracle": ok, "clocks": clocks.summary(),
+            "index": "every 64th key copied to the workspace (rebuilt every call, inside the timed region)",
+            "plain_bisection": {"ms": min(t_plain[-2:]), "value": M / (min(t_plain[-2:]) * 1e-3) / 1e9},
+            "queries_recipe": "half keys of the sorted array at random positions, half fresh draws of the same "
+                              "generator, shuffled"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.sweep_samples:
         return run_sweep(args)
+    if args.search_queries:
+        return run_search(args)
     if args.impl == "reference":
         run_reference(args)
         return

@@ -292,6 +292,38 @@ size_t pgs_fit_workspace_bytes(uint64_t m, uint32_t P, const pgs_config* cfg);
 int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
                       const pgs_config* cfg, void* splitters_out, float* model_out);
 
+/* Bytes of device workspace pgs_search can use for n sorted keys (0: it uses
+ * none at this size).  With that much cfg->workspace the search first bisects a
+ * compact copy of every 64th key, which stays in L2, then one 64-key block of
+ * the array (a plain bisection of a large array misses in L2 on most of its
+ * lower levels). */
+size_t pgs_search_workspace_bytes(uint64_t n, const pgs_config* cfg);
+
+/* Binary search on sorted output (Section IV-C: the library lets its users
+ * search the sorted data).
+ *   keys: n keys of cfg->dtype (cfg may be NULL: u32) sorted by key order, e.g.
+ *   a pgs_sort output (float32 by IEEE totalOrder of the bits); queries: m keys
+ *   of the same type.  side 0 = lower bound (the number of keys ordered before
+ *   the query), 1 = upper bound (ordered before or equal).  pos_out: m uint64.
+ *   bucket_bounds (the sort's e[0..P]) and bucket_out (m uint32) are both NULL
+ *   or both set: bucket_out[i] = the bucket b with e[b] <= pos < e[b+1], or P
+ *   for pos = n.  cfg->workspace (optional, 256-byte aligned): scratch of
+ *   pgs_search_workspace_bytes(n, cfg) bytes for the indexed search; without
+ *   it (or smaller) the search bisects the array directly, same results.  All
+ *   pointers device memory; asynchronous on stream; allocates nothing. */
+int pgs_search(const void* keys, uint64_t n, const void* queries, uint64_t m, int side,
+               const uint64_t* bucket_bounds, uint32_t P, uint64_t* pos_out, uint32_t* bucket_out,
+               void* stream, const pgs_config* cfg);
+
+/* Previous processor and index of sorted entries whose payload is their input
+ * position (Section IV step 6 keeps this provenance): for v = vals[i] < n,
+ * run_out[i] = r with floor(r n / P') <= v < floor((r+1) n / P'),
+ * P' = max(1, min(P, n)), and index_out[i] = v - floor(r n / P'); v >= n gives
+ * run P' and index v - n.  run_out or index_out may be NULL (not both).  All
+ * pointers device memory; asynchronous on stream. */
+int pgs_provenance(const uint32_t* vals, uint64_t m, uint64_t n, uint32_t P, uint32_t* run_out,
+                   uint64_t* index_out, void* stream);
+
 /* Copy a device pgs_stats to host memory; synchronises `stream` and returns
  * PGS_ERR_TIMEOUT if the device error word reports an expired wait, PGS_ERR_CUDA
  * if it reports any other device-side inconsistency. */

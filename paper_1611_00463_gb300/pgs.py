@@ -83,6 +83,12 @@ EXPORTS = {
     "pgs_host_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
     "pgs_sort_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_search": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "pgs_search_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_void_p]),
+    "pgs_provenance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pgs_fit_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
     "pgs_fit_splitters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -299,6 +305,35 @@ def pgs_sort_host(keys_in: torch.Tensor, vals_in: torch.Tensor | None, keys_out:
         raise ValueError("length mismatch")
     _check(load().pgs_sort_host(_host_ptr(keys_in), _host_ptr(vals_in), _host_ptr(keys_out), _host_ptr(vals_out),
                                 n, P, _stream(stream), ctypes.byref(cfg)), "pgs_sort_host")
+
+
+def pgs_search_workspace_bytes(n: int, dtype: str = "u32") -> int:
+    cfg = make_config(dtype=dtype)
+    return load().pgs_search_workspace_bytes(n, ctypes.byref(cfg))
+
+
+def pgs_search(keys: torch.Tensor, queries: torch.Tensor, pos_out: torch.Tensor, side: str = "left",
+               dtype: str = "u32", bucket_bounds: torch.Tensor | None = None, bucket_out: torch.Tensor | None = None,
+               workspace: torch.Tensor | None = None, stream=None) -> None:
+    """Lower ("left") or upper ("right") bound of every query in sorted keys;
+    with the sort's bucket bounds, also the bucket holding each position.  A
+    workspace of pgs_search_workspace_bytes(n) bytes enables the indexed search."""
+    if side not in ("left", "right"):
+        raise ValueError(side)
+    P = bucket_bounds.numel() - 1 if bucket_bounds is not None else 0
+    if pos_out.numel() != queries.numel() or (bucket_out is not None and bucket_out.numel() != queries.numel()):
+        raise ValueError("length mismatch")
+    cfg = make_config(dtype=dtype, workspace=workspace)
+    _check(load().pgs_search(_ptr(keys) if keys.numel() else None, keys.numel(), _ptr(queries), queries.numel(),
+                             1 if side == "right" else 0, _ptr(bucket_bounds), P, _ptr(pos_out), _ptr(bucket_out),
+                             _stream(stream), ctypes.byref(cfg)), "pgs_search")
+
+
+def pgs_provenance(vals: torch.Tensor, n: int, P: int, run_out: torch.Tensor | None, index_out: torch.Tensor | None,
+                   stream=None) -> None:
+    """Previous processor (run) and index of entries whose payload is their input position."""
+    _check(load().pgs_provenance(_ptr(vals), vals.numel(), n, P, _ptr(run_out), _ptr(index_out), _stream(stream)),
+           "pgs_provenance")
 
 
 STATIC_MAX_KEYS = 1 << 16
