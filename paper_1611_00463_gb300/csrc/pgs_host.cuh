@@ -473,7 +473,8 @@ int learned_cuts(const Shape& sh, const Options& o, const K* sorted, const K* ru
         k_mlp_grad<K><<<nparts, kMlpBatch, sizeof(MlpGradSmem), st>>>(sorted, S, b.mlp, b.mlp_part);
       }));
       PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 4ull * nparts * (kMlpW + 1), [&] {
-        k_mlp_adam<<<1, 1024, 0, st>>>(b.mlp_part, nparts, b.mlp, step, S);
+        k_mlp_adam<<<(unsigned)ceil_div(kMlpW + 1, kAdamParams), kAdamParams * kAdamWarps, 0, st>>>(
+            b.mlp_part, nparts, b.mlp, step, S);
       }));
     }
     PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 16 * kMlpW, [&] { k_mlp_finalize<<<1, 256, 0, st>>>(b.mlp, b.model); }));
@@ -951,7 +952,8 @@ int run_fit(uint64_t m, uint32_t P, const Options& o, const K* samples, K* split
       k_mlp_grad<K><<<nparts, kMlpBatch, sizeof(MlpGradSmem), st>>>(ordered, m, mlp, part);
     }));
     PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 4ull * nparts * (kMlpW + 1), [&] {
-      k_mlp_adam<<<1, 1024, 0, st>>>(part, nparts, mlp, step, m);
+      k_mlp_adam<<<(unsigned)ceil_div(kMlpW + 1, kAdamParams), kAdamParams * kAdamWarps, 0, st>>>(
+          part, nparts, mlp, step, m);
     }));
   }
   return launch(c, PGS_KERNEL_SPLITTERS, 3, 16 * kMlpW, [&] { k_mlp_finalize<<<1, 256, 0, st>>>(mlp, model_out); });

@@ -189,56 +189,80 @@ k_mlp_grad(const K* __restrict__ sorted, uint64_t S, const MlpState* __restrict_
   sm.dy[tid] = dy;
   sm.r2[tid] = r * r;
   __syncthreads();
+  // Sums over the CTA's samples in four interleaved chains (s mod 4), added in a
+  // fixed order at the end: four independent FMA chains per parameter.
   float* out = part + (uint64_t)blockIdx.x * (kMlpW + 1);
+  auto sum4 = [](auto term) {
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+#pragma unroll 4
+    for (int s = 0; s < kMlpBatch; s += 4) {
+      a0 += term(s);
+      a1 += term(s + 1);
+      a2 += term(s + 2);
+      a3 += term(s + 3);
+    }
+    return (a0 + a1) + (a2 + a3);
+  };
+  static_assert(kMlpBatch % 4 == 0, "four chains");
   for (int p = tid; p <= kMlpW; p += blockDim.x) {
     float g = 0.0f;
     if (p < kMlpOffB1) {
-      for (int s = 0; s < kMlpBatch; ++s) g += sm.dz1[s][p] * sm.x[s];
-      g *= sm.w[p];
+      g = sum4([&](int s) { return sm.dz1[s][p] * sm.x[s]; }) * sm.w[p];
     } else if (p < kMlpOffW2) {
-      for (int s = 0; s < kMlpBatch; ++s) g += sm.dz1[s][p - kMlpOffB1];
+      const int q = p - kMlpOffB1;
+      g = sum4([&](int s) { return sm.dz1[s][q]; });
     } else if (p < kMlpOffB2) {
       const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
-      if (same_half(k, j)) {
-        for (int s = 0; s < kMlpBatch; ++s) g += sm.dz2[s][k] * sm.h1[s][j];
-        g *= sm.w[p];
-      }
+      if (same_half(k, j)) g = sum4([&](int s) { return sm.dz2[s][k] * sm.h1[s][j]; }) * sm.w[p];
     } else if (p < kMlpOffW3) {
-      for (int s = 0; s < kMlpBatch; ++s) g += sm.dz2[s][p - kMlpOffB2];
+      const int q = p - kMlpOffB2;
+      g = sum4([&](int s) { return sm.dz2[s][q]; });
     } else if (p < kMlpOffB3) {
-      for (int s = 0; s < kMlpBatch; ++s) g += sm.dy[s] * sm.h2[s][p - kMlpOffW3];
-      g *= sm.w[p];
+      const int q = p - kMlpOffW3;
+      g = sum4([&](int s) { return sm.dy[s] * sm.h2[s][q]; }) * sm.w[p];
     } else if (p == kMlpOffB3) {
-      for (int s = 0; s < kMlpBatch; ++s) g += sm.dy[s];
+      g = sum4([&](int s) { return sm.dy[s]; });
     } else {
-      for (int s = 0; s < kMlpBatch; ++s) g += sm.r2[s];
+      g = sum4([&](int s) { return sm.r2[s]; });
     }
     out[p] = g;
   }
 }
 
-// One CTA: sum the partial gradients in CTA order, then one Adam step
-// (beta1 0.9, beta2 0.999, eps 1e-8).  Entries of W2 across halves stay 0.
-static __global__ void __launch_bounds__(1024)
+// Sum the partial gradients and take one Adam step (beta1 0.9, beta2 0.999,
+// eps 1e-8); entries of W2 across halves stay 0.  CTA b owns parameters
+// [32 b, 32 b + 32): lane l of warp w sums partials w, w + 8, ... of parameter
+// 32 b + l, and the eight warp sums are added in warp order (a fixed order).
+constexpr int kAdamParams = 32;
+constexpr int kAdamWarps = 8;
+static __global__ void __launch_bounds__(kAdamParams * kAdamWarps)
 k_mlp_adam(const float* __restrict__ part, uint32_t nparts, MlpState* st, uint32_t step, uint64_t S) {
-  const float c1 = 1.0f - powf(0.9f, (float)step), c2 = 1.0f - powf(0.999f, (float)step);
-  for (int p = threadIdx.x; p <= kMlpW; p += blockDim.x) {
-    float g = 0.0f;
-    for (uint32_t c = 0; c < nparts; ++c) g += part[(uint64_t)c * (kMlpW + 1) + p];
-    if (p == kMlpW) {
-      st->loss = g / (float)S;
-      continue;
-    }
-    if (p >= kMlpOffW2 && p < kMlpOffB2) {
-      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
-      if (!same_half(k, j)) continue;
-    }
-    const float m = 0.9f * st->m[p] + 0.1f * g;
-    const float v = 0.999f * st->v[p] + 0.001f * g * g;
-    st->m[p] = m;
-    st->v[p] = v;
-    st->raw[p] -= kMlpLr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+  __shared__ float sums[kAdamWarps][kAdamParams];
+  const int lane = threadIdx.x % kAdamParams, warp = threadIdx.x / kAdamParams;
+  const int p = blockIdx.x * kAdamParams + lane;
+  float g = 0.0f;
+  if (p <= kMlpW)
+    for (uint32_t c = warp; c < nparts; c += kAdamWarps) g += part[(uint64_t)c * (kMlpW + 1) + p];
+  sums[warp][lane] = g;
+  __syncthreads();
+  if (warp != 0 || p > kMlpW) return;
+  g = 0.0f;
+#pragma unroll
+  for (int w = 0; w < kAdamWarps; ++w) g += sums[w][lane];
+  if (p == kMlpW) {
+    st->loss = g / (float)S;
+    return;
   }
+  if (p >= kMlpOffW2 && p < kMlpOffB2) {
+    const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
+    if (!same_half(k, j)) return;
+  }
+  const float c1 = 1.0f - powf(0.9f, (float)step), c2 = 1.0f - powf(0.999f, (float)step);
+  const float m = 0.9f * st->m[p] + 0.1f * g;
+  const float v = 0.999f * st->v[p] + 0.001f * g * g;
+  st->m[p] = m;
+  st->v[p] = v;
+  st->raw[p] -= kMlpLr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
 }
 
 // Effective weights and normalisation of the trained model.
