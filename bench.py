@@ -134,6 +134,22 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x: float, device, world: int) -> float:
+    """The largest of every rank's value (a time: the job ends with its slowest rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(keys_per_rank: int, world: int, seconds: float) -> float:
+    """Gkeys/s of the whole job: every rank's keys over the slowest rank's time (weak scaling)."""
+    return keys_per_rank * world / seconds / 1e9
+
+
 def kernel_source_hash(kernel: str = "k_merge_tile") -> str:
     """Hash of one kernel's source text (its template header to its closing
     brace) plus the PTX helpers it uses, so committed counters are used only
@@ -333,12 +349,8 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
-    ms_step = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = n * world / (ms_step * 1e-3) / 1e9
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev, world)
+    value = whole_job_rate(n, world, ms_step * 1e-3)
     # The same instances, one pgs_sort_copy call (its own launch sequence) each.
     per = None
     if rank == 0:
@@ -580,13 +592,9 @@ def main():
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), dev, world)
     ms_step = ms_total / args.steps
-    value = n * world / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(n, world, ms_step * 1e-3)
 
     # Dominant kernel and its roofline, from the launch timer of the timed region.
     peak, peak_src = peaks()
@@ -633,11 +641,7 @@ def main():
         for _ in range(k_e2e):
             pgs.sort(hk, hv, P, out=(ko, vo), **opts)
         torch.cuda.synchronize(dev)
-        dt = (time.perf_counter() - t0) / k_e2e
-        if world > 1:
-            t = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / k_e2e, dev, world)
         # Steady state: two calls in flight, each on its own stream with its own
         # workspace and output buffers, so one call's copy to the device overlaps
         # the previous call's merge and copy back (the copy engines of the two
@@ -663,18 +667,14 @@ def main():
         for k in range(k_pipe):
             call(k)
         torch.cuda.synchronize(dev)
-        dt_pipe = (time.perf_counter() - t0) / k_pipe
-        if world > 1:
-            t = torch.tensor([dt_pipe], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt_pipe = float(t.item())
+        dt_pipe = max_over_ranks((time.perf_counter() - t0) / k_pipe, dev, world)
         same = all(torch.equal(ln[2], ko) and torch.equal(ln[3], vo) for ln in lanes)
         del lanes, cfgs
         nbytes = n * (kin.element_size() + 4)
-        e2e = {"value": n * world / dt_pipe / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": nbytes,
+        e2e = {"value": whole_job_rate(n, world, dt_pipe), "unit": "Gkeys/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": dt_pipe * 1e3, "in_flight": 2,
                "outputs_equal_single_call": same,
-               "single_call": {"value": n * world / dt / 1e9, "ms": dt * 1e3},
+               "single_call": {"value": whole_job_rate(n, world, dt), "ms": dt * 1e3},
                "api": "pgs_sort_host (C ABI, host buffers): pinned host keys/payloads in and out, "
                       "host-to-device copies in run groups overlapped with step 1, device-to-host copies "
                       "in bucket groups overlapped with step 6, all inside the call; two calls in flight "
