@@ -124,3 +124,27 @@ def test_host_sorts_in_flight_on_two_streams():
         want_k, want_v = O.stable_sort(keys, vals, "u64")
         assert np.array_equal(ko.numpy().view(np.uint64), want_k)
         assert np.array_equal(vo.numpy().view(np.uint32), want_v)
+
+
+@pytest.mark.parametrize("opts,P", [({"merge_ways": 4}, 64), ({"merge_ways": 4}, 32), ({"exchange": "scatter"}, 16),
+                                    ({"exchange": "scatter", "merge_ways": 4}, 128), ({"splitters": "learned"}, 24),
+                                    ({"investigator": "local"}, 12), ({"guaranteed": True}, 40), ({}, 2), ({}, 3)])
+def test_host_sort_bucket_groups_with_every_option(opts, P):
+    """Step 6 in bucket groups under four-way rounds, the scatter exchange,
+    learned splitters and every P shape (bucket rounds after the first: none,
+    odd, even)."""
+    n = 4 * TILE * 9 + 123
+    keys = inputs.zipf_dup_f32(n, P)
+    vals = inputs.index_payload(n)
+    got_k, got_v, e, _, _ = run_host(keys, vals, P, "f32", **opts)
+    if opts.get("investigator") == "local":
+        ref = O.sample_sort(keys, vals, P, "f32", variant=O.INVESTIGATOR_LOCAL)
+        assert np.array_equal(got_k, ref["keys"]) and np.array_equal(got_v, ref["vals"])
+        assert np.array_equal(e, ref["e"])
+        return
+    want_k, want_v = O.stable_sort(keys, vals, "f32")
+    assert np.array_equal(got_k, want_k) and np.array_equal(got_v, want_v)
+    if "splitters" not in opts:
+        s = (max(O.paper_samples_per_run(P, 4), O.guaranteed_samples_per_run(P, 0.05))
+             if opts.get("guaranteed") else None)
+        assert np.array_equal(e, O.buckets(keys, P, "f32", samples_per_run=s)["e"])
