@@ -45,7 +45,7 @@ typedef enum {
   PGS_ERR_WORKSPACE = -2,    /* workspace NULL, misaligned (needs 256 B) or too small */
   PGS_ERR_CUDA = -3,         /* a CUDA runtime call or launch failed */
   PGS_ERR_TIMEOUT = -4,      /* a bounded device-side wait ran out */
-  PGS_ERR_UNSUPPORTED = -5   /* valid request this build does not implement */
+  PGS_ERR_UNSUPPORTED = -5   /* valid request the library does not implement */
 } pgs_status;
 
 /* Investigator variants (Section IV-B).  With e_b the number of stable ranks
