@@ -578,8 +578,7 @@ def main():
     torch.cuda.synchronize(dev)
     stats = pgs.pgs_get_stats(st, stream)
 
-    if timer:
-        timer.reset()
+    # The timed region: the steps exactly as a caller runs them.
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clocks:
         if world > 1:
@@ -587,7 +586,7 @@ def main():
         torch.cuda.synchronize(dev)
         ev0.record(stream)
         for _ in range(args.steps):
-            pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_timed if timer else cfg_plain, stream)
+            pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_plain, stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         if world > 1:
@@ -595,6 +594,45 @@ def main():
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), dev, world)
     ms_step = ms_total / args.steps
     value = whole_job_rate(n, world, ms_step * 1e-3)
+
+    # The same steps again with a CUDA-event pair around every launch on the
+    # sort's stream: the per-kernel durations of the roofline and the per-step
+    # breakdown (the events themselves add a little time between launches).
+    ms_instr = None
+    if timer:
+        timer.reset()
+        torch.cuda.synchronize(dev)
+        iev0, iev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iev0.record(stream)
+        for _ in range(args.steps):
+            pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_timed, stream)
+        iev1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_instr = iev0.elapsed_time(iev1) / args.steps
+
+    # The same sort replayed from a CUDA graph (captured once): what the launch
+    # sequence costs without the host's per-launch work, reported beside it.
+    graph = None
+    try:
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=gs):
+            pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_plain, gs)
+        for _ in range(max(args.warmup, 1)):
+            cg.replay()
+        torch.cuda.synchronize(dev)
+        gev0, gev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gev0.record(torch.cuda.current_stream(dev))
+        for _ in range(args.steps):
+            cg.replay()
+        gev1.record(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize(dev)
+        gms = max_over_ranks(gev0.elapsed_time(gev1) / args.steps, dev, world)
+        graph = {"ms_per_step": gms, "value": whole_job_rate(n, world, gms * 1e-3), "unit": "Gkeys/s"}
+        del cg
+    except RuntimeError as ex:                           # capture unavailable: report why, keep the line
+        graph = {"unavailable": str(ex).splitlines()[0][:200]}
 
     # Dominant kernel and its roofline, from the launch timer of the timed region.
     peak, peak_src = peaks()
@@ -618,7 +656,8 @@ def main():
                 "frac": achieved / peak, "traffic": traffic, "bytes_per_launch": per_launch,
                 "avg_launch_ms": avg_ms, "launches_counted": len(sel), "peak_source": peak_src,
                 "note": "achieved = algorithmic bytes (read + write of every key and payload) per "
-                        "full-size launch / mean CUDA-event duration"}
+                        "full-size launch / mean CUDA-event duration, events around every launch on the sort's "
+                        "stream in a second pass of the timed steps"}
         for k in per_kernel:
             per_kernel[k]["share"] = per_kernel[k]["ms"] / sum(v["ms"] for v in per_kernel.values())
     bytes_per_pass = 2 * n * (kin.element_size() + 4)
@@ -703,6 +742,8 @@ def main():
             "launches_per_step": stats["launches"],
             "clocks": clocks.summary(),
             "e2e": e2e,
+            "graph_replay": graph,
+            "instrumented_ms_per_step": ms_instr,
             "cpu_baseline": cpu,
             "per_kernel": per_kernel,
             "per_step_ms": {str(k): v / args.steps for k, v in sorted(step_ms.items())},

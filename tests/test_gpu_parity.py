@@ -233,3 +233,38 @@ def test_local_investigator_matches_oracle_pipeline(dtype, n, P, s):
     assert np.array_equal(got["keys"], ref["keys"]) and np.array_equal(got["vals"], ref["vals"])
     assert np.array_equal(got["e"], ref["e"]) and np.array_equal(got["cut"], ref["cut"])
     assert np.array_equal(got["keys"], O.stable_sort(keys, vals, dtype)[0])
+
+
+@pytest.mark.parametrize("dtype,n,P", [("u32", 1 << 20, 16), ("f32", 100_003, 7)])
+def test_single_sort_replays_from_a_cuda_graph(dtype, n, P):
+    """A single sort captured once into a CUDA graph (after one direct call has
+    set the kernels' attributes) and replayed twice from fresh input."""
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    gen = {"u32": inputs.uniform_u32, "f32": inputs.zipf_dup_f32}[dtype]
+    keys = gen(n, 77)
+    vals = inputs.index_payload(n)
+    kin = pgs.as_device_keys(keys, dtype)
+    vin = torch.from_numpy(vals.view(np.int32)).cuda()
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    cfg0 = pgs.make_config(dtype=dtype)
+    ws = pgs.workspace(n, P, cfg0)
+    bounds = torch.zeros(P + 1, dtype=torch.int64, device="cuda")
+    cfg = pgs.make_config(dtype=dtype, workspace=ws, bucket_bounds=bounds)
+    pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg)           # first call on the device: attributes set here
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg, stream=s)
+    want_k, want_v = O.stable_sort(keys, vals, dtype)
+    for _ in range(2):
+        kout.zero_()
+        vout.zero_()
+        bounds.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(pgs.to_numpy_keys(kout, dtype), want_k)
+        assert np.array_equal(vout.cpu().numpy().view(np.uint32), want_v)
+        assert np.array_equal(bounds.cpu().numpy(), O.buckets(keys, P, dtype)["e"])
