@@ -533,39 +533,82 @@ struct HostGroups {
   cudaEvent_t done = nullptr;          // recorded on cs after the last output copy
 };
 
-// The launch sequence itself (no attribute or allocation calls, so it can be
-// captured into a CUDA graph once set_all_smem_attrs has run on the device).
+// One sort's launch sequence, step by step (Section IV).  The keys move
+// between the caller's output and the workspace's alternate buffer on every
+// full pass; `left` counts the passes still to come, and the pass that leaves
+// none writes the caller's output, with float keys back in their own bits.
+// No attribute or allocation calls: the sequence can be captured into a CUDA
+// graph once set_all_smem_attrs has run on the device.
 template <typename K, bool V>
-int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
-                 Ctx& c, const Buffers& b, const HostGroups* hg = nullptr) {
-  cudaStream_t st = c.st;
-  c.variant = o.tile_variant;
-  const Geo g = b.geo(sh);
-  const uint64_t n = sh.n;
-  const uint32_t R = sh.R;
-  const int f32 = o.dtype == PGS_F32;
-  const uint64_t kv = sizeof(K) + (V ? 4 : 0);       // bytes per key/payload pair
-  PGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), st));
+struct Pipeline {
+  const Shape& sh;
+  const Options& o;
+  Ctx& c;
+  const Buffers& b;
+  const Geo g;
+  const K* kin;
+  const uint32_t* vin;
+  K* kout;
+  uint32_t* vout;
+  cudaStream_t st;
+  int f32;
+  uint64_t kv;                                         // bytes per key/payload pair
+  uint32_t mtile;                                      // outputs per merge tile
+  K* cur_k;
+  K* oth_k;
+  uint32_t* cur_v;
+  uint32_t* oth_v;
+  int left;
+  int k0 = 0;                                          // bucket rounds already done by step 5
 
-  // Ping-pong so that the last pass lands in kout.
-  const int after_block = sh.passes - 1;
-  K* cur_k = (after_block % 2 == 0) ? kout : static_cast<K*>(b.alt_k);
-  K* oth_k = (cur_k == kout) ? static_cast<K*>(b.alt_k) : kout;
-  uint32_t* cur_v = V ? ((after_block % 2 == 0) ? vout : b.alt_v) : nullptr;
-  uint32_t* oth_v = V ? ((cur_v == vout) ? b.alt_v : vout) : nullptr;
-  int left = after_block;
+  struct Saved {
+    K* ck;
+    K* ok;
+    uint32_t* cv;
+    uint32_t* ov;
+    int left;
+  };
 
-  // Step 1: local sort of every run.  Block sort of kTile tiles ...
-  const uint32_t tiles_per_run = (uint32_t)std::max<uint64_t>(1, ceil_div(sh.maxlen, kTile));
-  // Runs [r0, r0 + Rg) holding len keys; every group goes through the same rounds.
-  auto sort_runs = [&](uint32_t r0, uint32_t Rg, uint64_t len) -> int {
+  Pipeline(const Shape& sh_, const Options& o_, const K* kin_, const uint32_t* vin_, K* kout_, uint32_t* vout_,
+           Ctx& c_, const Buffers& b_)
+      : sh(sh_), o(o_), c(c_), b(b_), g(b_.geo(sh_)), kin(kin_), vin(vin_), kout(kout_), vout(vout_), st(c_.st) {
+    c.variant = o.tile_variant;
+    f32 = o.dtype == PGS_F32;
+    kv = sizeof(K) + (V ? 4 : 0);
+    mtile = (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt);
+    // Ping-pong so that the last pass lands in kout.
+    const int after_block = sh.passes - 1;
+    cur_k = (after_block % 2 == 0) ? kout : static_cast<K*>(b.alt_k);
+    oth_k = (cur_k == kout) ? static_cast<K*>(b.alt_k) : kout;
+    cur_v = V ? ((after_block % 2 == 0) ? vout : b.alt_v) : nullptr;
+    oth_v = V ? ((cur_v == vout) ? b.alt_v : vout) : nullptr;
+    left = after_block;
+  }
+
+  Saved save() const { return Saved{cur_k, oth_k, cur_v, oth_v, left}; }
+  void restore(const Saved& s) {
+    cur_k = s.ck;
+    oth_k = s.ok;
+    cur_v = s.cv;
+    oth_v = s.ov;
+    left = s.left;
+  }
+  void flip() {
+    std::swap(cur_k, oth_k);
+    std::swap(cur_v, oth_v);
+  }
+  int f32_out() const { return left == 0 ? f32 : 0; }   // float bits back on the last pass
+
+  // Step 1 for runs [r0, r0 + Rg) holding len keys: block sort of kTile tiles,
+  // then the balanced merge tree (Fig. 2) until each run is one list: two
+  // levels per pass (four-way rounds) while two remain, else a pairwise round.
+  int sort_runs(uint32_t r0, uint32_t Rg, uint64_t len) {
+    const uint32_t tiles_per_run = (uint32_t)std::max<uint64_t>(1, ceil_div(sh.maxlen, kTile));
     const uint64_t* ro = b.run_off + r0;
     PGS_TRY(launch(c, PGS_KERNEL_BLOCK_SORT, 1, 2 * len * kv, [&] {
       k_block_sort<K, V><<<(unsigned)((uint64_t)Rg * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
-          kin, vin, cur_k, cur_v, ro, tiles_per_run, f32, left == 0 ? f32 : 0);
+          kin, vin, cur_k, cur_v, ro, tiles_per_run, f32, f32_out());
     }));
-    // ... then the balanced merge tree (Fig. 2) until each run is one list: two
-    // levels per pass (four-way rounds) while two remain, else a pairwise round.
     uint64_t w = kTile;
     int levels = sh.run_rounds;
     while (levels > 0) {
@@ -576,43 +619,43 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 80 * nq, [&] {
           k_quads_runs<<<grid_for(nq, 256), 256, 0, st>>>(b.quads, b.ccount, ro, Rg, w, cmax, kMerge4Cut);
         }));
-        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, len, b, left == 0 ? f32 : 0, 1)));
+        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, len, b, f32_out(), 1)));
         w *= 4;
         levels -= 2;
       } else {
         const uint64_t cmax = ceil_div(sh.maxlen, 2 * w);
         const uint64_t np = cmax * Rg;
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
-          k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, ro, Rg, w, cmax,
-                                                          (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
+          k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, ro, Rg, w, cmax, mtile);
         }));
-        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, len, b, left == 0 ? f32 : 0, 1)));
+        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, len, b, f32_out(), 1)));
         w *= 2;
         levels -= 1;
       }
-      std::swap(cur_k, oth_k);
-      std::swap(cur_v, oth_v);
+      flip();
     }
     return PGS_OK;
-  };
-  if (hg == nullptr || hg->groups == 0) {
-    PGS_TRY(sort_runs(0, R, n));
-  } else {
-    K* const ck = cur_k;
-    K* const okk = oth_k;
-    uint32_t* const cv = cur_v;
-    uint32_t* const ov = oth_v;
-    const int left0 = left;
-    for (uint32_t gi = 0; gi < hg->groups; ++gi) {
-      cur_k = ck; oth_k = okk; cur_v = cv; oth_v = ov; left = left0;
-      const uint32_t r0 = hg->r0[gi], r1 = hg->r0[gi + 1];
-      PGS_CUDA(cudaStreamWaitEvent(st, hg->ev[gi], 0));
-      PGS_TRY(sort_runs(r0, r1 - r0, host_run_start(r1, n, R) - host_run_start(r0, n, R)));
-    }
   }
 
-  if (sh.Pmax > 1) {
-    // Step 2: regular samples of every sorted run, gathered in (run, position) order.
+  // Step 1 for every run; with host groups, group by group as their copies land.
+  int local_sort(const HostGroups* hg) {
+    if (hg == nullptr || hg->groups == 0) return sort_runs(0, sh.R, sh.n);
+    const Saved s0 = save();
+    for (uint32_t gi = 0; gi < hg->groups; ++gi) {
+      restore(s0);
+      const uint32_t r0 = hg->r0[gi], r1 = hg->r0[gi + 1];
+      PGS_CUDA(cudaStreamWaitEvent(st, hg->ev[gi], 0));
+      PGS_TRY(sort_runs(r0, r1 - r0, host_run_start(r1, sh.n, sh.R) - host_run_start(r0, sh.n, sh.R)));
+    }
+    return PGS_OK;
+  }
+
+  // Step 2: regular samples of every sorted run, gathered in (run, position)
+  // order.  Step 3: the Master sorts the samples (merging each instance's P
+  // sorted sample lists with the Fig. 2 schedule) and picks every (S/P)-th one.
+  // Returns the sorted samples.
+  int sample_and_splitters(K** sorted_sample) {
+    const uint32_t R = sh.R;
     K* sa = static_cast<K*>(b.samp_a);
     K* sb = static_cast<K*>(b.samp_b);
     PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 16 * (uint64_t)R, [&] {
@@ -622,13 +665,10 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
     PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 2 * sh.S * sizeof(K), [&] {
       k_sample<K><<<grid_for(sh.S, 256), 256, 0, st>>>(cur_k, g, b.samp_off, sa, sh.S);
     }));
-    // Step 3: the Master sorts the samples (merging each instance's P sorted
-    // sample lists with the Fig. 2 schedule) and picks every (S/P)-th one.
     for (int k = 0; k < sh.bucket_rounds; ++k) {
       const uint32_t step = 1u << k;
       PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 3, 32 * (uint64_t)R, [&] {
-        k_pairs_sample_lists<<<grid_for(R, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.samp_off, step,
-                                                               (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt));
+        k_pairs_sample_lists<<<grid_for(R, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.samp_off, step, mtile);
       }));
       PGS_TRY((merge_round<K, false>(c, sa, nullptr, sb, nullptr, R, sh.S, b, 0, 3)));
       std::swap(sa, sb);
@@ -637,7 +677,15 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       k_pick_splitters<K><<<grid_for(R, 256), 256, 0, st>>>(sa, g, b.samp_off, static_cast<K*>(b.spl),
                                                             static_cast<K*>(o.splitters), f32);
     }));
-    // Step 4: binary search of every splitter in every run, then the investigator.
+    *sorted_sample = sa;
+    return PGS_OK;
+  }
+
+  // Step 4: binary search of every splitter in every run, then the
+  // investigator (Section IV-B); LEARNED mode adds the model's cuts and its
+  // judge.  Then the receive offset of every (bucket, run) segment (IV-C).
+  int cuts(const K* sorted_sample) {
+    const uint32_t R = sh.R;
     PGS_TRY(launch(c, PGS_KERNEL_CUT_SEARCH, 4, 16 * sh.Q, [&] {
       k_cut_search<K><<<grid_for(sh.Q, 256), 256, 0, st>>>(cur_k, g, sh.Q, static_cast<const K*>(b.spl), b.lb,
                                                            b.cnt);
@@ -649,15 +697,21 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       k_investigator<K><<<R, 256, 0, st>>>(b.lb, b.cnt, static_cast<const K*>(b.spl), g, o.investigator, b.cut,
                                            b.e);
     }));
-    if (sh.learned) PGS_TRY((learned_cuts<K>(sh, o, sa, cur_k, c, b)));
-    // Section IV-C: receive offsets of every (bucket, run) segment.
+    if (sh.learned) PGS_TRY((learned_cuts<K>(sh, o, sorted_sample, cur_k, c, b)));
     PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 32 * sh.Q, [&] {
       k_bucket_sizes<<<grid_for(sh.Q, 256), 256, 0, st>>>(g, sh.Q, b.cut, b.sizes, b.seg_src);
     }));
-    PGS_TRY(scan_u64(c, b.sizes, b.off, sh.Q, b.scan_sums, b.scan_sums2, 5));
-    const uint32_t mtile = (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt);
+    return scan_u64(c, b.sizes, b.off, sh.Q, b.scan_sums, b.scan_sums2, 5);
+  }
+
+  // Step 5.  SCATTER: the exchange as an in-HBM scatter into bucket-major
+  // order.  Otherwise fused with step 6: the first merge round of every bucket
+  // reads its two segments where the sorted runs hold them and writes the
+  // merged pair to its place in bucket-major order (all buckets at once: the
+  // runs' buffer is free only after every bucket has read its segments).
+  int exchange() {
+    const uint64_t n = sh.n;
     if (sh.scatter) {
-      // Step 5: the exchange, as an in-HBM scatter into bucket-major order.
       const uint64_t stiles = ceil_div(n, kScatterTile);
       PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 8 * stiles, [&] {
         k_scatter_part<<<grid_for(stiles, 256), 256, 0, st>>>(b.off, sh.Q, n, b.first_seg);
@@ -665,104 +719,121 @@ int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t
       --left;
       PGS_TRY(launch(c, PGS_KERNEL_SCATTER, 5, 2 * n * kv, [&] {
         k_scatter<K, V><<<(unsigned)stiles, kScatterNT, sizeof(ScatterSmem<K>), st>>>(
-            cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, left == 0 ? f32 : 0);
+            cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, f32_out());
       }));
-      std::swap(cur_k, oth_k);
-      std::swap(cur_v, oth_v);
-    }
-    int k0 = 0;
-    if (!sh.scatter) {
-      // Steps 5 and 6 fused: the first merge round of every bucket reads its
-      // two segments where the sorted runs hold them and writes the merged pair
-      // to its place in bucket-major order (all buckets at once: the runs'
-      // buffer is free only after every bucket has read its segments).
-      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 5, 48 * sh.Q, [&] {
-        k_pairs_fused<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, b.seg_src, 0, sh.Q, mtile);
-      }));
-      --left;
-      PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, left == 0 ? f32 : 0, 6)));
-      std::swap(cur_k, oth_k);
-      std::swap(cur_v, oth_v);
-      k0 = 1;
-    }
-    // Step 6 for the buckets of segment slots [q0, q0 + Qg), len keys, already
-    // in bucket-major order: every bucket merges its P segments with the Fig. 2
-    // schedule, two levels per pass while two remain.
-    auto merge_buckets = [&](uint64_t q0, uint64_t Qg, uint64_t len) -> int {
-      int levels = sh.bucket_rounds - k0;
-      uint32_t step = 1u << k0;
-      while (levels > 0) {
-        --left;
-        if (sh.four && levels >= 2) {
-          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * Qg, [&] {
-            k_quads_buckets<<<grid_for(Qg, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, q0, Qg, step,
-                                                               kMerge4Cut);
-          }));
-          PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, left == 0 ? f32 : 0, 6)));
-          step *= 4;
-          levels -= 2;
-        } else {
-          PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * Qg, [&] {
-            k_pairs_bucket_lists<<<grid_for(Qg, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, q0, Qg, step,
-                                                                     mtile);
-          }));
-          PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, left == 0 ? f32 : 0, 6)));
-          step *= 2;
-          levels -= 1;
-        }
-        std::swap(cur_k, oth_k);
-        std::swap(cur_v, oth_v);
-      }
+      flip();
+      k0 = 0;
       return PGS_OK;
-    };
-    if (hg == nullptr || hg->out_groups == 0) {
-      PGS_TRY(merge_buckets(0, sh.Q, n));
-    } else {
-      // Host-buffer sort of one instance: the bucket bounds come back once
-      // (the host waits for steps 1-5 here), then the remaining rounds run
-      // bucket group by bucket group; a group's range is final when its last
-      // round ends, and no later group writes inside it.
-      std::vector<uint64_t> e(R + 1);
-      PGS_CUDA(cudaMemcpyAsync(e.data(), b.e, (R + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-      PGS_CUDA(cudaStreamSynchronize(st));
-      K* const ck = cur_k;
-      K* const okk = oth_k;
-      uint32_t* const cv = cur_v;
-      uint32_t* const ov = oth_v;
-      const int left0 = left;
-      for (uint32_t gi = 0; gi < hg->out_groups; ++gi) {
-        cur_k = ck; oth_k = okk; cur_v = cv; oth_v = ov; left = left0;
-        const uint64_t b0 = ((uint64_t)gi * R) / hg->out_groups, b1 = ((uint64_t)(gi + 1) * R) / hg->out_groups;
-        const uint64_t lo = e[b0], hi = e[b1];
-        if (b1 > b0) PGS_TRY(merge_buckets(b0 * R, (b1 - b0) * R, hi - lo));
-        PGS_CUDA(cudaEventRecord(hg->ev_out[gi], st));
-        PGS_CUDA(cudaStreamWaitEvent(hg->cs, hg->ev_out[gi], 0));
-        if (hi > lo) {
-          PGS_CUDA(cudaMemcpyAsync(static_cast<K*>(hg->hk_out) + lo, kout + lo, (hi - lo) * sizeof(K),
-                                   cudaMemcpyDeviceToHost, hg->cs));
-          if (V) PGS_CUDA(cudaMemcpyAsync(hg->hv_out + lo, vout + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost, hg->cs));
-        }
-      }
-      PGS_CUDA(cudaEventRecord(hg->done, hg->cs));
-      PGS_CUDA(cudaStreamWaitEvent(st, hg->done, 0));
     }
-  } else {
-    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)R, [&] {
-      k_cut_edges<<<grid_for(R, 256), 256, 0, st>>>(g, b.cut, b.e);
+    PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 5, 48 * sh.Q, [&] {
+      k_pairs_fused<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, b.seg_src, 0, sh.Q, mtile);
     }));
+    --left;
+    PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, f32_out(), 6)));
+    flip();
+    k0 = 1;
+    return PGS_OK;
   }
-  if (left != 0 || cur_k != kout) return PGS_ERR_CUDA;   // plan/launch mismatch: never expected
 
-  if (o.cuts && sh.I == 1) {
-    PGS_CUDA(cudaMemcpyAsync(o.cuts, b.cut, sizeof(uint64_t) * sh.MAT, cudaMemcpyDeviceToDevice, st));
+  // Step 6 for the buckets of segment slots [q0, q0 + Qg), len keys, already
+  // in bucket-major order: every bucket merges its P segments with the Fig. 2
+  // schedule, two levels per pass while two remain.
+  int merge_buckets(uint64_t q0, uint64_t Qg, uint64_t len) {
+    int levels = sh.bucket_rounds - k0;
+    uint32_t step = 1u << k0;
+    while (levels > 0) {
+      --left;
+      if (sh.four && levels >= 2) {
+        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * Qg, [&] {
+          k_quads_buckets<<<grid_for(Qg, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, q0, Qg, step, kMerge4Cut);
+        }));
+        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6)));
+        step *= 4;
+        levels -= 2;
+      } else {
+        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * Qg, [&] {
+          k_pairs_bucket_lists<<<grid_for(Qg, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, q0, Qg, step,
+                                                                   mtile);
+        }));
+        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6)));
+        step *= 2;
+        levels -= 1;
+      }
+      flip();
+    }
+    return PGS_OK;
   }
-  const uint32_t launches = c.launches + 1;             // including the statistics kernel
-  return launch(c, PGS_KERNEL_STATS, 0, 8 * ((uint64_t)R + sh.I), [&] {
-    k_stats<<<1, 256, 0, st>>>(g, b.e, n, (uint32_t)std::min<uint64_t>(sh.s, 0xFFFFFFFFu),
-                               sh.learned ? PGS_SPLITTERS_LEARNED : PGS_SPLITTERS_SAMPLED, (uint32_t)sh.passes,
-                               launches, b.err, b.fallback, b.learned_ratio, static_cast<DevStats*>(o.stats),
-                               o.bucket_bounds, b.max_ratio);
-  });
+
+  // Step 6 of a host-buffer sort of one instance: the bucket bounds come back
+  // once (the host waits for steps 1-5 here), then the rounds run bucket group
+  // by bucket group; a group's range is final when its last round ends, no
+  // later group writes inside it, and its copy to the host starts right away.
+  int merge_buckets_to_host(const HostGroups& hg) {
+    const uint32_t R = sh.R;
+    std::vector<uint64_t> e(R + 1);
+    PGS_CUDA(cudaMemcpyAsync(e.data(), b.e, (R + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    PGS_CUDA(cudaStreamSynchronize(st));
+    const Saved s0 = save();
+    for (uint32_t gi = 0; gi < hg.out_groups; ++gi) {
+      restore(s0);
+      const uint64_t b0 = ((uint64_t)gi * R) / hg.out_groups, b1 = ((uint64_t)(gi + 1) * R) / hg.out_groups;
+      const uint64_t lo = e[b0], hi = e[b1];
+      if (b1 > b0) PGS_TRY(merge_buckets(b0 * R, (b1 - b0) * R, hi - lo));
+      PGS_CUDA(cudaEventRecord(hg.ev_out[gi], st));
+      PGS_CUDA(cudaStreamWaitEvent(hg.cs, hg.ev_out[gi], 0));
+      if (hi > lo) {
+        PGS_CUDA(cudaMemcpyAsync(static_cast<K*>(hg.hk_out) + lo, kout + lo, (hi - lo) * sizeof(K),
+                                 cudaMemcpyDeviceToHost, hg.cs));
+        if (V) PGS_CUDA(cudaMemcpyAsync(hg.hv_out + lo, vout + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost, hg.cs));
+      }
+    }
+    PGS_CUDA(cudaEventRecord(hg.done, hg.cs));
+    PGS_CUDA(cudaStreamWaitEvent(st, hg.done, 0));
+    return PGS_OK;
+  }
+
+  // P = 1 for every instance: the sorted runs are the buckets.
+  int single_bucket() {
+    return launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)sh.R, [&] {
+      k_cut_edges<<<grid_for(sh.R, 256), 256, 0, st>>>(g, b.cut, b.e);
+    });
+  }
+
+  // The plan and the launches must agree; then the cut matrix and Table II's loads.
+  int finish() {
+    if (left != 0 || cur_k != kout) return PGS_ERR_CUDA;   // plan/launch mismatch: never expected
+    if (o.cuts && sh.I == 1) {
+      PGS_CUDA(cudaMemcpyAsync(o.cuts, b.cut, sizeof(uint64_t) * sh.MAT, cudaMemcpyDeviceToDevice, st));
+    }
+    const uint32_t launches = c.launches + 1;             // including the statistics kernel
+    return launch(c, PGS_KERNEL_STATS, 0, 8 * ((uint64_t)sh.R + sh.I), [&] {
+      k_stats<<<1, 256, 0, st>>>(g, b.e, sh.n, (uint32_t)std::min<uint64_t>(sh.s, 0xFFFFFFFFu),
+                                 sh.learned ? PGS_SPLITTERS_LEARNED : PGS_SPLITTERS_SAMPLED, (uint32_t)sh.passes,
+                                 launches, b.err, b.fallback, b.learned_ratio, static_cast<DevStats*>(o.stats),
+                                 o.bucket_bounds, b.max_ratio);
+    });
+  }
+};
+
+template <typename K, bool V>
+int run_pipeline(const Shape& sh, const Options& o, const K* kin, const uint32_t* vin, K* kout, uint32_t* vout,
+                 Ctx& c, const Buffers& b, const HostGroups* hg = nullptr) {
+  Pipeline<K, V> p(sh, o, kin, vin, kout, vout, c, b);
+  PGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), c.st));
+  PGS_TRY(p.local_sort(hg));                                  // step 1
+  if (sh.Pmax > 1) {
+    K* sample = nullptr;
+    PGS_TRY(p.sample_and_splitters(&sample));                 // steps 2-3
+    PGS_TRY(p.cuts(sample));                                  // step 4, offsets of step 5
+    PGS_TRY(p.exchange());                                    // step 5 (or fused with step 6's first round)
+    if (hg && hg->out_groups)
+      PGS_TRY(p.merge_buckets_to_host(*hg));                  // step 6, copied back group by group
+    else
+      PGS_TRY(p.merge_buckets(0, sh.Q, sh.n));                // step 6
+  } else {
+    PGS_TRY(p.single_bucket());
+  }
+  return p.finish();
 }
 
 // A single sort: build the batch-of-one tables on the device, then the pipeline.
