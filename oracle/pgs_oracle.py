@@ -19,6 +19,11 @@ Two things are computed:
   Section IV-A, Fig. 2 balanced merge; Section IV-B, sample budget and the
   investigator), giving the bucket vector e[0..P], the per-run cut matrix, the
   exchange offsets and, after the per-bucket merges, again the sorted output.
+  The investigator also has the text's literal per-run rule (LOCAL), whose
+  output keys are sorted but not in stable order.
+* Part 3, lookups on the sorted output (end of Section IV-C): lower and upper
+  bounds of query keys, the bucket holding a position, and every entry's
+  previous processor and index.
 
 Readings of points the paper leaves open (each is listed in the design notes):
 sample positions are the last element of s equal blocks of a sorted run; the
