@@ -180,6 +180,7 @@ struct Buffers {
   uint64_t *samp_counts, *samp_off;
   Pair* pairs; uint64_t *tcount, *tbegin;
   TileSplit* split;
+  void* kidx;                // key index of the last pass: the key at every 64th position
   Quad* quads; uint64_t *ccount, *coff; Cut4 *cuts_a, *cuts_b; Chunk4* chunks4;
   uint64_t *scan_sums, *scan_sums2;
   uint64_t* first_seg;
@@ -227,6 +228,7 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->tcount = c.take<uint64_t>(sh.max_pairs);
   b->tbegin = c.take<uint64_t>(sh.max_pairs + 1);
   b->split = c.take<TileSplit>(sh.max_tiles);
+  b->kidx = c.take<char>(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) * sh.w);
   if (sh.four) {
     b->quads = c.take<Quad>(sh.max_quads);
     b->ccount = c.take<uint64_t>(sh.max_quads);
@@ -394,33 +396,38 @@ inline int set_smem_attrs() {
 
 template <typename K, bool V, int NT, int VT>
 inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t tiles,
-                              const Buffers& b, const uint64_t* total, int f32_out, cudaStream_t st) {
+                              const Buffers& b, const uint64_t* total, int f32_out, K* idx_out, cudaStream_t st) {
   k_merge_tile<K, V, NT, VT><<<(unsigned)tiles, NT, Merge2Layout<K, V, NT, VT>::bytes, st>>>(
-      ks, vs, kd, vd, b.split, total, f32_out, b.err);
+      ks, vs, kd, vd, b.split, total, f32_out, b.err, idx_out);
 }
 
 // One pairwise merge round over pairs already described in b.pairs / b.tcount
 // (tile counts of the chosen tile shape).  `len` keys take part; every one of
-// them is read and written once.
+// them is read and written once.  idx_in: the key index of ks (NULL: none);
+// idx_out: where the round writes the key index of kd (NULL: not written).
 template <typename K, bool V>
 inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
-                       uint64_t len, const Buffers& b, int f32_out, uint32_t step) {
+                       uint64_t len, const Buffers& b, int f32_out, uint32_t step, const K* idx_in = nullptr,
+                       K* idx_out = nullptr) {
   const MergeShape ms = kMergeShapes[c.variant];
   const uint32_t tile = (uint32_t)(ms.nt * ms.vt);
   PGS_TRY(scan_u64(c, b.tcount, b.tbegin, npairs, b.scan_sums, b.scan_sums2, step));
   const uint64_t tiles_ub = ceil_div(len, tile) + npairs;
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, tile), [&] {
-    k_partition_split<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.split, tile);
+    k_partition_split<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.split, tile,
+                                                                    idx_in);
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
   const uint64_t* total = b.tbegin + npairs;
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     switch (c.variant) {
 #define PGS_MERGE_SHAPE(i) kMergeShapes[i].nt, kMergeShapes[i].vt
-      case 1: launch_merge_tile<K, V, PGS_MERGE_SHAPE(1)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
-      case 2: launch_merge_tile<K, V, PGS_MERGE_SHAPE(2)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
-      case 3: launch_merge_tile<K, V, PGS_MERGE_SHAPE(3)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
-      default: launch_merge_tile<K, V, PGS_MERGE_SHAPE(0)>(ks, vs, kd, vd, tiles_ub, b, total, f32_out, c.st); break;
+#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, total, f32_out, idx_out, c.st
+      case 1: launch_merge_tile<K, V, PGS_MERGE_SHAPE(1)>(PGS_MERGE_ARGS); break;
+      case 2: launch_merge_tile<K, V, PGS_MERGE_SHAPE(2)>(PGS_MERGE_ARGS); break;
+      case 3: launch_merge_tile<K, V, PGS_MERGE_SHAPE(3)>(PGS_MERGE_ARGS); break;
+      default: launch_merge_tile<K, V, PGS_MERGE_SHAPE(0)>(PGS_MERGE_ARGS); break;
+#undef PGS_MERGE_ARGS
 #undef PGS_MERGE_SHAPE
     }
   });
@@ -430,7 +437,7 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
 // cuts, their order by rank, then one CTA per chunk.
 template <typename K, bool V>
 inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t nquads,
-                        uint64_t len, const Buffers& b, int f32_out, uint32_t step) {
+                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, K* idx_out) {
   PGS_TRY(scan_u64(c, b.ccount, b.coff, nquads, b.scan_sums, b.scan_sums2, step));
   const uint64_t chunks_ub = ceil_div(len, kMerge4Cut) + nquads;
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, kMerge4Cut), [&] {
@@ -448,7 +455,7 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
   constexpr size_t smem = Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes;
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     k_merge4<K, V, kMerge4NT, kMerge4VT><<<(unsigned)chunks_ub, kMerge4NT, smem, c.st>>>(
-        ks, vs, kd, vd, b.chunks4, b.coff + nquads, f32_out, b.err);
+        ks, vs, kd, vd, b.chunks4, b.coff + nquads, f32_out, b.err, idx_out);
   });
 }
 
@@ -560,6 +567,7 @@ struct Pipeline {
   uint32_t* oth_v;
   int left;
   int k0 = 0;                                          // bucket rounds already done by step 5
+  bool idx_ok = false;                                 // b.kidx indexes cur_k (written by its pass)
 
   struct Saved {
     K* ck;
@@ -567,6 +575,7 @@ struct Pipeline {
     uint32_t* cv;
     uint32_t* ov;
     int left;
+    bool idx_ok;
   };
 
   Pipeline(const Shape& sh_, const Options& o_, const K* kin_, const uint32_t* vin_, K* kout_, uint32_t* vout_,
@@ -585,19 +594,31 @@ struct Pipeline {
     left = after_block;
   }
 
-  Saved save() const { return Saved{cur_k, oth_k, cur_v, oth_v, left}; }
+  Saved save() const { return Saved{cur_k, oth_k, cur_v, oth_v, left, idx_ok}; }
   void restore(const Saved& s) {
     cur_k = s.ck;
     oth_k = s.ok;
     cur_v = s.cv;
     oth_v = s.ov;
     left = s.left;
+    idx_ok = s.idx_ok;
   }
   void flip() {
     std::swap(cur_k, oth_k);
     std::swap(cur_v, oth_v);
   }
   int f32_out() const { return left == 0 ? f32 : 0; }   // float bits back on the last pass
+  // The key index: read while it describes the round's input; written by
+  // every merge pass but the last (whose output no partition searches).
+  const K* idx_in() const { return idx_ok ? static_cast<const K*>(b.kidx) : nullptr; }
+  K* idx_out() const { return left > 0 ? static_cast<K*>(b.kidx) : nullptr; }
+  // A pairwise round of the pairs in b.pairs from cur to oth (left already counts it).
+  int pair_round(uint64_t npairs, uint64_t len, uint32_t step) {
+    K* io = idx_out();
+    PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, npairs, len, b, f32_out(), step, idx_in(), io)));
+    idx_ok = io != nullptr;
+    return PGS_OK;
+  }
 
   // Step 1 for runs [r0, r0 + Rg) holding len keys: block sort of kTile tiles,
   // then the balanced merge tree (Fig. 2) until each run is one list: two
@@ -609,6 +630,7 @@ struct Pipeline {
       k_block_sort<K, V><<<(unsigned)((uint64_t)Rg * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
           kin, vin, cur_k, cur_v, ro, tiles_per_run, f32, f32_out());
     }));
+    idx_ok = false;
     uint64_t w = kTile;
     int levels = sh.run_rounds;
     while (levels > 0) {
@@ -619,7 +641,8 @@ struct Pipeline {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 80 * nq, [&] {
           k_quads_runs<<<grid_for(nq, 256), 256, 0, st>>>(b.quads, b.ccount, ro, Rg, w, cmax, kMerge4Cut);
         }));
-        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, len, b, f32_out(), 1)));
+        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, len, b, f32_out(), 1, idx_out())));
+        idx_ok = idx_out() != nullptr;
         w *= 4;
         levels -= 2;
       } else {
@@ -628,7 +651,7 @@ struct Pipeline {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
           k_pairs_runs<<<grid_for(np, 256), 256, 0, st>>>(b.pairs, b.tcount, ro, Rg, w, cmax, mtile);
         }));
-        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, np, len, b, f32_out(), 1)));
+        PGS_TRY(pair_round(np, len, 1));
         w *= 2;
         levels -= 1;
       }
@@ -721,6 +744,7 @@ struct Pipeline {
         k_scatter<K, V><<<(unsigned)stiles, kScatterNT, sizeof(ScatterSmem<K>), st>>>(
             cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, f32_out());
       }));
+      idx_ok = false;
       flip();
       k0 = 0;
       return PGS_OK;
@@ -729,7 +753,7 @@ struct Pipeline {
       k_pairs_fused<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, b.seg_src, 0, sh.Q, mtile);
     }));
     --left;
-    PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, sh.Q, n, b, f32_out(), 6)));
+    PGS_TRY(pair_round(sh.Q, n, 6));
     flip();
     k0 = 1;
     return PGS_OK;
@@ -747,7 +771,8 @@ struct Pipeline {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * Qg, [&] {
           k_quads_buckets<<<grid_for(Qg, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, q0, Qg, step, kMerge4Cut);
         }));
-        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6)));
+        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6, idx_out())));
+        idx_ok = idx_out() != nullptr;
         step *= 4;
         levels -= 2;
       } else {
@@ -755,7 +780,7 @@ struct Pipeline {
           k_pairs_bucket_lists<<<grid_for(Qg, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, q0, Qg, step,
                                                                    mtile);
         }));
-        PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6)));
+        PGS_TRY(pair_round(Qg, len, 6));
         step *= 2;
         levels -= 1;
       }

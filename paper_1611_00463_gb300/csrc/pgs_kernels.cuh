@@ -141,6 +141,21 @@ __device__ __forceinline__ void serial_merge(const K* s, int ai, int a_end, int 
 // 2i+1 into list 2i, exactly the balanced schedule of Fig. 2, in shared memory.
 // ---------------------------------------------------------------------------
 
+// Key index of a merge pass's output: entry e holds the (order-mapped) key at
+// global position 64 e.  Every merge kernel that writes a tile of sorted
+// output [g0, g0 + cnt) also writes the entries whose positions fall inside
+// it, so after the pass the index covers all of the output; the next round's
+// partition bisects it before touching the keys themselves.  (The block sort
+// writes none: its lists, one tile each, are short enough to bisect directly.)
+constexpr uint64_t kIdxStride = 64;
+
+template <typename K>
+__device__ __forceinline__ void write_key_index(K* kidx, const K* tile, uint64_t g0, int cnt) {
+  const uint64_t first = (g0 + kIdxStride - 1) / kIdxStride;
+  const uint64_t last = (g0 + (uint64_t)cnt + kIdxStride - 1) / kIdxStride;
+  for (uint64_t e = first + threadIdx.x; e < last; e += blockDim.x) kidx[e] = tile[e * kIdxStride - g0];
+}
+
 template <typename K>
 struct BlockSortSmem {
   K keys[kTile + 1];      // + one slot the serial merge may read past the last list
@@ -394,10 +409,66 @@ struct TileSplit {
   uint64_t pair;          // index of the pair the tile belongs to
 };
 
+// Merge path of a and b at diagonal d, searched only inside [lo, hi], which
+// must hold the answer.
+template <typename K>
+__device__ __forceinline__ uint64_t merge_path_in(const K* a, const K* b, uint64_t d, uint64_t lo, uint64_t hi) {
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= b[d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int64_t ceil_div64(int64_t t) {            // ceil(t / 64) for any sign
+  return t >= 0 ? (t + (int64_t)kIdxStride - 1) / (int64_t)kIdxStride : -((-t) / (int64_t)kIdxStride);
+}
+
+// Merge path through the key index.  A' = A[oa + 64 i] and B' = B[ob + 64 j]
+// are the keys of A and B at global multiples of 64 (contiguous index
+// entries).  If c keys of B' are below A'[i], the keys of B below it number
+// between ob + 64 (c - 1) + 1 and ob + 64 c (none past B[ob + 64 c], all up to
+// B[ob + 64 (c - 1)]; for c = 0 at most ob), so the output position of A'[i]
+// in merge(A, B) lies in [o + 64 p - 63, o + 64 p], where p = i + c is its
+// position in merge(A', B') and o = oa + ob.  With t = d - o: every A' item
+// among the first ceil(t / 64) outputs of the sample merge comes before
+// output d, and the first A' item not among the first ceil((t + 63) / 64)
+// comes at or after it.  So the split lies in a window of at most 127
+// positions between the two, where the plain bisection finishes.  The two
+// sample diagonals differ by at most one: one sample merge path and one
+// comparison give both.
+template <typename K>
+__device__ __forceinline__ uint64_t merge_path_indexed(const K* src, const K* __restrict__ kidx, const Pair& pr,
+                                                       uint64_t d) {
+  const uint64_t na = pr.na, nb = pr.nb;
+  uint64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  const uint64_t ea = (pr.a + kIdxStride - 1) / kIdxStride, eb = (pr.b + kIdxStride - 1) / kIdxStride;
+  const uint64_t ca = (pr.a + na + kIdxStride - 1) / kIdxStride - ea;
+  const uint64_t cb = (pr.b + nb + kIdxStride - 1) / kIdxStride - eb;
+  const uint64_t oa = ea * kIdxStride - pr.a, ob = eb * kIdxStride - pr.b;
+  const int64_t t = (int64_t)d - (int64_t)(oa + ob);
+  const int64_t cmax = (int64_t)(ca + cb);
+  const int64_t dl = min(max(ceil_div64(t), (int64_t)0), cmax);
+  const int64_t dh = min(max(ceil_div64(t + (int64_t)kIdxStride - 1), (int64_t)0), cmax);
+  const K* ia = kidx + ea;
+  const K* ib = kidx + eb;
+  const uint64_t D = (uint64_t)dl;
+  const uint64_t alo = merge_path<K, uint64_t>(ia, ca, ib, cb, D);
+  uint64_t ahi = alo;
+  if (dh > dl && alo < ca && (D - alo >= cb || ia[alo] <= ib[D - alo])) ahi = alo + 1;
+  if (alo >= 1) lo = max(lo, oa + kIdxStride * (alo - 1) + 1);
+  if (ahi < ca) hi = min(hi, oa + kIdxStride * ahi);
+  return merge_path_in<K>(src + pr.a, src + pr.b, d, lo, hi);
+}
+
+// Lists shorter than this bisect the keys directly.
+constexpr uint64_t kIdxMinList = 1024;
+
 template <typename K>
 __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restrict__ pairs,
                                   const uint64_t* __restrict__ tbegin, uint64_t npairs, TileSplit* split,
-                                  uint32_t tile) {
+                                  uint32_t tile, const K* __restrict__ kidx) {
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t total = tbegin[npairs];
   if (i >= total) return;
@@ -408,7 +479,9 @@ __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restr
   }
   const Pair pr = pairs[lo];
   const uint64_t d0 = (i - tbegin[lo]) * tile;
-  const uint64_t a0 = merge_path<K, uint64_t>(src + pr.a, pr.na, src + pr.b, pr.nb, d0);
+  const uint64_t a0 = (kidx && pr.na >= kIdxMinList && pr.nb >= kIdxMinList)
+                          ? merge_path_indexed<K>(src, kidx, pr, d0)
+                          : merge_path<K, uint64_t>(src + pr.a, pr.na, src + pr.b, pr.nb, d0);
   split[i] = TileSplit{pr.a + a0, pr.b + (d0 - a0), pr.out + d0, pr.a + pr.na, pr.b + pr.nb, lo};
 }
 
@@ -416,7 +489,7 @@ template <typename K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT)
 k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
              uint32_t* __restrict__ vdst, const TileSplit* __restrict__ split, const uint64_t* __restrict__ total_ptr,
-             int f32_out, uint32_t* err) {
+             int f32_out, uint32_t* err, K* __restrict__ kidx) {
   using L = Merge2Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -520,6 +593,11 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
       s_kout[diag + j] = ok[j];
       if (VALS) s_vout[diag + j] = ov[j];
     }
+  }
+  static_assert(VT < kIdxStride, "at most one index entry per thread");
+  if (kidx) {
+    const int j0 = (int)((0u - (uint32_t)s_out - (uint32_t)diag) & (uint32_t)(kIdxStride - 1));
+    if (j0 < mine) kidx[(s_out + (uint64_t)(diag + j0)) / kIdxStride] = s_kout[diag + j0];
   }
   __syncthreads();
   store_tile_vec<K, NT>(kdst + s_out, s_kout, cnt);
@@ -772,7 +850,7 @@ template <typename K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT)
 k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
          uint32_t* __restrict__ vdst, const Chunk4* __restrict__ chunks, const uint64_t* __restrict__ total,
-         int f32_out, uint32_t* err) {
+         int f32_out, uint32_t* err, K* __restrict__ kidx) {
   using L = Merge4Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -860,6 +938,7 @@ k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __res
   __syncthreads();
   store_tile_vec<K, NT>(kdst + s_out, s_kout, cnt);
   if (VALS) store_tile_vec<uint32_t, NT>(vdst + s_out, s_vout, cnt);
+  if (kidx) write_key_index(kidx, s_kout, s_out, cnt);
 }
 
 // ---------------------------------------------------------------------------
