@@ -1,8 +1,10 @@
 """Summaries of Nsight Compute CSV output for this library's kernels.
 
-`python -m paper_1611_00463_gb300.profiling launches <ncu.csv>` prints, per
-kernel, the number of launches, the total device time and its share of a
-launch list taken with `ncu --metrics gpu__time_duration.sum --csv`.
+`python -m paper_1611_00463_gb300.profiling launches <ncu.csv> [--whole-sorts]`
+prints, per kernel, the number of launches, the total device time and its
+share of a launch list taken with `ncu --metrics gpu__time_duration.sum --csv`;
+`--whole-sorts` drops the launches after the last sort's closing statistics
+kernel (a list cut off by `ncu -c` mid-sort).
 `python -m paper_1611_00463_gb300.profiling metrics <raw.csv> [regex]` prints
 selected metrics of a `ncu -i <rep> --page raw --csv` export, per launch.
 """
@@ -32,8 +34,11 @@ def kernel_label(name: str) -> str:
     return label.replace(" ", "")
 
 
-def launches(path: str) -> str:
+def launches(path: str, whole_sorts: bool = False) -> str:
     rows = [r for r in _csv_rows(path) if r.get("Metric Name") == "gpu__time_duration.sum"]
+    if whole_sorts:
+        ends = [i for i, r in enumerate(rows) if kernel_label(r["Kernel Name"]) == "k_stats"]
+        rows = rows[:ends[-1] + 1] if ends else []
     agg: dict[str, list] = {}
     for r in rows:
         d = agg.setdefault(kernel_label(r["Kernel Name"]), [0, 0.0])
@@ -70,6 +75,6 @@ if __name__ == "__main__":
     if len(sys.argv) < 3 or sys.argv[1] not in ("launches", "metrics"):
         sys.exit(__doc__)
     if sys.argv[1] == "launches":
-        print(launches(sys.argv[2]))
+        print(launches(sys.argv[2], "--whole-sorts" in sys.argv[3:]))
     else:
         print(metrics(sys.argv[2], *sys.argv[3:]))
