@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-timer", action="store_true", help="skip per-launch events (profiling runs)")
+    ap.add_argument("--no-comparator", action="store_true", help="skip the torch.sort(stable=True) context line")
     return ap.parse_args()
 
 
@@ -526,6 +527,50 @@ def run_search(args):
     print(json.dumps(line), flush=True)
 
 
+def order_as_signed(k, dtype: str):
+    """Raw key bits (int64 for u64, int32 otherwise) -> a signed integer of the
+    same width whose order is the key order (float32: IEEE totalOrder); the map
+    is its own inverse."""
+    import torch
+    if dtype == "u64":
+        return k ^ torch.iinfo(torch.int64).min
+    if dtype == "u32":
+        return k ^ torch.iinfo(torch.int32).min
+    return k ^ ((k >> 31) & 0x7FFFFFFF)
+
+
+def library_comparator(kin, vin, kout, vout, dtype, args, dev, world):
+    """Context, not a baseline: the same stable sort through a library call,
+    torch.sort(stable=True) on the order-mapped keys plus a gather of the
+    payloads by the returned permutation, timed like the main arm; its output
+    is compared with this library's bit for bit."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        sk, idx = torch.sort(order_as_signed(kin, dtype), stable=True)
+        return order_as_signed(sk, dtype), vin[idx]
+    try:
+        for _ in range(max(args.warmup, 1)):
+            ko, vo = step()
+        same = bool(torch.equal(ko, kout) and torch.equal(vo, vout))
+        del ko, vo
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dev, world)
+        return {"call": "torch.sort(order-mapped keys, stable=True) + payload gather by the permutation",
+                "ms_per_step": ms, "value": whole_job_rate(kin.numel(), world, ms * 1e-3), "unit": "Gkeys/s",
+                "outputs_equal": same}
+    except RuntimeError as ex:                           # e.g. out of memory: report why, keep the line
+        torch.cuda.empty_cache()
+        return {"unavailable": str(ex).splitlines()[0][:200]}
+
+
 def main():
     args = parse()
     if args.sweep_samples:
@@ -633,6 +678,8 @@ def main():
         del cg
     except RuntimeError as ex:                           # capture unavailable: report why, keep the line
         graph = {"unavailable": str(ex).splitlines()[0][:200]}
+
+    comparator = None if args.no_comparator else library_comparator(kin, vin, kout, vout, dtype, args, dev, world)
 
     # Dominant kernel and its roofline, from the launch timer of the timed region.
     peak, peak_src = peaks()
@@ -743,6 +790,7 @@ def main():
             "clocks": clocks.summary(),
             "e2e": e2e,
             "graph_replay": graph,
+            "library_comparator": comparator,
             "instrumented_ms_per_step": ms_instr,
             "cpu_baseline": cpu,
             "per_kernel": per_kernel,
