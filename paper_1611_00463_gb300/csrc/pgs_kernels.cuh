@@ -348,7 +348,9 @@ static __global__ void k_pairs_fused(Pair* pairs, uint64_t* tcount, Geo g, const
 // input buffer it came from and leaves with 16-byte vector stores.  Reusing
 // the input buffer halves the shared memory a CTA holds, so more CTAs share an
 // SM and more copies are in flight (about 10 % faster than a separate output
-// staging area at every tile shape).
+// staging area at every tile shape).  With kidx set, the thread whose outputs
+// cover a global position 64 e also writes key index entry e for the next
+// round's partition.
 // ---------------------------------------------------------------------------
 
 template <typename K, bool VALS, int NT, int VT>
