@@ -240,7 +240,13 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
                 stats: torch.Tensor | None = None, timer: Timer | None = None,
                 model: torch.Tensor | None = None, model_out: torch.Tensor | None = None,
                 tile_variant: int = 0, merge_ways: int = 0) -> pgs_config:
+    """The options of a call.  The struct holds raw device addresses, so it
+    also keeps a reference to every tensor (and the timer) it points to: they
+    live as long as the config does, and `make_config(workspace=workspace(...))`
+    cannot leave the library writing into memory the allocator has handed on."""
     c = pgs_config()
+    c._keep = tuple(x for x in (workspace, bucket_bounds, cuts, splitters_out, stats, timer, model, model_out)
+                    if x is not None)
     c.dtype = DTYPES[dtype]
     c.samples_per_run = samples_per_run
     c.eps = eps

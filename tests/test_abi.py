@@ -128,3 +128,44 @@ def test_batch_plan_host_only(lib):
     zeroP = np.array([0], dtype=np.uint32)
     assert lib.pgs_batch_create(off.ctypes.data, 1, zeroP.ctypes.data, 1, ctypes.byref(cfg),
                                 ctypes.byref(h)) == pgs.PGS_ERR_INVALID
+
+
+class _FakeDeviceTensor:
+    """Stands in for a device tensor on a machine without a GPU: make_config
+    reads only these attributes."""
+    is_cuda = True
+
+    def __init__(self, addr, nbytes):
+        self.addr, self.nbytes = addr, nbytes
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        return self.addr
+
+    def numel(self):
+        return self.nbytes
+
+    def element_size(self):
+        return 1
+
+
+def test_config_keeps_its_tensors_alive():
+    """A config holds raw addresses; it must also hold the tensors, or a
+    workspace built inline is freed (and its memory reused) while the library
+    still writes into it."""
+    import gc
+    import weakref
+    from paper_1611_00463_gb300 import pgs
+    ws = _FakeDeviceTensor(0x7000000, 4096)
+    st = _FakeDeviceTensor(0x8000000, pgs.STATS_BYTES)
+    refs = [weakref.ref(ws), weakref.ref(st)]
+    cfg = pgs.make_config(dtype="u64", workspace=ws, stats=st)
+    del ws, st
+    gc.collect()
+    assert all(r() is not None for r in refs)
+    assert cfg.workspace == 0x7000000 and cfg.workspace_bytes == 4096 and cfg.stats == 0x8000000
+    del cfg
+    gc.collect()
+    assert all(r() is None for r in refs)
