@@ -80,6 +80,14 @@ typedef enum { PGS_EXCHANGE_AUTO = 0, PGS_EXCHANGE_SCATTER = 1, PGS_EXCHANGE_FUS
  * judge it and take over when its imbalance exceeds 1 + eps. */
 typedef enum { PGS_SPLITTERS_SAMPLED = 0, PGS_SPLITTERS_LEARNED = 1 } pgs_splitter_mode;
 
+/* How pgs_sort_host copies its output back.  GROUPS (default): the host waits
+ * once step 5 has fixed the bucket bounds, then each group of buckets is
+ * copied back while the next group merges (shortest single call).  AT_END:
+ * the call never waits; the whole output is copied back after step 6 (a longer
+ * single call, but several calls in flight keep the GPU and both copy
+ * directions busy).  Ignored by the device-buffer calls. */
+typedef enum { PGS_COPY_BACK_GROUPS = 0, PGS_COPY_BACK_AT_END = 1 } pgs_copy_back;
+
 /* Kernels of the pipeline, as reported by the launch timer. */
 typedef enum {
   PGS_KERNEL_BLOCK_SORT = 0,   /* step 1: shared-memory block sort of one tile */
@@ -143,7 +151,7 @@ typedef struct pgs_config {
   int32_t   merge_ways;       /* levels of the Fig. 2 merge tree per pass over the data: 2 (one level,
                                  pairwise rounds, default; 0 means 2) or 4 (two levels per pass: fewer
                                  passes, more shared-memory work per chunk) */
-  int32_t   reserved1;
+  int32_t   copy_back;         /* pgs_copy_back, pgs_sort_host only; default GROUPS */
 } pgs_config;
 
 /* Load statistics of one sort (Table II reports the per-processor share). */
@@ -196,12 +204,14 @@ size_t pgs_host_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg);
  *   pgs_host_workspace_bytes(n, P, cfg).
  *   The input is copied in up to 8 groups of whole runs on a stream of the
  *   call's own, and step 1 of a group starts as soon as its copy has landed,
- *   while later groups are still copying.  Once step 5 has fixed the bucket
- *   bounds the call reads them back (the host waits for steps 1-5 there), then
- *   runs the remaining merge rounds of step 6 in up to 8 groups of buckets and
- *   copies each group's sorted keys back while the next group merges.  With
- *   P = 1 the output is copied back after step 1.  The rest is asynchronous on
- *   `stream` for pinned memory: synchronise it before reading the outputs.
+ *   while later groups are still copying.  With cfg->copy_back = GROUPS (the
+ *   default), once step 5 has fixed the bucket bounds the call reads them back
+ *   (the host waits for steps 1-5 there), then runs the remaining merge rounds
+ *   of step 6 in up to 8 groups of buckets and copies each group's sorted keys
+ *   back while the next group merges.  With AT_END, or P = 1, the whole output
+ *   is copied back after the last pass and the call never waits.  The rest is
+ *   asynchronous on `stream` for pinned memory: synchronise it before reading
+ *   the outputs.
  *   The paper has no counterpart (its data starts in each machine's memory);
  *   this is the host-to-host form of pgs_sort_copy. */
 int pgs_sort_host(const void* keys_in, const uint32_t* vals_in, void* keys_out,

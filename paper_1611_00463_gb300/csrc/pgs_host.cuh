@@ -46,6 +46,7 @@ struct Options {
   float* model_out = nullptr;
   int tile_variant = 0;       // merge tile shape (see kMergeShapes)
   int merge_ways = 2;         // tree levels per pass: 2-way (one level) or 4-way (two levels)
+  int copy_back = PGS_COPY_BACK_GROUPS;   // pgs_sort_host: bucket groups after a host wait, or all at the end
 };
 
 // Validates and copies a (possibly NULL) pgs_config.  Returns PGS_OK or an error.
@@ -69,6 +70,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->model_out = cfg->model_out;
   o->tile_variant = cfg->tile_variant;
   o->merge_ways = cfg->merge_ways == 0 ? 2 : cfg->merge_ways;
+  o->copy_back = cfg->copy_back;
   if (o->dtype < PGS_U32 || o->dtype > PGS_F32) return PGS_ERR_INVALID;
   if (!(o->eps > 0.0f) || o->eps > 1.0f) return PGS_ERR_INVALID;
   if (o->investigator < 0 || o->investigator > 3) return PGS_ERR_INVALID;
@@ -76,6 +78,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
   if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;
   if (o->merge_ways != 2 && o->merge_ways != 4) return PGS_ERR_INVALID;
+  if (o->copy_back != PGS_COPY_BACK_GROUPS && o->copy_back != PGS_COPY_BACK_AT_END) return PGS_ERR_INVALID;
   return PGS_OK;
 }
 
@@ -940,7 +943,9 @@ int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t
   HostGroups& hg = hc.hg;
   hg.groups = std::min<uint32_t>(kHostGroups, R);
   for (uint32_t g = 0; g <= hg.groups; ++g) hg.r0[g] = (uint32_t)(((uint64_t)g * R) / hg.groups);
-  hg.out_groups = R > 1 ? std::min<uint32_t>(kHostGroups, R) : 0;   // P = 1 has no step 6
+  // Bucket groups copied back during step 6 (P = 1 has no step 6; AT_END
+  // copies everything after it and never waits on the host).
+  hg.out_groups = (R > 1 && o.copy_back == PGS_COPY_BACK_GROUPS) ? std::min<uint32_t>(kHostGroups, R) : 0;
   PGS_CUDA(cudaStreamCreateWithFlags(&hc.cs, cudaStreamNonBlocking));
   PGS_CUDA(cudaEventCreateWithFlags(&hc.start, cudaEventDisableTiming));
   for (uint32_t g = 0; g < hg.groups; ++g) PGS_CUDA(cudaEventCreateWithFlags(&hg.ev[g], cudaEventDisableTiming));
@@ -966,7 +971,7 @@ int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t
                                                           b.run_inst, n, R, sh.s);
   }));
   PGS_TRY((run_pipeline<K, V>(sh, o, dki, dvi, dko, dvo, c, b, &hg)));
-  if (hg.out_groups == 0) {                              // no bucket groups: one copy at the end
+  if (hg.out_groups == 0) {                              // no bucket groups: one copy after step 6
     PGS_CUDA(cudaMemcpyAsync(hko, dko, n * sizeof(K), cudaMemcpyDeviceToHost, st));
     if (V) PGS_CUDA(cudaMemcpyAsync(hvo, dvo, n * 4, cudaMemcpyDeviceToHost, st));
   }

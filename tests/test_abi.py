@@ -169,3 +169,12 @@ def test_config_keeps_its_tensors_alive():
     del cfg
     gc.collect()
     assert all(r() is None for r in refs)
+
+
+def test_copy_back_option_is_validated():
+    from paper_1611_00463_gb300 import pgs
+    good = pgs.make_config(dtype="u64", copy_back="end")
+    assert pgs.pgs_host_workspace_bytes(1 << 20, 16, good) > 0
+    bad = pgs.make_config(dtype="u64")
+    bad.copy_back = 2
+    assert pgs.pgs_host_workspace_bytes(1 << 20, 16, bad) == 0

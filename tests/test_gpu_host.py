@@ -97,20 +97,23 @@ def test_host_sort_rejects_device_buffers_and_small_workspace():
     assert pgs.pgs_host_workspace_bytes(n, P, cfg0) > pgs.pgs_workspace_bytes(n, P, cfg0)
 
 
-def test_host_sorts_in_flight_on_two_streams():
+@pytest.mark.parametrize("copy_back", ["groups", "end"])
+def test_host_sorts_in_flight_on_two_streams(copy_back):
     """Consecutive calls on two streams with their own workspaces overlap on the
-    GPU (one call's copy in during the other's merges); each result is exact."""
+    GPU (one call's copy in during the other's merges); each result is exact.
+    With copy_back = "end" no call waits, so all six are queued at once and a
+    lane's next call must wait for its previous one on the device."""
     import torch
     from paper_1611_00463_gb300 import pgs
     n, P = 600_011, 32
-    sets = [inputs.normal_lognormal_u64(n, 30 + i) for i in range(4)]
+    sets = [inputs.normal_lognormal_u64(n, 30 + i) for i in range(6)]
     vals = inputs.index_payload(n)
     hv = host_tensor(vals, "u32", True)
-    cfg0 = pgs.make_config(dtype="u64")
+    cfg0 = pgs.make_config(dtype="u64", copy_back=copy_back)
     lanes = []
     for _ in range(2):
         ws = torch.empty(pgs.pgs_host_workspace_bytes(n, P, cfg0), dtype=torch.uint8, device="cuda")
-        lanes.append((torch.cuda.Stream(), pgs.make_config(dtype="u64", workspace=ws), ws))
+        lanes.append((torch.cuda.Stream(), pgs.make_config(dtype="u64", workspace=ws, copy_back=copy_back), ws))
     outs = []
     for i, keys in enumerate(sets):
         s, cfg, _ = lanes[i % 2]
@@ -128,7 +131,9 @@ def test_host_sorts_in_flight_on_two_streams():
 
 @pytest.mark.parametrize("opts,P", [({"merge_ways": 4}, 64), ({"merge_ways": 4}, 32), ({"exchange": "scatter"}, 16),
                                     ({"exchange": "scatter", "merge_ways": 4}, 128), ({"splitters": "learned"}, 24),
-                                    ({"investigator": "local"}, 12), ({"guaranteed": True}, 40), ({}, 2), ({}, 3)])
+                                    ({"investigator": "local"}, 12), ({"guaranteed": True}, 40), ({}, 2), ({}, 3),
+                                    ({"copy_back": "end"}, 64), ({"copy_back": "end", "merge_ways": 4}, 5),
+                                    ({"copy_back": "end"}, 1)])
 def test_host_sort_bucket_groups_with_every_option(opts, P):
     """Step 6 in bucket groups under four-way rounds, the scatter exchange,
     learned splitters and every P shape (bucket rounds after the first: none,
