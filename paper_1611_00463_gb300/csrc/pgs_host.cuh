@@ -408,14 +408,17 @@ inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* 
 // (tile counts of the chosen tile shape).  `len` keys take part; every one of
 // them is read and written once.  idx_in: the key index of ks (NULL: none);
 // idx_out: where the round writes the key index of kd (NULL: not written).
+// live_pairs: an upper bound on the slots that can hold a non-empty pair (the
+// grid covers ceil(len / tile) tiles plus one partial tile per such pair;
+// empty CTAs beyond the round's total cost launch time).
 template <typename K, bool V>
 inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, const K* idx_in = nullptr,
-                       K* idx_out = nullptr) {
+                       K* idx_out = nullptr, uint64_t live_pairs = ~0ull) {
   const MergeShape ms = kMergeShapes[c.variant];
   const uint32_t tile = (uint32_t)(ms.nt * ms.vt);
   PGS_TRY(scan_u64(c, b.tcount, b.tbegin, npairs, b.scan_sums, b.scan_sums2, step));
-  const uint64_t tiles_ub = ceil_div(len, tile) + npairs;
+  const uint64_t tiles_ub = ceil_div(len, tile) + std::min(npairs, live_pairs);
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, tile), [&] {
     k_partition_split<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.split, tile,
                                                                     idx_in);
@@ -440,9 +443,10 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
 // cuts, their order by rank, then one CTA per chunk.
 template <typename K, bool V>
 inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t nquads,
-                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, K* idx_out) {
+                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, K* idx_out,
+                        uint64_t live_quads = ~0ull) {
   PGS_TRY(scan_u64(c, b.ccount, b.coff, nquads, b.scan_sums, b.scan_sums2, step));
-  const uint64_t chunks_ub = ceil_div(len, kMerge4Cut) + nquads;
+  const uint64_t chunks_ub = ceil_div(len, kMerge4Cut) + std::min(nquads, live_quads);
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, kMerge4Cut), [&] {
     k_cuts4<K><<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(ks, b.quads, b.coff, nquads, b.cuts_a, kMerge4Cut);
   }));
@@ -611,14 +615,23 @@ struct Pipeline {
     std::swap(cur_v, oth_v);
   }
   int f32_out() const { return left == 0 ? f32 : 0; }   // float bits back on the last pass
+  // Slots of a bucket round that can hold a non-empty pair: in a bucket of p
+  // segments only the ceil(p / (2 step)) slots j with j % (2 step) == 0 do,
+  // and summed over the buckets in Qg slots (at most sh.R of them) that is at
+  // most Qg / (2 step) + sh.R.  (A four-way round at `step` has its quads at
+  // j % (4 step) == 0: the same bound at 2 step.)
+  uint64_t bucket_live_pairs(uint64_t Qg, uint32_t step) const {
+    return ceil_div(Qg, 2ull * step) + sh.R;
+  }
   // The key index: read while it describes the round's input; written by
   // every merge pass but the last (whose output no partition searches).
   const K* idx_in() const { return idx_ok ? static_cast<const K*>(b.kidx) : nullptr; }
   K* idx_out() const { return left > 0 ? static_cast<K*>(b.kidx) : nullptr; }
   // A pairwise round of the pairs in b.pairs from cur to oth (left already counts it).
-  int pair_round(uint64_t npairs, uint64_t len, uint32_t step) {
+  int pair_round(uint64_t npairs, uint64_t len, uint32_t step, uint64_t live_pairs = ~0ull) {
     K* io = idx_out();
-    PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, npairs, len, b, f32_out(), step, idx_in(), io)));
+    PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, npairs, len, b, f32_out(), step, idx_in(), io,
+                               live_pairs)));
     idx_ok = io != nullptr;
     return PGS_OK;
   }
@@ -756,7 +769,7 @@ struct Pipeline {
       k_pairs_fused<<<grid_for(sh.Q, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, b.seg_src, 0, sh.Q, mtile);
     }));
     --left;
-    PGS_TRY(pair_round(sh.Q, n, 6));
+    PGS_TRY(pair_round(sh.Q, n, 6, bucket_live_pairs(sh.Q, 1)));
     flip();
     k0 = 1;
     return PGS_OK;
@@ -774,7 +787,8 @@ struct Pipeline {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * Qg, [&] {
           k_quads_buckets<<<grid_for(Qg, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, q0, Qg, step, kMerge4Cut);
         }));
-        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6, idx_out())));
+        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6, idx_out(),
+                                    bucket_live_pairs(Qg, 2 * step))));
         idx_ok = idx_out() != nullptr;
         step *= 4;
         levels -= 2;
@@ -783,7 +797,7 @@ struct Pipeline {
           k_pairs_bucket_lists<<<grid_for(Qg, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, q0, Qg, step,
                                                                    mtile);
         }));
-        PGS_TRY(pair_round(Qg, len, 6));
+        PGS_TRY(pair_round(Qg, len, 6, bucket_live_pairs(Qg, step)));
         step *= 2;
         levels -= 1;
       }
