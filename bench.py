@@ -640,6 +640,20 @@ def main():
     ms_step = ms_total / args.steps
     value = whole_job_rate(n, world, ms_step * 1e-3)
 
+    # The timed calls above replay the launch sequence that the library
+    # captured on the warm-up's second identical call (pgs_graph_cache AUTO);
+    # the same steps with every launch issued from the host are reported beside.
+    cfg_direct = pgs.make_config(workspace=ws, stats=st, graph_cache="off", **opts)
+    dev0, dev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    dev0.record(stream)
+    for _ in range(args.steps):
+        pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_direct, stream)
+    dev1.record(stream)
+    torch.cuda.synchronize(dev)
+    dms = max_over_ranks(dev0.elapsed_time(dev1) / args.steps, dev, world)
+    direct = {"ms_per_step": dms, "value": whole_job_rate(n, world, dms * 1e-3), "unit": "Gkeys/s"}
+
     # The same steps again with a CUDA-event pair around every launch on the
     # sort's stream: the per-kernel durations of the roofline and the per-step
     # breakdown (the events themselves add a little time between launches).
@@ -789,6 +803,9 @@ def main():
             "launches_per_step": stats["launches"],
             "clocks": clocks.summary(),
             "e2e": e2e,
+            "launch": "pgs_sort_copy calls; from the second identical call the library replays the launch "
+                      "sequence it captured into a CUDA graph (pgs_graph_cache AUTO)",
+            "direct_launches": direct,
             "graph_replay": graph,
             "library_comparator": comparator,
             "instrumented_ms_per_step": ms_instr,

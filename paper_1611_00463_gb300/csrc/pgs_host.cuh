@@ -47,6 +47,7 @@ struct Options {
   int tile_variant = 0;       // merge tile shape (see kMergeShapes)
   int merge_ways = 2;         // tree levels per pass: 2-way (one level) or 4-way (two levels)
   int copy_back = PGS_COPY_BACK_GROUPS;   // pgs_sort_host: bucket groups after a host wait, or all at the end
+  int graph_cache = PGS_GRAPH_CACHE_AUTO; // pgs_sort / pgs_sort_copy: replay repeated calls from a CUDA graph
 };
 
 // Validates and copies a (possibly NULL) pgs_config.  Returns PGS_OK or an error.
@@ -71,6 +72,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->tile_variant = cfg->tile_variant;
   o->merge_ways = cfg->merge_ways == 0 ? 2 : cfg->merge_ways;
   o->copy_back = cfg->copy_back;
+  o->graph_cache = cfg->graph_cache;
   if (o->dtype < PGS_U32 || o->dtype > PGS_F32) return PGS_ERR_INVALID;
   if (!(o->eps > 0.0f) || o->eps > 1.0f) return PGS_ERR_INVALID;
   if (o->investigator < 0 || o->investigator > 3) return PGS_ERR_INVALID;
@@ -79,6 +81,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;
   if (o->merge_ways != 2 && o->merge_ways != 4) return PGS_ERR_INVALID;
   if (o->copy_back != PGS_COPY_BACK_GROUPS && o->copy_back != PGS_COPY_BACK_AT_END) return PGS_ERR_INVALID;
+  if (o->graph_cache != PGS_GRAPH_CACHE_AUTO && o->graph_cache != PGS_GRAPH_CACHE_OFF) return PGS_ERR_INVALID;
   return PGS_OK;
 }
 

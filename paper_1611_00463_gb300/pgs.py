@@ -21,6 +21,7 @@ INVESTIGATOR = {"rank": 0, "equal": 1, "off": 2, "local": 3}
 EXCHANGE = {"auto": 0, "scatter": 1, "fused": 2}
 SPLITTERS = {"sampled": 0, "learned": 1}
 COPY_BACK = {"groups": 0, "end": 1}
+GRAPH_CACHE = {"auto": 0, "off": 1}
 DTYPES = {"u32": PGS_U32, "u64": PGS_U64, "f32": PGS_F32}
 KEY_TORCH = {"u32": torch.int32, "u64": torch.int64, "f32": torch.int32}
 MLP_FLOATS = 1 * 32 + 32 + 32 * 32 + 32 + 32 * 1 + 1
@@ -49,6 +50,8 @@ class pgs_config(ctypes.Structure):
         ("model_out", ctypes.c_void_p),
         ("merge_ways", ctypes.c_int32),
         ("copy_back", ctypes.c_int32),
+        ("graph_cache", ctypes.c_int32),
+        ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -240,7 +243,8 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
                 cuts: torch.Tensor | None = None, splitters_out: torch.Tensor | None = None,
                 stats: torch.Tensor | None = None, timer: Timer | None = None,
                 model: torch.Tensor | None = None, model_out: torch.Tensor | None = None,
-                tile_variant: int = 0, merge_ways: int = 0, copy_back: str = "groups") -> pgs_config:
+                tile_variant: int = 0, merge_ways: int = 0, copy_back: str = "groups",
+                graph_cache: str = "auto") -> pgs_config:
     """The options of a call.  The struct holds raw device addresses, so it
     also keeps a reference to every tensor (and the timer) it points to: they
     live as long as the config does, and `make_config(workspace=workspace(...))`
@@ -268,6 +272,7 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
     c.tile_variant = tile_variant
     c.merge_ways = merge_ways
     c.copy_back = COPY_BACK[copy_back]
+    c.graph_cache = GRAPH_CACHE[graph_cache]
     return c
 
 

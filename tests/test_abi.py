@@ -45,7 +45,7 @@ def test_struct_sizes_match_header(lib):
     assert ctypes.sizeof(pgs.pgs_stats) == 64
     assert [lib.pgs_batch_auto_partitions(n) for n in [1, 65535, 65536, 131071, 131072, 1 << 24, 1 << 30]] == \
         [1, 1, 1, 1, 2, 256, 256]
-    assert ctypes.sizeof(pgs.pgs_config) == 32 + 8 * 11
+    assert ctypes.sizeof(pgs.pgs_config) == 32 + 8 * 12
     assert ctypes.sizeof(pgs.pgs_launch_record) == 24
     assert [lib.pgs_kernel_name(i).decode() for i in range(len(pgs.KERNELS))] == pgs.KERNELS
 
@@ -178,3 +178,34 @@ def test_copy_back_option_is_validated():
     bad = pgs.make_config(dtype="u64")
     bad.copy_back = 2
     assert pgs.pgs_host_workspace_bytes(1 << 20, 16, bad) == 0
+
+
+def test_binding_structs_match_the_c_compiler():
+    """Every field of the binding's ctypes structs sits at the offset, and every
+    struct has the size, that the C compiler gives them from include/pgs.h."""
+    import os
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_1611_00463_gb300 import pgs
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = {"pgs_config": pgs.pgs_config, "pgs_stats": pgs.pgs_stats, "pgs_launch_record": pgs.pgs_launch_record}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pgs.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines) + "\n")
+        subprocess.run([cc, "-I", os.path.join(root, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
