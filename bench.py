@@ -73,31 +73,51 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region.
+
+    Sampling starts on entry and the entry waits for the first sample, so the
+    sampler is live before the timed region begins; every sample carries the
+    host time it arrived at, and the summary keeps the samples taken between
+    mark_start() and mark_end() (plus the first one after, which covers the
+    region's last interval).  Without marks every sample counts."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
-                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms",
+                 str(self.INTERVAL_MS), "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            deadline = time.perf_counter() + 5.0
+            while not self.lines and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
 
     def _read(self):
         for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+            self.lines.append((time.perf_counter(), ln.strip()))
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
+        if self.proc is not None:                     # let the sample covering the last interval arrive
+            time.sleep(self.INTERVAL_MS * 1.5e-3)
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -107,10 +127,17 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    def window(self) -> list[str]:
+        if self.t0 is None or self.t1 is None:
+            return [ln for _, ln in self.lines]
+        inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1]
+        after = [ln for t, ln in self.lines if t > self.t1]
+        return inside + after[:1]
+
     def summary(self) -> dict:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.window():
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 8:
                 continue
@@ -125,7 +152,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "interval_ms": self.INTERVAL_MS}
 
 
 def dist_env():
@@ -343,11 +370,13 @@ def run_batched(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
+        clocks.mark_start()
         ev0.record(cur)
         for _ in range(args.steps):
             g.replay()
         ev1.record(cur)
         torch.cuda.synchronize(dev)
+        clocks.mark_end()
         if world > 1:
             dist.barrier()
     ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev, world)
@@ -503,11 +532,13 @@ def run_search(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clocks:
         torch.cuda.synchronize(dev)
+        clocks.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             pgs.pgs_search(kout, q, pos, dtype=dtype, bucket_bounds=e, bucket_out=bkt, workspace=sws, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clocks.mark_end()
     ms = ev0.elapsed_time(ev1) / args.steps
     # Oracle check on a sample of the queries (the sorted array is the CUDA sort's output).
     samp = torch.from_numpy(g.integers(0, M, size=min(M, 1 << 16))).to(dev)
@@ -629,11 +660,13 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
+        clocks.mark_start()
         ev0.record(stream)
         for _ in range(args.steps):
             pgs.pgs_sort_copy(kin, vin, kout, vout, P, cfg_plain, stream)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
+        clocks.mark_end()
         if world > 1:
             dist.barrier()
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), dev, world)
