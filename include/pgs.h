@@ -88,14 +88,16 @@ typedef enum { PGS_SPLITTERS_SAMPLED = 0, PGS_SPLITTERS_LEARNED = 1 } pgs_splitt
  * directions busy).  Ignored by the device-buffer calls. */
 typedef enum { PGS_COPY_BACK_GROUPS = 0, PGS_COPY_BACK_AT_END = 1 } pgs_copy_back;
 
-/* Launch-sequence replay for pgs_sort / pgs_sort_copy.  AUTO: the second call
- * with the same arguments and options (pointers, sizes, every option) captures
- * its launch sequence into a CUDA graph on a stream of the library's own, and
- * that call and later identical ones launch the graph on `stream`: the same
- * kernels on the same buffers, without the host's per-launch work.  A call
- * with a timer, or on a stream that is itself being captured, always launches
- * directly.  At most 16 graphs are kept per process (least recently used
- * first out).  OFF: always launch directly. */
+/* Launch-sequence replay for pgs_sort / pgs_sort_copy and pgs_sort_batched /
+ * pgs_sort_batched_copy.  AUTO: the second call with the same arguments and
+ * options (pointers, sizes, every option; for a batch the plan, its workspace
+ * and buffers) captures its launch sequence into a CUDA graph on a stream of
+ * the library's own, and that call and later identical ones launch the graph
+ * on `stream`: the same kernels on the same buffers, without the host's
+ * per-launch work.  A call with a timer, on a stream that is itself being
+ * captured, or from pgs_batch_tune always launches directly.  At most 16
+ * graphs are kept per process (least recently used first out).  OFF: always
+ * launch directly. */
 typedef enum { PGS_GRAPH_CACHE_AUTO = 0, PGS_GRAPH_CACHE_OFF = 1 } pgs_graph_cache;
 
 /* Kernels of the pipeline, as reported by the launch timer. */
@@ -162,7 +164,7 @@ typedef struct pgs_config {
                                  pairwise rounds, default; 0 means 2) or 4 (two levels per pass: fewer
                                  passes, more shared-memory work per chunk) */
   int32_t   copy_back;         /* pgs_copy_back, pgs_sort_host only; default GROUPS */
-  int32_t   graph_cache;       /* pgs_graph_cache, pgs_sort / pgs_sort_copy; default AUTO */
+  int32_t   graph_cache;       /* pgs_graph_cache, device and batched sorts; default AUTO */
   int32_t   reserved2;
 } pgs_config;
 

@@ -7,6 +7,7 @@
 #include <new>
 #include <vector>
 
+#include "pgs_graph.cuh"
 #include "pgs_host.cuh"
 
 namespace pgs {
@@ -48,29 +49,36 @@ bool ranges_overlap(const void* a, const void* b, uint64_t bytes) {
   return x != y && x < y + bytes && y < x + bytes;
 }
 
+int sort_direct(const Shape& p, const Options& o, const void* ki, const uint32_t* vi, void* ko, uint32_t* vo,
+                cudaStream_t st) {
+  if (o.dtype == PGS_U64) return sort_u64(p, o, ki, vi, ko, vo, st);
+  return sort_u32(p, o, ki, vi, ko, vo, st);
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------------------
-// Launch-sequence replay (pgs_graph_cache).  A device sort's launches depend
-// only on its arguments and options, never on the data (every grid is sized
-// on the host from n, P and the options, and every data-dependent quantity
-// stays on the device), so the sequence of an identical call can be captured
-// once and replayed.
+// The graph cache behind launch_cached (declared in pgs_graph.cuh).
 // ---------------------------------------------------------------------------
 
+namespace {
+
 constexpr size_t kGraphCacheSize = 16;
-using GraphKey = std::array<uint64_t, 24>;
+constexpr int kGraphMaxDevices = 64;
 
 struct GraphEntry {
   GraphKey key{};
   cudaGraphExec_t exec = nullptr;
-  bool failed = false;         // capture did not work for this call: launch directly
+  bool failed = false;         // capture did not work for this key: run directly
   uint64_t used = 0;           // last use, for eviction
 };
 
 struct GraphCache {
-  std::mutex mu;
+  std::mutex mu;               // entries, clock, streams
+  std::mutex capture_mu;       // one capture at a time (the capture streams are shared)
   std::vector<GraphEntry> entries;
   uint64_t clock = 0;
-  std::array<cudaStream_t, 64> capture_stream{};   // per device, created on first use
+  std::array<cudaStream_t, kGraphMaxDevices> capture_stream{};
 };
 
 GraphCache& graph_cache() {
@@ -78,38 +86,18 @@ GraphCache& graph_cache() {
   return *c;
 }
 
-GraphKey graph_key(const Options& o, int device, const void* ki, const uint32_t* vi, const void* ko,
-                   const uint32_t* vo, uint64_t n, uint32_t P) {
-  auto u = [](const void* q) { return (uint64_t)reinterpret_cast<uintptr_t>(q); };
-  uint32_t eps_bits;
-  std::memcpy(&eps_bits, &o.eps, sizeof(eps_bits));
-  return GraphKey{u(ki), u(vi), u(ko), u(vo), n, P, (uint64_t)device, (uint64_t)o.dtype, o.samples_per_run,
-                  eps_bits, (uint64_t)o.guaranteed, (uint64_t)o.investigator, (uint64_t)o.exchange,
-                  (uint64_t)o.splitter_mode, u(o.workspace), o.workspace_bytes, u(o.bucket_bounds), u(o.cuts),
-                  u(o.splitters), u(o.stats), u(o.model), u(o.model_out), (uint64_t)o.tile_variant,
-                  (uint64_t)o.merge_ways};
-}
+}  // namespace
 
-int sort_direct(const Shape& p, const Options& o, const void* ki, const uint32_t* vi, void* ko, uint32_t* vo,
-                cudaStream_t st) {
-  if (o.dtype == PGS_U64) return sort_u64(p, o, ki, vi, ko, vo, st);
-  return sort_u32(p, o, ki, vi, ko, vo, st);
-}
-
-// The first call with a key launches directly and records the key; the second
-// captures the sequence on the library's own stream and launches the graph;
-// later ones launch it.  A capture that fails marks the key for direct launches.
-int sort_cached(const Shape& p, const Options& o, const void* ki, const uint32_t* vi, void* ko, uint32_t* vo,
-                cudaStream_t st) {
+int launch_cached(const GraphKey& key_in, bool allow, cudaStream_t st, const std::function<int(cudaStream_t)>& run) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (o.timer || o.graph_cache == PGS_GRAPH_CACHE_OFF || cudaStreamIsCapturing(st, &cap) != cudaSuccess ||
-      cap != cudaStreamCaptureStatusNone) {
+  if (!allow || cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
-    return sort_direct(p, o, ki, vi, ko, vo, st);
+    return run(st);
   }
   int device = -1;
-  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= 64) return PGS_ERR_CUDA;
-  const GraphKey key = graph_key(o, device, ki, vi, ko, vo, p.n, p.R);
+  if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kGraphMaxDevices) return PGS_ERR_CUDA;
+  GraphKey key = key_in;
+  key[key.size() - 1] = (uint64_t)device + 1;
   GraphCache& gc = graph_cache();
   cudaStream_t cs = nullptr;
   {
@@ -117,7 +105,7 @@ int sort_cached(const Shape& p, const Options& o, const void* ki, const uint32_t
     GraphEntry* e = nullptr;
     for (auto& x : gc.entries)
       if (x.key == key) e = &x;
-    if (e == nullptr) {                               // first call: remember it, launch directly
+    if (e == nullptr) {                               // first call: remember the key, run directly
       if (gc.entries.size() >= kGraphCacheSize) {
         size_t lru = 0;
         for (size_t i = 1; i < gc.entries.size(); ++i)
@@ -129,13 +117,9 @@ int sort_cached(const Shape& p, const Options& o, const void* ki, const uint32_t
       ne.key = key;
       ne.used = ++gc.clock;
       gc.entries.push_back(ne);
-      e = nullptr;
     } else {
       e->used = ++gc.clock;
-      if (e->exec) {                                  // replay
-        if (cudaGraphLaunch(e->exec, st) != cudaSuccess) return PGS_ERR_CUDA;
-        return PGS_OK;
-      }
+      if (e->exec) return cudaGraphLaunch(e->exec, st) == cudaSuccess ? PGS_OK : PGS_ERR_CUDA;   // replay
       if (!e->failed) {
         if (!gc.capture_stream[device] &&
             cudaStreamCreateWithFlags(&gc.capture_stream[device], cudaStreamNonBlocking) != cudaSuccess)
@@ -144,15 +128,13 @@ int sort_cached(const Shape& p, const Options& o, const void* ki, const uint32_t
       }
     }
   }
-  if (cs == nullptr) return sort_direct(p, o, ki, vi, ko, vo, st);
-  // Second call: capture (nothing runs), instantiate, launch.  The capture
-  // stream of a device is shared, so captures take turns.
-  static std::mutex capture_mu;
-  std::lock_guard<std::mutex> cap_lock(capture_mu);
+  if (cs == nullptr) return run(st);
+  // Second call: capture (nothing runs), instantiate, launch.
+  std::lock_guard<std::mutex> cap_lock(gc.capture_mu);
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  int rc = ok ? sort_direct(p, o, ki, vi, ko, vo, cs) : PGS_OK;
+  int rc = ok ? run(cs) : PGS_OK;
   if (ok) ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && rc == PGS_OK && g != nullptr;
   if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
@@ -161,23 +143,20 @@ int sort_cached(const Shape& p, const Options& o, const void* ki, const uint32_t
     std::lock_guard<std::mutex> lock(gc.mu);
     for (auto& x : gc.entries)
       if (x.key == key) x.failed = true;
-    return sort_direct(p, o, ki, vi, ko, vo, st);
+    return run(st);
   }
-  {
-    std::lock_guard<std::mutex> lock(gc.mu);
-    bool kept = false;
-    for (auto& x : gc.entries)
-      if (x.key == key && !x.exec) {
-        x.exec = exec;
-        kept = true;
-      }
-    if (cudaGraphLaunch(exec, st) != cudaSuccess) return PGS_ERR_CUDA;
-    if (!kept) cudaGraphExecDestroy(exec);           // evicted meanwhile (or raced): freed once idle
-  }
-  return PGS_OK;
+  std::lock_guard<std::mutex> lock(gc.mu);
+  bool kept = false;
+  for (auto& x : gc.entries)
+    if (x.key == key && !x.exec) {
+      x.exec = exec;
+      kept = true;
+    }
+  const bool launched = cudaGraphLaunch(exec, st) == cudaSuccess;
+  if (!kept) cudaGraphExecDestroy(exec);             // evicted meanwhile, or another thread won: freed once idle
+  return launched ? PGS_OK : PGS_ERR_CUDA;
 }
 
-}  // namespace
 }  // namespace pgs
 
 using namespace pgs;
@@ -215,7 +194,18 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out, 
   rc = use_device_of(keys_out);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  return sort_cached(p, o, keys_in, vals_in, keys_out, vals_out, st);
+  uint32_t eps_bits;
+  std::memcpy(&eps_bits, &o.eps, sizeof(eps_bits));
+  const GraphKey key{1, key_ptr(keys_in), key_ptr(vals_in), key_ptr(keys_out), key_ptr(vals_out), n, p.R,
+                     (uint64_t)o.dtype, o.samples_per_run, eps_bits, (uint64_t)o.guaranteed,
+                     (uint64_t)o.investigator, (uint64_t)o.exchange, (uint64_t)o.splitter_mode, key_ptr(o.workspace),
+                     o.workspace_bytes, key_ptr(o.bucket_bounds), key_ptr(o.cuts), key_ptr(o.splitters),
+                     key_ptr(o.stats), key_ptr(o.model), key_ptr(o.model_out), (uint64_t)o.tile_variant,
+                     (uint64_t)o.merge_ways};
+  const bool allow = o.timer == nullptr && o.graph_cache == PGS_GRAPH_CACHE_AUTO;
+  return launch_cached(key, allow, st, [&](cudaStream_t s) {
+    return sort_direct(p, o, keys_in, vals_in, keys_out, vals_out, s);
+  });
 }
 
 int pgs_sort(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream, const pgs_config* cfg) {

@@ -159,3 +159,29 @@ def test_caller_capture_of_a_cached_call():
         torch.cuda.synchronize()
         g.replay()
         check(kout, vout, bounds, keys, P, dtype)
+
+
+def test_repeated_batched_calls_sort_each_new_input():
+    """The batched sort goes through the same cache: one plan and one set of
+    buffers, fresh keys on every call (direct, capture, replays), each
+    instance exact; a new plan at the same buffers is not mistaken for it."""
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    sizes = [0, 1, 5000, 70_001, 123, 40_000]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(offsets[-1])
+    for Pv in ([1, 1, 4, 32, 2, 16], None):
+        bt = pgs.Batch(offsets, None if Pv is None else np.array(Pv, np.uint32), dtype="u64", with_vals=True)
+        k = torch.empty(n, dtype=torch.int64, device="cuda")
+        v = torch.empty(n, dtype=torch.int32, device="cuda")
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        for i in range(4):
+            keys = inputs.normal_lognormal_u64(n, 900 + i)
+            k.copy_(pgs.as_device_keys(keys, "u64"))
+            v.copy_(torch.arange(n, dtype=torch.int32, device="cuda"))
+            bt.sort_copy(k, v, ko, vo)
+            torch.cuda.synchronize()
+            got_k, got_v = pgs.to_numpy_keys(ko, "u64"), vo.cpu().numpy().view(np.uint32)
+            for a, b in zip(offsets[:-1].astype(int), offsets[1:].astype(int)):
+                wk, wv = O.stable_sort(keys[a:b], np.arange(a, b, dtype=np.uint32), "u64")
+                assert np.array_equal(got_k[a:b], wk) and np.array_equal(got_v[a:b], wv)
