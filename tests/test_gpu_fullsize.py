@@ -164,3 +164,51 @@ def test_full_size_batched():
     with cf.ThreadPoolExecutor(THREADS) as ex:
         res = list(ex.map(loads, range(len(Pi))))
     assert stats["max_bucket"] == max(m for m, _ in res) and stats["min_bucket"] == min(m for _, m in res)
+
+
+def test_more_than_2_32_keys():
+    """2^32 + 12345 u64 keys on P = 1024 (155 GB on the device): positions, tile
+    and index arithmetic past 2^32.  Key j = (hi(j) << 33) | j with hi(j) a
+    multiplicative hash of j, the payload j mod 2^32 (payloads are 32-bit).
+    Checked elementwise and on neighbours, without tensors indexed by other
+    tensors of this size: the output rises strictly, every output key is an
+    input key (its hash part is hi of its own j), every payload is its key's j
+    mod 2^32; n distinct members of the n input keys are a permutation.  The
+    paper-budget load stays under its bound 1 + P/s."""
+    import torch
+    from paper_1611_00463_gb300 import pgs
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < 170e9:
+        pytest.skip(f"needs 170 GB of free device memory, {free / 1e9:.0f} GB free")
+    mult, mask33 = 0x3C6EF35F, (1 << 33) - 1             # j * mult < 2^63 for j < 2^33
+
+    def hi_of(j):
+        return ((j * mult) >> 17) & ((1 << 30) - 1)
+    n, P = (1 << 32) + 12345, 1024
+    dev = torch.device("cuda")
+    kin = torch.empty(n, dtype=torch.int64, device=dev)
+    vin = torch.empty(n, dtype=torch.int32, device=dev)
+    chunk = 1 << 28
+    for lo in range(0, n, chunk):
+        j = torch.arange(lo, min(n, lo + chunk), dtype=torch.int64, device=dev)
+        kin[lo:lo + len(j)] = (hi_of(j) << 33) | j
+        vin[lo:lo + len(j)] = (j & 0xFFFFFFFF).to(torch.int32)
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+    ws = pgs.workspace(n, P, pgs.make_config(dtype="u64"), dev)
+    st = torch.zeros(pgs.STATS_BYTES, dtype=torch.uint8, device=dev)
+    pgs.pgs_sort_copy(kin, vin, kout, vout, P, pgs.make_config(dtype="u64", workspace=ws, stats=st))
+    s = pgs.pgs_get_stats(st)
+    assert s["error"] == 0 and s["n"] == n and s["P"] == P
+    assert s["max_over_mean"] < 1 + P / s["samples_per_run"]
+    del kin, ws
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk + 1)
+        k = kout[lo:hi]
+        assert bool((k[:-1] < k[1:]).all()), f"not strictly rising near {lo}"
+        j = k & mask33
+        assert bool(((k >> 33) == hi_of(j)).all()), f"an output key is not an input key near {lo}"
+        assert bool((j < n).all())
+        assert bool(((j & 0xFFFFFFFF) == (vout[lo:hi].to(torch.int64) & 0xFFFFFFFF)).all()), f"payload near {lo}"
+    del kout, vout
+    torch.cuda.empty_cache()
