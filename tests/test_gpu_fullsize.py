@@ -189,6 +189,8 @@ def test_more_than_2_32_keys():
     dev = torch.device("cuda")
     kin = torch.empty(n, dtype=torch.int64, device=dev)
     vin = torch.empty(n, dtype=torch.int32, device=dev)
+    # Built in chunks: a single torch.arange of more than 2^32 elements leaves
+    # the positions past 2^32 at 0 on CUDA (measured with PyTorch 2.9.1).
     chunk = 1 << 28
     for lo in range(0, n, chunk):
         j = torch.arange(lo, min(n, lo + chunk), dtype=torch.int64, device=dev)
