@@ -211,8 +211,10 @@ size_t pgs_host_workspace_bytes(uint64_t n, uint32_t P, const pgs_config* cfg);
 
 /* Sort host-resident keys (and payloads) out of place through the device: the
  * same sort as pgs_sort_copy, with the copies inside the call.
- *   keys_in/vals_in, keys_out/vals_out: host memory (pinned memory moves at the
- *   link's full rate; pageable memory works, slower); vals both NULL or both
+ *   keys_in/vals_in, keys_out/vals_out: host memory, pinned or pageable (a
+ *   copy from or to pageable memory holds the host until it is done, so each
+ *   group's copy is issued after the previous group's work is enqueued and
+ *   the host waits while the GPU sorts); vals both NULL or both
  *   non-NULL; inputs and outputs must not overlap.  Device pointers are
  *   PGS_ERR_INVALID.  cfg->workspace (device, on the GPU that sorts) must hold
  *   pgs_host_workspace_bytes(n, P, cfg).

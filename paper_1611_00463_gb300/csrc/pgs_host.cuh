@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <vector>
 
 #include "pgs.h"
@@ -542,6 +543,11 @@ struct HostGroups {
   uint32_t groups = 0;                 // 0: the input is already on the device
   uint32_t r0[kHostGroups + 1] = {};   // runs [r0[g], r0[g+1]) form group g
   cudaEvent_t ev[kHostGroups] = {};
+  // Issues group g's copy to the device on cs and records ev[g].  A copy from
+  // pageable memory may hold the host until it is done, so group g + 1's copy
+  // is issued after group g's sort is enqueued: the GPU sorts while the host
+  // waits.  (Pinned copies return at once; the order changes nothing for them.)
+  std::function<int(uint32_t)> copy_in;
   uint32_t out_groups = 0;             // 0: the caller copies the output
   cudaStream_t cs = nullptr;           // copy stream
   void* hk_out = nullptr;              // host outputs
@@ -679,15 +685,18 @@ struct Pipeline {
     return PGS_OK;
   }
 
-  // Step 1 for every run; with host groups, group by group as their copies land.
+  // Step 1 for every run; with host groups, group by group as their copies
+  // land (group g + 1's copy is issued once group g's sort is enqueued).
   int local_sort(const HostGroups* hg) {
     if (hg == nullptr || hg->groups == 0) return sort_runs(0, sh.R, sh.n);
     const Saved s0 = save();
+    PGS_TRY(hg->copy_in(0));
     for (uint32_t gi = 0; gi < hg->groups; ++gi) {
       restore(s0);
       const uint32_t r0 = hg->r0[gi], r1 = hg->r0[gi + 1];
       PGS_CUDA(cudaStreamWaitEvent(st, hg->ev[gi], 0));
       PGS_TRY(sort_runs(r0, r1 - r0, host_run_start(r1, sh.n, sh.R) - host_run_start(r0, sh.n, sh.R)));
+      if (gi + 1 < hg->groups) PGS_TRY(hg->copy_in(gi + 1));
     }
     return PGS_OK;
   }
@@ -819,19 +828,28 @@ struct Pipeline {
     PGS_CUDA(cudaMemcpyAsync(e.data(), b.e, (R + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     PGS_CUDA(cudaStreamSynchronize(st));
     const Saved s0 = save();
-    for (uint32_t gi = 0; gi < hg.out_groups; ++gi) {
-      restore(s0);
+    // Group g's copy back is issued once group g + 1's merges are enqueued (a
+    // copy to pageable memory may hold the host until it is done).
+    auto copy_out = [&](uint32_t gi) -> int {
       const uint64_t b0 = ((uint64_t)gi * R) / hg.out_groups, b1 = ((uint64_t)(gi + 1) * R) / hg.out_groups;
       const uint64_t lo = e[b0], hi = e[b1];
-      if (b1 > b0) PGS_TRY(merge_buckets(b0 * R, (b1 - b0) * R, hi - lo));
-      PGS_CUDA(cudaEventRecord(hg.ev_out[gi], st));
       PGS_CUDA(cudaStreamWaitEvent(hg.cs, hg.ev_out[gi], 0));
       if (hi > lo) {
         PGS_CUDA(cudaMemcpyAsync(static_cast<K*>(hg.hk_out) + lo, kout + lo, (hi - lo) * sizeof(K),
                                  cudaMemcpyDeviceToHost, hg.cs));
         if (V) PGS_CUDA(cudaMemcpyAsync(hg.hv_out + lo, vout + lo, (hi - lo) * 4, cudaMemcpyDeviceToHost, hg.cs));
       }
+      return PGS_OK;
+    };
+    for (uint32_t gi = 0; gi < hg.out_groups; ++gi) {
+      restore(s0);
+      const uint64_t b0 = ((uint64_t)gi * R) / hg.out_groups, b1 = ((uint64_t)(gi + 1) * R) / hg.out_groups;
+      const uint64_t lo = e[b0], hi = e[b1];
+      if (b1 > b0) PGS_TRY(merge_buckets(b0 * R, (b1 - b0) * R, hi - lo));
+      PGS_CUDA(cudaEventRecord(hg.ev_out[gi], st));
+      if (gi > 0) PGS_TRY(copy_out(gi - 1));
     }
+    if (hg.out_groups > 0) PGS_TRY(copy_out(hg.out_groups - 1));
     PGS_CUDA(cudaEventRecord(hg.done, hg.cs));
     PGS_CUDA(cudaStreamWaitEvent(st, hg.done, 0));
     return PGS_OK;
@@ -975,14 +993,15 @@ int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t
   // The copies may overwrite the workspace only after earlier work on `st`.
   PGS_CUDA(cudaEventRecord(hc.start, st));
   PGS_CUDA(cudaStreamWaitEvent(hc.cs, hc.start, 0));
-  for (uint32_t g = 0; g < hg.groups; ++g) {
+  hg.copy_in = [&](uint32_t g) -> int {
     const uint64_t e0 = host_run_start(hg.r0[g], n, R), e1 = host_run_start(hg.r0[g + 1], n, R);
     if (e1 > e0) {
       PGS_CUDA(cudaMemcpyAsync(dki + e0, hk + e0, (e1 - e0) * sizeof(K), cudaMemcpyHostToDevice, hc.cs));
       if (V) PGS_CUDA(cudaMemcpyAsync(dvi + e0, hv + e0, (e1 - e0) * 4, cudaMemcpyHostToDevice, hc.cs));
     }
     PGS_CUDA(cudaEventRecord(hg.ev[g], hc.cs));
-  }
+    return PGS_OK;
+  };
   PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 0, 16 * (uint64_t)(R + 1), [&] {
     k_tables_single<<<grid_for(R + 1, 256), 256, 0, st>>>(b.koff, b.Pt, b.R0, b.mat, b.seg, b.st, b.run_off,
                                                           b.run_inst, n, R, sh.s);
