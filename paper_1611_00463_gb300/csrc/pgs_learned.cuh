@@ -28,7 +28,7 @@ constexpr int kMlpOffW1 = 0, kMlpOffB1 = 32, kMlpOffW2 = 64, kMlpOffB2 = 1088, k
 constexpr int kMlpSteps = 300;
 constexpr float kMlpLr = 0.01f;
 constexpr float kMlpOffDiag = -6.0f;
-constexpr int kMlpBatch = 256;              // training samples per CTA
+constexpr int kMlpBatch = 128;              // training samples per CTA (3 CTAs of 72 KB per SM)
 
 __device__ __forceinline__ bool same_half(int k, int j) { return (k < kMlpHalf) == (j < kMlpHalf); }
 
@@ -117,12 +117,17 @@ __global__ void k_mlp_init(const K* __restrict__ sorted, uint64_t S, MlpState* s
   }
 }
 
+// Per-sample activations are stored unit-major with a padded row (kMlpBatch + 1
+// floats): a thread's stores of its own sample and the per-parameter sums over
+// samples (consecutive units across a warp) are both free of bank conflicts.
+constexpr int kMlpRow = kMlpBatch + 1;
+
 struct MlpGradSmem {
   float w[kMlpW];                 // effective weights
-  float h1[kMlpBatch][kMlpH];
-  float dz1[kMlpBatch][kMlpH];
-  float h2[kMlpBatch][kMlpH];
-  float dz2[kMlpBatch][kMlpH];
+  float h1[kMlpH][kMlpRow];
+  float dz1[kMlpH][kMlpRow];
+  float h2[kMlpH][kMlpRow];
+  float dz2[kMlpH][kMlpRow];
   float x[kMlpBatch];
   float dy[kMlpBatch];
   float r2[kMlpBatch];
@@ -152,38 +157,45 @@ k_mlp_grad(const K* __restrict__ sorted, uint64_t S, const MlpState* __restrict_
   const bool live = i < S;
   const float x = live ? mlp_input<K>(sorted[i], st->kmin, st->scale) : 0.0f;
   const float t = live ? ((float)i + 0.5f) / (float)S : 0.0f;
-  float z1[kMlpH], h1[kMlpH], z2[kMlpH], h2[kMlpH];
+  // Forward pass.  A ReLU's derivative test z > 0 is the same as h > 0 for
+  // h = max(z, 0) (NaN included), so only h1 and the signs of h2 are kept.
+  // Layer 2 runs half by half with the unit loop rolled up, so only h1 stays
+  // in registers (indexed by constants); the operation order is unchanged.
+  float h1[kMlpH];
 #pragma unroll
   for (int j = 0; j < kMlpH; ++j) {
-    z1[j] = sm.w[kMlpOffW1 + j] * x + sm.w[kMlpOffB1 + j];
-    h1[j] = fmaxf(z1[j], 0.0f);
+    h1[j] = fmaxf(sm.w[kMlpOffW1 + j] * x + sm.w[kMlpOffB1 + j], 0.0f);
+    sm.h1[j][tid] = h1[j];
   }
   float y = sm.w[kMlpOffB3];
-#pragma unroll
-  for (int k = 0; k < kMlpH; ++k) {
+  uint32_t live2 = 0;                                   // bit k: h2_k > 0
+  auto unit2 = [&](int k, const float* h) {             // h: the 16 h1 values of k's half
     float acc = sm.w[kMlpOffB2 + k];
     const int lo = k < kMlpHalf ? 0 : kMlpHalf;
 #pragma unroll
-    for (int j = 0; j < kMlpHalf; ++j) acc += sm.w[kMlpOffW2 + k * kMlpH + lo + j] * h1[lo + j];
-    z2[k] = acc;
-    h2[k] = fmaxf(acc, 0.0f);
-    y += sm.w[kMlpOffW3 + k] * h2[k];
-  }
+    for (int j = 0; j < kMlpHalf; ++j) acc += sm.w[kMlpOffW2 + k * kMlpH + lo + j] * h[j];
+    const float h2 = fmaxf(acc, 0.0f);
+    sm.h2[k][tid] = h2;
+    if (h2 > 0.0f) live2 |= 1u << k;
+    y += sm.w[kMlpOffW3 + k] * h2;
+  };
+#pragma unroll 1
+  for (int k = 0; k < kMlpHalf; ++k) unit2(k, h1);
+#pragma unroll 1
+  for (int k = kMlpHalf; k < kMlpH; ++k) unit2(k, h1 + kMlpHalf);
   const float r = live ? y - t : 0.0f;
   const float dy = 2.0f * r / (float)S;
-  float dz2[kMlpH];
-#pragma unroll
-  for (int k = 0; k < kMlpH; ++k) dz2[k] = z2[k] > 0.0f ? dy * sm.w[kMlpOffW3 + k] : 0.0f;
-#pragma unroll
+  // Backward pass: dz2_k = dy w3_k where h2_k > 0, recomputed where used.
+  auto dz2 = [&](int k) { return ((live2 >> k) & 1u) ? dy * sm.w[kMlpOffW3 + k] : 0.0f; };
+#pragma unroll 1
+  for (int k = 0; k < kMlpH; ++k) sm.dz2[k][tid] = dz2(k);
+#pragma unroll 1
   for (int j = 0; j < kMlpH; ++j) {
     const int lo = j < kMlpHalf ? 0 : kMlpHalf;
     float acc = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kMlpHalf; ++k) acc += dz2[lo + k] * sm.w[kMlpOffW2 + (lo + k) * kMlpH + j];
-    sm.dz1[tid][j] = z1[j] > 0.0f ? acc : 0.0f;
-    sm.h1[tid][j] = h1[j];
-    sm.h2[tid][j] = h2[j];
-    sm.dz2[tid][j] = dz2[j];
+    for (int k = 0; k < kMlpHalf; ++k) acc += dz2(lo + k) * sm.w[kMlpOffW2 + (lo + k) * kMlpH + j];
+    sm.dz1[j][tid] = sm.h1[j][tid] > 0.0f ? acc : 0.0f;
   }
   sm.x[tid] = x;
   sm.dy[tid] = dy;
@@ -204,25 +216,41 @@ k_mlp_grad(const K* __restrict__ sorted, uint64_t S, const MlpState* __restrict_
     return (a0 + a1) + (a2 + a3);
   };
   static_assert(kMlpBatch % 4 == 0, "four chains");
-  for (int p = tid; p <= kMlpW; p += blockDim.x) {
-    float g = 0.0f;
-    if (p < kMlpOffB1) {
-      g = sum4([&](int s) { return sm.dz1[s][p] * sm.x[s]; }) * sm.w[p];
-    } else if (p < kMlpOffW2) {
+  // Threads take the 642 sums that can be non-zero (w1, b1, the same-half
+  // entries of W2, b2, w3, b3, the squared residuals) in this order; W2's
+  // cross-half entries are always 0 and are written apart.
+  constexpr int kLiveW2 = kMlpH * kMlpHalf;                       // 512
+  constexpr int kLive = kMlpOffW2 + kLiveW2 + kMlpH + kMlpH + 2;  // 642
+  for (int q = tid; q < kMlpH * kMlpH; q += blockDim.x)
+    if (!same_half(q / kMlpH, q % kMlpH)) out[kMlpOffW2 + q] = 0.0f;
+  for (int l = tid; l < kLive; l += blockDim.x) {
+    float g;
+    int p;
+    if (l < kMlpOffB1) {                                            // w1
+      p = l;
+      g = sum4([&](int s) { return sm.dz1[p][s] * sm.x[s]; }) * sm.w[p];
+    } else if (l < kMlpOffW2) {                                     // b1
+      p = l;
       const int q = p - kMlpOffB1;
-      g = sum4([&](int s) { return sm.dz1[s][q]; });
-    } else if (p < kMlpOffB2) {
-      const int k = (p - kMlpOffW2) / kMlpH, j = (p - kMlpOffW2) % kMlpH;
-      if (same_half(k, j)) g = sum4([&](int s) { return sm.dz2[s][k] * sm.h1[s][j]; }) * sm.w[p];
-    } else if (p < kMlpOffW3) {
-      const int q = p - kMlpOffB2;
-      g = sum4([&](int s) { return sm.dz2[s][q]; });
-    } else if (p < kMlpOffB3) {
-      const int q = p - kMlpOffW3;
-      g = sum4([&](int s) { return sm.dy[s] * sm.h2[s][q]; }) * sm.w[p];
-    } else if (p == kMlpOffB3) {
+      g = sum4([&](int s) { return sm.dz1[q][s]; });
+    } else if (l < kMlpOffW2 + kLiveW2) {                           // W2 within a half
+      const int m = l - kMlpOffW2;
+      const int k = m / kMlpHalf, j = (k < kMlpHalf ? 0 : kMlpHalf) + m % kMlpHalf;
+      p = kMlpOffW2 + k * kMlpH + j;
+      g = sum4([&](int s) { return sm.dz2[k][s] * sm.h1[j][s]; }) * sm.w[p];
+    } else if (l < kMlpOffW2 + kLiveW2 + kMlpH) {                   // b2
+      const int q = l - kMlpOffW2 - kLiveW2;
+      p = kMlpOffB2 + q;
+      g = sum4([&](int s) { return sm.dz2[q][s]; });
+    } else if (l < kMlpOffW2 + kLiveW2 + 2 * kMlpH) {               // w3
+      const int q = l - kMlpOffW2 - kLiveW2 - kMlpH;
+      p = kMlpOffW3 + q;
+      g = sum4([&](int s) { return sm.dy[s] * sm.h2[q][s]; }) * sm.w[p];
+    } else if (l == kLive - 2) {                                    // b3
+      p = kMlpOffB3;
       g = sum4([&](int s) { return sm.dy[s]; });
-    } else {
+    } else {                                                        // squared residuals
+      p = kMlpW;
       g = sum4([&](int s) { return sm.r2[s]; });
     }
     out[p] = g;
