@@ -197,7 +197,7 @@ struct Buffers {
   uint32_t* err;
   float* max_ratio;
   // learned splitters
-  MlpState* mlp; float* mlp_part; float* model; uint64_t* hist; uint64_t* hscan; uint64_t* cutL; uint64_t* eL;
+  MlpState* mlp; float* mlp_part; float* model; uint64_t* cutL; uint64_t* eL;
   uint32_t* fallback; float* learned_ratio;
   Geo geo(const Shape& sh) const {
     return Geo{koff, Pt, R0, mat, seg, st, run_off, run_inst, sh.I, sh.R};
@@ -258,15 +258,13 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->mlp = nullptr;
   b->mlp_part = nullptr;
   b->model = nullptr;
-  b->hist = b->hscan = b->cutL = b->eL = nullptr;
+  b->cutL = b->eL = nullptr;
   b->fallback = nullptr;
   b->learned_ratio = nullptr;
   if (sh.learned) {
     b->mlp = c.take<MlpState>(1);
     b->mlp_part = c.take<float>(ceil_div(std::max<uint64_t>(sh.S, 1), kMlpBatch) * (kMlpW + 1));
     b->model = c.take<float>(kMlpWords);
-    b->hist = c.take<uint64_t>(sh.Q);
-    b->hscan = c.take<uint64_t>(sh.Q + 1);
     b->cutL = c.take<uint64_t>(sh.MAT);
     b->eL = c.take<uint64_t>(sh.R + 1);
     b->fallback = c.take<uint32_t>(1);
@@ -471,9 +469,9 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
 }
 
 // Learned splitters (single sort, P > 1): the model (trained on the sorted
-// sample `sorted` or the caller's), the per-run histogram of every key's
-// bucket, the learned cuts, and the judge's choice between them and the
-// sampled cuts already in b.cut / b.e.
+// sample `sorted` or the caller's), the learned cuts (a bisection of each run
+// per bucket), and the judge's choice between them and the sampled cuts
+// already in b.cut / b.e.
 template <typename K>
 int learned_cuts(const Shape& sh, const Options& o, const K* sorted, const K* runs, Ctx& c, const Buffers& b) {
   cudaStream_t st = c.st;
@@ -500,17 +498,10 @@ int learned_cuts(const Shape& sh, const Options& o, const K* sorted, const K* ru
   if (o.model_out) {
     PGS_CUDA(cudaMemcpyAsync(o.model_out, b.model, 4ull * kMlpWords, cudaMemcpyDeviceToDevice, st));
   }
-  // K11: every key's bucket, one pass over the sorted runs, as per-run counts.
-  PGS_CUDA(cudaMemsetAsync(b.hist, 0, sizeof(uint64_t) * sh.Q, st));
-  const uint64_t segs_per_run = std::max<uint64_t>(1, ceil_div(sh.maxlen, kHistWarpKeys));
-  const uint64_t warps = segs_per_run * P;
-  PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 4, sh.n * sizeof(K) / 2, [&] {
-    k_learned_hist<K><<<(unsigned)ceil_div(warps, kHistNT / 32), kHistNT, 0, st>>>(runs, b.run_off, P, segs_per_run,
-                                                                                  b.model, b.hist);
-  }));
-  PGS_TRY(scan_u64(c, b.hist, b.hscan, sh.Q, b.scan_sums, b.scan_sums2, 4));
-  PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 16 * sh.MAT, [&] {
-    k_learned_cuts<<<grid_for(sh.MAT, 256), 256, 0, st>>>(b.hscan, P, b.cutL);
+  // K11: the learned cut matrix, one bisection of a sorted run per (run, bucket).
+  PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 4, 8 * sh.MAT * (uint64_t)ceil_log2(std::max<uint64_t>(sh.maxlen, 2)), [&] {
+    k_learned_search<K><<<grid_for(sh.MAT, kLearnedSearchNT), kLearnedSearchNT, 0, st>>>(runs, b.run_off, P,
+                                                                                         b.model, b.cutL);
   }));
   PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 8 * sh.MAT, [&] {
     k_learned_colsum<<<grid_for(P + 1, 256), 256, 0, st>>>(b.cutL, P, b.eL);

@@ -1,7 +1,8 @@
 // Learned-CDF splitters: a monotone 1 -> 32 -> 32 -> 1 ReLU model of the key
-// CDF, trained in FP32 on the method's own sorted sample (K10), predicts every
-// key's bucket in one pass over the sorted runs (K11), whose per-run histogram
-// gives the cut matrix.  The sampled splitters with the investigator stay the
+// CDF, trained in FP32 on the method's own sorted sample (K10), gives every
+// key a bucket; as the model is monotone and the runs sorted, the cut of run r
+// at bucket b is found by bisection of the run (K11).  The sampled splitters
+// with the investigator stay the
 // judge: if the learned buckets are more unbalanced than 1 + eps, or a given
 // model is not monotone, the sampled cuts are kept.
 //
@@ -44,7 +45,10 @@ __device__ __forceinline__ float mlp_input(K key, uint64_t kmin, float scale) {
 // order with every product and sum rounded separately (no fused multiply-add):
 // h1_j = max(w1_j x + b1_j, 0); acc = b2_k; acc += W2_kj h1_j for j of k's half
 // in increasing order; h2_k = max(acc, 0); y = b3; y += w3_k h2_k, k = 0..31.
-__device__ __forceinline__ uint32_t mlp_bucket(const float* __restrict__ w, float x, uint32_t P) {
+// W: a pointer to the weights (a volatile one keeps a loop that evaluates the
+// model many times from holding every weight in registers).
+template <typename W = const float*>
+__device__ __forceinline__ uint32_t mlp_bucket(W w, float x, uint32_t P) {
   float h1[kMlpH];
 #pragma unroll
   for (int j = 0; j < kMlpH; ++j) {
@@ -336,82 +340,47 @@ static __global__ void k_mlp_validate(const float* __restrict__ given, float* mo
 }
 
 // ---------------------------------------------------------------------------
-// K11: bucket ids of every key of the sorted runs, in one pass, as a per-run
-// histogram.  A warp covers 32 x 32 consecutive keys of one run: lane l first
-// evaluates the first and the last key of its sub-block of 32; because the
-// bucket id is monotone and the run sorted, equal ids at both ends give the
-// whole sub-block that id.  Sub-blocks with a bucket boundary inside are then
-// evaluated key by key by the whole warp.  Counts are accumulated with
-// warp-aggregated atomics: __match_any_sync groups the lanes holding the same
-// bucket and one lane adds the group's count.
+// K11: the learned cut matrix by bisection of the sorted runs.  The model's
+// signs make every fp32 operation of its evaluation monotone, so its bucket id
+// never decreases along a sorted run and the keys of run r whose id is below b
+// are a prefix: cut[r][b] = #{x in run r : id(x) < b} is the first position
+// whose id is at least b, about log2(n_r) evaluations per (run, bucket)
+// instead of one pass over every key.  (A caller's model whose signs are not
+// monotone is marked invalid and the judge keeps the sampled cuts; its search
+// still ends and stays inside the run.)
 // ---------------------------------------------------------------------------
 
-constexpr int kHistSub = 32;                    // keys per lane sub-block
-constexpr int kHistWarpKeys = 32 * kHistSub;    // keys per warp segment
-constexpr int kHistNT = 256;
-
-__device__ __forceinline__ void hist_add(uint64_t* row, uint32_t bucket, uint32_t count, bool active) {
-  const uint32_t act = __ballot_sync(0xFFFFFFFFu, active);
-  if (!active) return;
-  const uint32_t peers = __match_any_sync(act, bucket);       // lanes holding the same bucket
-  const uint32_t sum = __reduce_add_sync(peers, count);
-  const int leader = __ffs(peers) - 1;
-  if ((int)(threadIdx.x & 31) == leader)
-    atomicAdd(reinterpret_cast<unsigned long long*>(&row[bucket]), (unsigned long long)sum);
-}
+constexpr int kLearnedSearchNT = 256;
 
 template <typename K>
-__global__ void __launch_bounds__(kHistNT)
-k_learned_hist(const K* __restrict__ runs, const uint64_t* __restrict__ run_off, uint32_t P,
-               uint64_t segs_per_run, const float* __restrict__ model, uint64_t* hist) {
+__global__ void __launch_bounds__(kLearnedSearchNT)
+k_learned_search(const K* __restrict__ runs, const uint64_t* __restrict__ run_off, uint32_t P,
+                 const float* __restrict__ model, uint64_t* cutL) {
   __shared__ float w[kMlpW];
   for (int p = threadIdx.x; p < kMlpW; p += blockDim.x) w[p] = model[p];
   __syncthreads();
+  const uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= (uint64_t)P * (P + 1)) return;
   const uint32_t* u = reinterpret_cast<const uint32_t*>(model);
   const uint64_t kmin = (uint64_t)u[kMlpW] | ((uint64_t)u[kMlpW + 1] << 32);
   const float scale = model[kMlpW + 2];
-  const int lane = threadIdx.x & 31;
-  const uint64_t seg = blockIdx.x * (uint64_t)(kHistNT / 32) + (threadIdx.x >> 5);
-  const uint64_t r = seg / segs_per_run, sidx = seg % segs_per_run;
-  if (r >= P) return;
-  const uint64_t rs = run_off[r], re = run_off[r + 1];
-  const uint64_t s0 = rs + sidx * kHistWarpKeys;
-  if (s0 >= re) return;                                      // warp-uniform
-  uint64_t* row = hist + r * P;
-  const uint64_t a = s0 + (uint64_t)lane * kHistSub;
-  const uint64_t b = umin(a + kHistSub, re);                 // [a, b): this lane's sub-block
-  const bool has = a < re;
-  uint32_t bf = 0, bl = 0;
-  if (has) {
-    bf = mlp_bucket(w, mlp_input<K>(runs[a], kmin, scale), P);
-    bl = mlp_bucket(w, mlp_input<K>(runs[b - 1], kmin, scale), P);
-  }
-  const bool whole = has && bf == bl;
-  hist_add(row, bf, (uint32_t)(b - a), whole);
-  uint32_t mixed = __ballot_sync(0xFFFFFFFFu, has && !whole);
-  while (mixed) {
-    const int l = __ffs(mixed) - 1;
-    mixed &= mixed - 1;
-    const uint64_t la = s0 + (uint64_t)l * kHistSub;
-    const uint64_t lb = umin(la + kHistSub, re);
-    const uint64_t p = la + lane;
-    const bool in = p < lb;
-    const uint32_t id = in ? mlp_bucket(w, mlp_input<K>(runs[p], kmin, scale), P) : 0;
-    hist_add(row, id, 1, in);
-  }
-}
-
-// cut[r][b] = sum_{b' < b} hist[r][b'] (from the run-major exclusive scan of
-// the histogram), the learned bucket vector e_b = sum_r cut[r][b], and the
-// decision: keep the learned cuts only for a valid model whose largest bucket
-// is at most (1 + eps) n / P.
-static __global__ void k_learned_cuts(const uint64_t* __restrict__ scanned, uint32_t P, uint64_t* cutL) {
-  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (q >= (uint64_t)P * (P + 1)) return;
   const uint64_t r = q / (P + 1), b = q % (P + 1);
-  cutL[q] = scanned[r * P + b] - scanned[r * P];
+  const uint64_t rs = run_off[r], n = run_off[r + 1] - rs;
+  uint64_t lo = b == P ? n : 0, hi = b == 0 ? 0 : n;       // b = 0: none below; b = P: all below
+  if (b > 0 && b < P) {
+    while (lo < hi) {
+      const uint64_t mid = lo + ((hi - lo) >> 1);
+      if (mlp_bucket<const volatile float*>(w, mlp_input<K>(runs[rs + mid], kmin, scale), P) < (uint32_t)b)
+        lo = mid + 1;
+      else hi = mid;
+    }
+  }
+  cutL[q] = lo;
 }
 
+// The learned bucket vector e_b = sum_r cut[r][b], and the decision: keep the
+// learned cuts only for a valid model whose largest bucket is at most
+// (1 + eps) n / P.
 static __global__ void k_learned_colsum(const uint64_t* __restrict__ cutL, uint32_t P, uint64_t* eL) {
   const uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (b > P) return;
