@@ -467,6 +467,37 @@ __device__ __forceinline__ uint64_t merge_path_indexed(const K* src, const K* __
 // Lists shorter than this bisect the keys directly.
 constexpr uint64_t kIdxMinList = 1024;
 
+// The last p in [0, n) with t[p] <= i, for t non-decreasing with t[0] = 0 <= i:
+// gallop from the guess g to a bracket, then bisect it.  Tiles spread nearly
+// evenly over the pairs, so the guess i n / t[n] is usually a few pairs off
+// and the search takes a few loads instead of log2(n).
+__device__ __forceinline__ uint64_t last_le_from(const uint64_t* __restrict__ t, uint64_t n, uint64_t i,
+                                                 uint64_t g) {
+  uint64_t lo, hi;                                  // t[lo] <= i, and hi == n or t[hi] > i
+  if (t[g] <= i) {
+    lo = g;
+    for (uint64_t step = 1;; step <<= 1) {
+      const uint64_t nx = lo + step;
+      if (nx >= n) { hi = n; break; }
+      if (t[nx] > i) { hi = nx; break; }
+      lo = nx;
+    }
+  } else {
+    hi = g;
+    for (uint64_t step = 1;; step <<= 1) {
+      if (hi <= step) { lo = 0; break; }
+      const uint64_t nx = hi - step;
+      if (t[nx] <= i) { lo = nx; break; }
+      hi = nx;
+    }
+  }
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (t[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 template <typename K>
 __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restrict__ pairs,
                                   const uint64_t* __restrict__ tbegin, uint64_t npairs, TileSplit* split,
@@ -474,11 +505,8 @@ __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restr
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t total = tbegin[npairs];
   if (i >= total) return;
-  uint64_t lo = 0, hi = npairs;                     // last p with tbegin[p] <= i
-  while (hi - lo > 1) {
-    uint64_t mid = (lo + hi) >> 1;
-    if (tbegin[mid] <= i) lo = mid; else hi = mid;
-  }
+  const uint64_t guess = (uint64_t)(((unsigned __int128)i * npairs) / total);   // < npairs as i < total
+  const uint64_t lo = last_le_from(tbegin, npairs, i, guess);                 // the tile's pair
   const Pair pr = pairs[lo];
   const uint64_t d0 = (i - tbegin[lo]) * tile;
   const uint64_t a0 = (kidx && pr.na >= kIdxMinList && pr.nb >= kIdxMinList)

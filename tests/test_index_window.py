@@ -1,5 +1,7 @@
-"""The window bound of the indexed merge-path search (the partition kernel's
-`merge_path_indexed`), checked by brute force.
+"""The partition kernel's two searches, in its own integer steps, checked by
+brute force: the window bound of the indexed merge-path search
+(`merge_path_indexed`) and the pair search that starts from a guess
+(`last_le_from`).
 
 Lists A = src[pa, pa + na) and B = src[pb, pb + nb) are sorted; the index
 holds the keys at global multiples of the stride S (64 in the kernel).  The
@@ -99,3 +101,52 @@ def test_window_is_narrow_at_the_kernel_stride():
             want = int(np.sum(posA < d))
             lo, hi = window(src, pa, na, pb, nb, d, S)
             assert lo <= want <= hi and hi - lo <= 2 * S - 1
+
+
+def last_le_from(t, n, i, g):
+    """The partition kernel's pair search (gallop from a guess, then bisect),
+    in the kernel's steps."""
+    if t[g] <= i:
+        lo, step = g, 1
+        while True:
+            nx = lo + step
+            if nx >= n:
+                hi = n
+                break
+            if t[nx] > i:
+                hi = nx
+                break
+            lo, step = nx, step * 2
+    else:
+        hi, step = g, 1
+        while True:
+            if hi <= step:
+                lo = 0
+                break
+            nx = hi - step
+            if t[nx] <= i:
+                lo = nx
+                break
+            hi, step = nx, step * 2
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if t[mid] <= i:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def test_pair_search_from_any_guess():
+    """For tile i the search returns the last pair p with tbegin[p] <= i (empty
+    pairs repeat a tbegin value) from any starting guess."""
+    g = np.random.default_rng(11)
+    for _ in range(200):
+        n = int(g.integers(1, 60))
+        counts = g.integers(0, 4, size=n) * (g.random(n) < 0.7)
+        t = np.concatenate([[0], np.cumsum(counts)]).astype(int)
+        total = int(t[-1])
+        for i in range(total):
+            want = max(p for p in range(n) if t[p] <= i)
+            for guess in {0, n - 1, (i * n) // total, int(g.integers(0, n))}:
+                assert last_le_from(t, n, i, guess) == want
