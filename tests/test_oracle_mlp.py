@@ -98,6 +98,23 @@ def test_effective_weights_are_monotone_and_forward_rises():
         assert np.all(np.diff(b) >= 0)
 
 
+def test_halves_are_convex_and_concave():
+    """The sign constraints make the +x half a rising convex function and the
+    -x half a rising concave one (the model class is their sums): second
+    differences on a uniform grid have the half's sign."""
+    x = np.linspace(-0.5, 1.5, 20_001)
+    half = np.arange(32) < 16
+    for seed in range(5):
+        eff = O.mlp_effective(random_raw(seed))
+        for keep, sign in ((half, 1.0), (~half, -1.0)):
+            e = dict(eff)
+            e["w3"] = np.where(keep, eff["w3"], 0.0)
+            e["b3"] = np.array(0.0)
+            y, _ = O.mlp_forward64(e, x)
+            assert np.all(np.diff(y) >= -1e-12)
+            assert np.all(sign * np.diff(y, 2) >= -1e-12)
+
+
 def test_float32_buckets_agree_with_float64_away_from_boundaries():
     eff = O.mlp_effective(random_raw(7))
     w = O.mlp_pack(eff)
