@@ -199,7 +199,10 @@ int pgs_batch_tune(pgs_batch* bt, void* scratch_keys, uint32_t* scratch_vals, vo
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   PGS_CUDA(cudaEventCreate(&e0));
-  PGS_CUDA(cudaEventCreate(&e1));
+  if (cudaError_t e = cudaEventCreate(&e1); e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return record_cuda_error(e, "cudaEventCreate", __LINE__);
+  }
   float best = 0.0f;
   int best_v = 0;
   int rc = PGS_OK;
