@@ -138,7 +138,9 @@ typedef struct pgs_config {
   int32_t  dtype;             /* pgs_dtype, default PGS_U32 */
   uint32_t samples_per_run;   /* s; 0 = the paper's budget floor(262144 / (P * key_bytes)) */
   float    eps;               /* target imbalance; 0 = 0.05 */
-  int32_t  guaranteed;        /* 1: s = max(s, ceil(P / eps)) so every bucket < (1 + eps) n / P */
+  int32_t  guaranteed;        /* 1: s = max(s, ceil(P / eps)).  With runs of equal length m = n / P every
+                                 bucket is then below (1 + P/s) m + P <= (1 + eps) m + P, and below
+                                 (1 + eps) m when s divides m (regular-sampling bound, any input) */
   int32_t  investigator;      /* pgs_investigator, default RANK */
   int32_t  exchange;          /* pgs_exchange, default AUTO */
   int32_t  splitter_mode;     /* pgs_splitter_mode, default SAMPLED */
@@ -153,7 +155,10 @@ typedef struct pgs_config {
                                  positions [cut[r][b], cut[r][b+1]) to bucket b */
   void*     splitters;        /* t_1..t_{P-1}, P-1 keys of the key type (float keys as bits) */
   void*     stats;            /* a pgs_stats in device memory */
-  uint64_t  spin_limit;       /* ignored: every device-side wait is bounded at 2 s of %globaltimer */
+  uint64_t  spin_limit;       /* limit of every device-side wait (the merge kernels' waits for their bulk
+                                 copies), in ns of %globaltimer; 0 = 2 s.  A wait that runs out sets bit 0
+                                 of the device error word, the kernel lets its copies in flight land and
+                                 returns, and pgs_get_stats reports PGS_ERR_TIMEOUT */
   pgs_timer* timer;           /* optional: record every launch's duration (host object) */
   /* LEARNED mode only (single sorts): */
   const float* model;         /* optional device model of PGS_MLP_WORDS words to use instead of
@@ -165,8 +170,14 @@ typedef struct pgs_config {
                                  passes, more shared-memory work per chunk) */
   int32_t   copy_back;         /* pgs_copy_back, pgs_sort_host only; default GROUPS */
   int32_t   graph_cache;       /* pgs_graph_cache, device and batched sorts; default AUTO */
-  int32_t   reserved2;
+  int32_t   fault_inject;      /* testing only, 0 = off.  PGS_FAULT_WAIT_TIMEOUT: the first tile of the
+                                  call's first merge round announces its copies to its barrier but issues
+                                  none (nothing is in flight), so its bounded wait runs out after
+                                  spin_limit; the call's output is then incomplete */
 } pgs_config;
+
+/* pgs_config.fault_inject values. */
+#define PGS_FAULT_WAIT_TIMEOUT 1
 
 /* Load statistics of one sort (Table II reports the per-processor share). */
 typedef struct pgs_stats {
@@ -241,16 +252,24 @@ int pgs_sort_host(const void* keys_in, const uint32_t* vals_in, void* keys_out,
  *   Temporary storage is one file-scope device array of
  *   PGS_STATIC_SCRATCH_BYTES inside the library, present on every GPU that
  *   loads it until the process exits; the call allocates and frees nothing.
- *   Limits: n <= PGS_STATIC_MAX_KEYS and P <= PGS_STATIC_MAX_P, otherwise
- *   PGS_ERR_UNSUPPORTED before anything is launched; cfg->workspace must be
- *   NULL (PGS_ERR_INVALID otherwise); every other option works as in pgs_sort.
- *   The first call on a device looks up the array's device address with that
- *   device current (set-up), so make that first call before any stream capture.
- *   All calls share the array: two calls whose work overlaps on the GPU race
- *   and corrupt each other's results; serialise them (one stream). */
+ *   Limits: n <= PGS_STATIC_MAX_KEYS and max(1, min(P, n)) <= PGS_STATIC_MAX_P,
+ *   otherwise PGS_ERR_UNSUPPORTED before anything is launched.  Within those
+ *   limits every option combination fits the array.  cfg->workspace must be
+ *   NULL (PGS_ERR_INVALID otherwise); cfg->graph_cache has no effect (every
+ *   launch is issued directly); every other option works as in pgs_sort.
+ *   The first call on a device is its set-up: it looks up the array's device
+ *   address with that device current, and the CUDA runtime may load the
+ *   library's device code there (lazy loading), which can allocate device
+ *   memory.  Make that first call outside any allocation-free context and
+ *   before any stream capture.  The looked-up address is kept per device for
+ *   the process's lifetime: after cudaDeviceReset the entry point must not be
+ *   used again in that process.
+ *   All calls share the array and it keeps the last call's contents: two calls
+ *   whose work overlaps on the GPU race and corrupt each other's results;
+ *   serialise them (one stream). */
 #define PGS_STATIC_MAX_KEYS (1u << 16)
 #define PGS_STATIC_MAX_P 64u
-#define PGS_STATIC_SCRATCH_BYTES (4u << 20)
+#define PGS_STATIC_SCRATCH_BYTES (8u << 20)
 int pgs_sort_static(void* keys, uint32_t* vals, uint64_t n, uint32_t P, void* stream,
                     const pgs_config* cfg);
 

@@ -20,20 +20,6 @@ int fit_u64(uint64_t, uint32_t, const Options&, const void*, void*, float*, cuda
 
 namespace {
 
-// Make the device that owns `ptr` current (the library has its own runtime state).
-int use_device_of(const void* ptr) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
-    cudaGetLastError();
-    return PGS_ERR_INVALID;
-  }
-  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return PGS_ERR_INVALID;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return PGS_ERR_CUDA;
-  if (cur != a.device && cudaSetDevice(a.device) != cudaSuccess) return PGS_ERR_CUDA;
-  return PGS_OK;
-}
-
 // Host memory (pinned or pageable), not a device allocation.
 bool is_host_pointer(const void* ptr) {
   cudaPointerAttributes a;
@@ -157,6 +143,66 @@ int launch_cached(const GraphKey& key_in, bool allow, cudaStream_t st, const std
   return launched ? PGS_OK : PGS_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------------------
+// The copy streams and events of host-buffer sorts (declared in pgs_host.cuh).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kHostCopiesCache = 16;
+
+struct HostCopiesEntry {
+  int device = -1;
+  const void* workspace = nullptr;
+  HostCopies hc;
+  uint64_t used = 0;
+};
+
+struct HostCopiesCache {
+  std::mutex mu;
+  std::vector<HostCopiesEntry> entries;
+  uint64_t clock = 0;
+};
+
+HostCopiesCache& host_copies_cache() {
+  static HostCopiesCache* c = new HostCopiesCache();   // never destroyed: its streams may outlive static teardown
+  return *c;
+}
+
+}  // namespace
+
+int host_copies_for(const void* workspace, HostCopies* out) {
+  int device = -1;
+  PGS_CUDA(cudaGetDevice(&device));
+  HostCopiesCache& hc = host_copies_cache();
+  std::lock_guard<std::mutex> lock(hc.mu);
+  for (auto& e : hc.entries)
+    if (e.device == device && e.workspace == workspace) {
+      e.used = ++hc.clock;
+      *out = e.hc;
+      return PGS_OK;
+    }
+  HostCopiesEntry ne;
+  ne.device = device;
+  ne.workspace = workspace;
+  const int rc = ne.hc.create();
+  if (rc != PGS_OK) {
+    ne.hc.release();
+    return rc;
+  }
+  if (hc.entries.size() >= kHostCopiesCache) {
+    size_t lru = 0;
+    for (size_t i = 1; i < hc.entries.size(); ++i)
+      if (hc.entries[i].used < hc.entries[lru].used) lru = i;
+    hc.entries[lru].hc.release();
+    hc.entries.erase(hc.entries.begin() + (long)lru);
+  }
+  ne.used = ++hc.clock;
+  hc.entries.push_back(ne);
+  *out = ne.hc;
+  return PGS_OK;
+}
+
 }  // namespace pgs
 
 using namespace pgs;
@@ -191,7 +237,8 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out, 
   const size_t need = carve(p, nullptr, &b);
   if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
     return PGS_ERR_WORKSPACE;
-  rc = use_device_of(keys_out);
+  DeviceGuard dg;
+  rc = dg.use_device_of(keys_out);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t eps_bits;
@@ -201,7 +248,7 @@ int pgs_sort_copy(const void* keys_in, const uint32_t* vals_in, void* keys_out, 
                      (uint64_t)o.investigator, (uint64_t)o.exchange, (uint64_t)o.splitter_mode, key_ptr(o.workspace),
                      o.workspace_bytes, key_ptr(o.bucket_bounds), key_ptr(o.cuts), key_ptr(o.splitters),
                      key_ptr(o.stats), key_ptr(o.model), key_ptr(o.model_out), (uint64_t)o.tile_variant,
-                     (uint64_t)o.merge_ways};
+                     (uint64_t)o.merge_ways, o.spin_limit, (uint64_t)o.fault_inject};
   const bool allow = o.timer == nullptr && o.graph_cache == PGS_GRAPH_CACHE_AUTO;
   return launch_cached(key, allow, st, [&](cudaStream_t s) {
     return sort_direct(p, o, keys_in, vals_in, keys_out, vals_out, s);
@@ -240,7 +287,8 @@ int pgs_sort_host(const void* keys_in, const uint32_t* vals_in, void* keys_out, 
   const size_t need = host_layout(p).total;
   if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
     return PGS_ERR_WORKSPACE;
-  rc = use_device_of(o.workspace);
+  DeviceGuard dg;
+  rc = dg.use_device_of(o.workspace);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (o.dtype == PGS_U64) return sort_host_u64(p, o, keys_in, vals_in, keys_out, vals_out, st);
@@ -265,7 +313,8 @@ int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
   const size_t need = fit_workspace(m, o, nullptr, nullptr);
   if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < need)
     return PGS_ERR_WORKSPACE;
-  rc = use_device_of(samples);
+  DeviceGuard dg;
+  rc = dg.use_device_of(samples);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (o.dtype == PGS_U64) return fit_u64(m, P, o, samples, splitters_out, model_out, st);

@@ -134,12 +134,8 @@ int pgs_batch_upload(pgs_batch* bt, void* workspace, uint64_t workspace_bytes, v
   if (!bt) return PGS_ERR_INVALID;
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 || workspace_bytes < bt->ws_bytes)
     return PGS_ERR_WORKSPACE;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, workspace) != cudaSuccess) {
-    cudaGetLastError();
-    return PGS_ERR_INVALID;
-  }
-  PGS_CUDA(cudaSetDevice(a.device));
+  DeviceGuard dg;
+  PGS_TRY(dg.use_device_of(workspace));
   PGS_TRY(bt->o.dtype == PGS_U64 ? batch_attrs_u64(bt->sh.vals) : batch_attrs_u32(bt->sh.vals));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   PGS_CUDA(cudaMemcpyAsync(workspace, bt->tables.data(), bt->tables_bytes, cudaMemcpyHostToDevice, st));
@@ -160,6 +156,8 @@ int pgs_sort_batched_copy(pgs_batch* bt, const void* keys_in, const uint32_t* va
   if (!keys_in || !keys_out) return PGS_ERR_INVALID;
   if (!o.workspace || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0 || o.workspace_bytes < bt->ws_bytes)
     return PGS_ERR_WORKSPACE;
+  DeviceGuard dg;
+  PGS_TRY(dg.use_device_of(o.workspace));                   // the device the batch's tables were uploaded to
   // Batch options: the sampling settings fixed at create time; the per-call
   // outputs of a single sort are not written for a batch.
   Options run = bt->o;
@@ -172,13 +170,15 @@ int pgs_sort_batched_copy(pgs_batch* bt, const void* keys_in, const uint32_t* va
   run.bucket_bounds = nullptr;
   run.cuts = nullptr;
   run.splitters = nullptr;
+  run.spin_limit = o.spin_limit;
+  run.fault_inject = o.fault_inject;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // Repeated identical calls replay a captured graph (pgs_graph_cache): the
   // key holds the plan, the buffers (the workspace holds the uploaded tables)
   // and the per-call options.
   const GraphKey key{2, bt->id, key_ptr(keys_in), key_ptr(vals_in), key_ptr(keys_out), key_ptr(vals_out),
                      key_ptr(run.workspace), run.workspace_bytes, key_ptr(run.stats), (uint64_t)run.investigator,
-                     (uint64_t)run.tile_variant, (uint64_t)run.dtype};
+                     (uint64_t)run.tile_variant, (uint64_t)run.dtype, run.spin_limit, (uint64_t)run.fault_inject};
   const bool allow = o.timer == nullptr && o.graph_cache == PGS_GRAPH_CACHE_AUTO;
   const Shape& sh = bt->sh;
   return launch_cached(key, allow, st, [&](cudaStream_t s) {
@@ -196,6 +196,8 @@ int pgs_batch_tune(pgs_batch* bt, void* scratch_keys, uint32_t* scratch_vals, vo
   if (!bt) return PGS_ERR_INVALID;
   if (bt->sh.n && !scratch_keys) return PGS_ERR_INVALID;
   if ((scratch_vals != nullptr) != bt->sh.vals) return PGS_ERR_INVALID;
+  DeviceGuard dg;
+  if (bt->sh.n) PGS_TRY(dg.use_device_of(scratch_keys));     // the events belong to the sorting device
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   PGS_CUDA(cudaEventCreate(&e0));

@@ -49,6 +49,8 @@ struct Options {
   int merge_ways = 2;         // tree levels per pass: 2-way (one level) or 4-way (two levels)
   int copy_back = PGS_COPY_BACK_GROUPS;   // pgs_sort_host: bucket groups after a host wait, or all at the end
   int graph_cache = PGS_GRAPH_CACHE_AUTO; // pgs_sort / pgs_sort_copy: replay repeated calls from a CUDA graph
+  uint64_t spin_limit = 0;    // ns of %globaltimer a device-side wait may take; 0 = kWaitLimitNs
+  int fault_inject = 0;       // testing only: PGS_FAULT_WAIT_TIMEOUT
 };
 
 // Validates and copies a (possibly NULL) pgs_config.  Returns PGS_OK or an error.
@@ -74,6 +76,8 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->merge_ways = cfg->merge_ways == 0 ? 2 : cfg->merge_ways;
   o->copy_back = cfg->copy_back;
   o->graph_cache = cfg->graph_cache;
+  o->spin_limit = cfg->spin_limit;
+  o->fault_inject = cfg->fault_inject;
   if (o->dtype < PGS_U32 || o->dtype > PGS_F32) return PGS_ERR_INVALID;
   if (!(o->eps > 0.0f) || o->eps > 1.0f) return PGS_ERR_INVALID;
   if (o->investigator < 0 || o->investigator > 3) return PGS_ERR_INVALID;
@@ -83,6 +87,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   if (o->merge_ways != 2 && o->merge_ways != 4) return PGS_ERR_INVALID;
   if (o->copy_back != PGS_COPY_BACK_GROUPS && o->copy_back != PGS_COPY_BACK_AT_END) return PGS_ERR_INVALID;
   if (o->graph_cache != PGS_GRAPH_CACHE_AUTO && o->graph_cache != PGS_GRAPH_CACHE_OFF) return PGS_ERR_INVALID;
+  if (o->fault_inject != 0 && o->fault_inject != PGS_FAULT_WAIT_TIMEOUT) return PGS_ERR_INVALID;
   return PGS_OK;
 }
 
@@ -299,6 +304,48 @@ inline int record_cuda_error(cudaError_t e, const char* where, int line) {
     if (rc_ != PGS_OK) return rc_; \
   } while (0)
 
+// Makes the device that owns a call's memory current for the rest of the call
+// and gives the caller back its own current device on every return path.
+struct DeviceGuard {
+  int saved = -1;
+  bool changed = false;
+  DeviceGuard() {
+    if (cudaGetDevice(&saved) != cudaSuccess) {
+      cudaGetLastError();
+      saved = -1;
+    }
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+  // Device memory (or managed memory) only: the device it lives on.
+  static int device_of(const void* ptr, int* dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+      cudaGetLastError();
+      return PGS_ERR_INVALID;
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return PGS_ERR_INVALID;
+    *dev = a.device;
+    return PGS_OK;
+  }
+  int use(int dev) {
+    if (dev == saved && !changed) return PGS_OK;
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return record_cuda_error(e, "cudaSetDevice", __LINE__);
+    changed = dev != saved;
+    return PGS_OK;
+  }
+  // Makes the device of `ptr` current; PGS_ERR_INVALID if it is not device memory.
+  int use_device_of(const void* ptr) {
+    int dev = -1;
+    PGS_TRY(device_of(ptr, &dev));
+    return use(dev);
+  }
+  ~DeviceGuard() {
+    if (changed && saved >= 0) cudaSetDevice(saved);
+  }
+};
+
 inline unsigned grid_for(uint64_t threads, unsigned block) {
   return (unsigned)std::max<uint64_t>(1, ceil_div(threads, block));
 }
@@ -322,6 +369,8 @@ struct Ctx {
   pgs_timer* timer = nullptr;
   uint32_t launches = 0;
   int variant = 0;            // merge tile shape
+  uint64_t wait_ns = 0;       // limit of every bounded device-side wait (0: kWaitLimitNs)
+  int inject_timeout = 0;     // testing only: the next merge launch's tile 0 waits for copies never issued
 };
 
 // Run `f` (which launches exactly one kernel on c.st), check the launch, count
@@ -401,9 +450,10 @@ inline int set_smem_attrs() {
 
 template <typename K, bool V, int NT, int VT>
 inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t tiles,
-                              const Buffers& b, const uint64_t* total, int f32_out, K* idx_out, cudaStream_t st) {
+                              const Buffers& b, const uint64_t* total, int f32_out, K* idx_out, uint64_t wait_ns,
+                              int inject, cudaStream_t st) {
   k_merge_tile<K, V, NT, VT><<<(unsigned)tiles, NT, Merge2Layout<K, V, NT, VT>::bytes, st>>>(
-      ks, vs, kd, vd, b.split, total, f32_out, b.err, idx_out);
+      ks, vs, kd, vd, b.split, total, f32_out, b.err, idx_out, wait_ns, inject);
 }
 
 // One pairwise merge round over pairs already described in b.pairs / b.tcount
@@ -427,10 +477,12 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
   const uint64_t* total = b.tbegin + npairs;
+  const int inject = c.inject_timeout;
+  c.inject_timeout = 0;                                   // injected into one launch only
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     switch (c.variant) {
 #define PGS_MERGE_SHAPE(i) kMergeShapes[i].nt, kMergeShapes[i].vt
-#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, total, f32_out, idx_out, c.st
+#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, total, f32_out, idx_out, c.wait_ns, inject, c.st
       case 1: launch_merge_tile<K, V, PGS_MERGE_SHAPE(1)>(PGS_MERGE_ARGS); break;
       case 2: launch_merge_tile<K, V, PGS_MERGE_SHAPE(2)>(PGS_MERGE_ARGS); break;
       case 3: launch_merge_tile<K, V, PGS_MERGE_SHAPE(3)>(PGS_MERGE_ARGS); break;
@@ -464,7 +516,7 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
   constexpr size_t smem = Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes;
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     k_merge4<K, V, kMerge4NT, kMerge4VT><<<(unsigned)chunks_ub, kMerge4NT, smem, c.st>>>(
-        ks, vs, kd, vd, b.chunks4, b.coff + nquads, f32_out, b.err, idx_out);
+        ks, vs, kd, vd, b.chunks4, b.coff + nquads, f32_out, b.err, idx_out, c.wait_ns);
   });
 }
 
@@ -589,6 +641,8 @@ struct Pipeline {
            Ctx& c_, const Buffers& b_)
       : sh(sh_), o(o_), c(c_), b(b_), g(b_.geo(sh_)), kin(kin_), vin(vin_), kout(kout_), vout(vout_), st(c_.st) {
     c.variant = o.tile_variant;
+    c.wait_ns = o.spin_limit;
+    c.inject_timeout = o.fault_inject == PGS_FAULT_WAIT_TIMEOUT;
     f32 = o.dtype == PGS_F32;
     kv = sizeof(K) + (V ? 4 : 0);
     mtile = (uint32_t)(kMergeShapes[c.variant].nt * kMergeShapes[c.variant].vt);
@@ -931,22 +985,43 @@ inline HostLayout host_layout(const Shape& sh) {
   return L;
 }
 
-// Copy stream and events of one host-buffer sort, released when the call
-// returns (the runtime frees them once their pending work has finished).
+// Copy stream and events of host-buffer sorts.  They belong to the
+// (device, workspace) pair a call uses and are kept for later calls with the
+// same pair (two calls sharing a workspace must not overlap anyway), so a
+// call creates no stream or event once its pair has been seen.
 struct HostCopies {
   cudaStream_t cs = nullptr;
   cudaEvent_t start = nullptr;
-  HostGroups hg;
-  ~HostCopies() {
+  cudaEvent_t ev[kHostGroups] = {};
+  cudaEvent_t ev_out[kHostGroups] = {};
+  cudaEvent_t done = nullptr;
+  void release() {                 // the runtime frees each object once its pending work has finished
     for (uint32_t g = 0; g < kHostGroups; ++g) {
-      if (hg.ev[g]) cudaEventDestroy(hg.ev[g]);
-      if (hg.ev_out[g]) cudaEventDestroy(hg.ev_out[g]);
+      if (ev[g]) cudaEventDestroy(ev[g]);
+      if (ev_out[g]) cudaEventDestroy(ev_out[g]);
+      ev[g] = ev_out[g] = nullptr;
     }
-    if (hg.done) cudaEventDestroy(hg.done);
+    if (done) cudaEventDestroy(done);
     if (start) cudaEventDestroy(start);
     if (cs) cudaStreamDestroy(cs);
+    done = start = nullptr;
+    cs = nullptr;
+  }
+  int create() {
+    PGS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    PGS_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    for (uint32_t g = 0; g < kHostGroups; ++g) {
+      PGS_CUDA(cudaEventCreateWithFlags(&ev[g], cudaEventDisableTiming));
+      PGS_CUDA(cudaEventCreateWithFlags(&ev_out[g], cudaEventDisableTiming));
+    }
+    PGS_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    return PGS_OK;
   }
 };
+
+// Process-wide cache of HostCopies (16 pairs, least recently used out).
+// Defined once, in the C ABI's translation unit.
+int host_copies_for(const void* workspace, HostCopies* out);
 
 template <typename K, bool V>
 int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t* hv, K* hko, uint32_t* hvo,
@@ -966,18 +1041,18 @@ int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t
   const uint64_t n = sh.n;
   const uint32_t R = sh.R;
   HostCopies hc;
-  HostGroups& hg = hc.hg;
+  PGS_TRY(host_copies_for(o.workspace, &hc));
+  HostGroups hg;
   hg.groups = std::min<uint32_t>(kHostGroups, R);
   for (uint32_t g = 0; g <= hg.groups; ++g) hg.r0[g] = (uint32_t)(((uint64_t)g * R) / hg.groups);
   // Bucket groups copied back during step 6 (P = 1 has no step 6; AT_END
   // copies everything after it and never waits on the host).
   hg.out_groups = (R > 1 && o.copy_back == PGS_COPY_BACK_GROUPS) ? std::min<uint32_t>(kHostGroups, R) : 0;
-  PGS_CUDA(cudaStreamCreateWithFlags(&hc.cs, cudaStreamNonBlocking));
-  PGS_CUDA(cudaEventCreateWithFlags(&hc.start, cudaEventDisableTiming));
-  for (uint32_t g = 0; g < hg.groups; ++g) PGS_CUDA(cudaEventCreateWithFlags(&hg.ev[g], cudaEventDisableTiming));
-  for (uint32_t g = 0; g < hg.out_groups; ++g)
-    PGS_CUDA(cudaEventCreateWithFlags(&hg.ev_out[g], cudaEventDisableTiming));
-  PGS_CUDA(cudaEventCreateWithFlags(&hg.done, cudaEventDisableTiming));
+  for (uint32_t g = 0; g < kHostGroups; ++g) {
+    hg.ev[g] = hc.ev[g];
+    hg.ev_out[g] = hc.ev_out[g];
+  }
+  hg.done = hc.done;
   hg.cs = hc.cs;
   hg.hk_out = hko;
   hg.hv_out = hvo;

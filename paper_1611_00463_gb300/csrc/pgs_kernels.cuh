@@ -528,7 +528,7 @@ template <typename K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT, (merge_min_blocks<K, NT, VT>()))
 k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
              uint32_t* __restrict__ vdst, const TileSplit* __restrict__ split, const uint64_t* __restrict__ total_ptr,
-             int f32_out, uint32_t* err, K* __restrict__ kidx) {
+             int f32_out, uint32_t* err, K* __restrict__ kidx, uint64_t wait_ns, int inject_timeout) {
   using L = Merge2Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -568,11 +568,15 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
       mbar_init(bar, 1);
       fence_barrier_init();
       mbar_arrive_expect_tx(bar, ka.bytes + kb.bytes + va.bytes + vb.bytes);
-      if (ka.bytes) bulk_load(s_kin, ka.base, ka.bytes, bar);
-      if (kb.bytes) bulk_load(reinterpret_cast<char*>(s_kin) + ka.bytes, kb.base, kb.bytes, bar);
-      if (VALS) {
-        if (va.bytes) bulk_load(s_vin, va.base, va.bytes, bar);
-        if (vb.bytes) bulk_load(reinterpret_cast<char*>(s_vin) + va.bytes, vb.base, vb.bytes, bar);
+      // Fault injection (testing only): tile 0 announces its bytes but issues
+      // no copy, so nothing is in flight and its wait runs out.
+      if (!(inject_timeout && tile == 0)) {
+        if (ka.bytes) bulk_load(s_kin, ka.base, ka.bytes, bar);
+        if (kb.bytes) bulk_load(reinterpret_cast<char*>(s_kin) + ka.bytes, kb.base, kb.bytes, bar);
+        if (VALS) {
+          if (va.bytes) bulk_load(s_vin, va.base, va.bytes, bar);
+          if (vb.bytes) bulk_load(reinterpret_cast<char*>(s_vin) + va.bytes, vb.base, vb.bytes, bar);
+        }
       }
     }
     s_na = na;
@@ -595,9 +599,9 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
     sva = s_vin + va.skip;
     svb = reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(s_vin) + va.bytes) + vb.skip;
   }
-  if (!mbar_wait(bar, 0)) {
+  if (!mbar_wait(bar, 0, wait_ns)) {                   // gave up: flag it, let copies in flight land, leave
     if (tid == 0) atomicOr(err, kErrWaitTimeout);
-    mbar_wait(bar, 0);
+    mbar_wait(bar, 0, wait_ns);
     return;
   }
   const int diag = min(tid * VT, cnt);
@@ -889,7 +893,7 @@ template <typename K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT)
 k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
          uint32_t* __restrict__ vdst, const Chunk4* __restrict__ chunks, const uint64_t* __restrict__ total,
-         int f32_out, uint32_t* err, K* __restrict__ kidx) {
+         int f32_out, uint32_t* err, K* __restrict__ kidx, uint64_t wait_ns) {
   using L = Merge4Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -939,9 +943,9 @@ k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __res
   const int na = (int)s_cnt[0], nb = (int)s_cnt[1], nc = (int)s_cnt[2], nd = (int)s_cnt[3];
   const int nx = na + nb, ny = nc + nd, cnt = nx + ny;
   if (cnt == 0) return;
-  if (!mbar_wait(bar, 0)) {
+  if (!mbar_wait(bar, 0, wait_ns)) {
     if (tid == 0) atomicOr(err, kErrWaitTimeout);
-    mbar_wait(bar, 0);
+    mbar_wait(bar, 0, wait_ns);
     return;
   }
   const K* A = reinterpret_cast<const K*>(s_kin + s_off_k[0]);

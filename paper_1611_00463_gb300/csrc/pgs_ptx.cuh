@@ -6,7 +6,7 @@
 
 namespace pgs {
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s: far above any legitimate wait
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // default limit, 2 s: far above any legitimate wait
 constexpr uint32_t kErrWaitTimeout = 1u;           // error word bit: a bounded wait expired
 constexpr uint32_t kErrBadTile = 2u;               // error word bit: a merge tile did not fit its buffer
 
@@ -55,13 +55,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
   return ok != 0;
 }
 
-// Wait for phase `phase` of the barrier to complete, for at most kWaitLimitNs.
-// Returns false if the wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+// Wait for phase `phase` of the barrier to complete, for at most limit_ns of
+// %globaltimer (0: kWaitLimitNs).  Returns false if the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, uint64_t limit_ns) {
   if (mbar_try_wait(bar, phase)) return true;
+  const uint64_t limit = limit_ns ? limit_ns : kWaitLimitNs;
   const uint64_t t0 = global_timer_ns();
   while (!mbar_try_wait(bar, phase)) {
-    if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+    if (global_timer_ns() - t0 > limit) return false;
   }
   return true;
 }

@@ -162,11 +162,8 @@ int pgs_search(const void* keys, uint64_t n, const void* queries, uint64_t m, in
       (bucket_bounds && (!on_device(bucket_bounds) || !on_device(bucket_out))))
     return PGS_ERR_INVALID;
   if (ceil_div(m, kSearchNT) > 0x7FFFFFFFull) return PGS_ERR_UNSUPPORTED;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, pos_out) != cudaSuccess) return PGS_ERR_CUDA;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return PGS_ERR_CUDA;
-  if (cur != a.device && cudaSetDevice(a.device) != cudaSuccess) return PGS_ERR_CUDA;
+  DeviceGuard dg;
+  PGS_TRY(dg.use_device_of(pos_out));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int f32 = o.dtype == PGS_F32;
   if (o.workspace && (!on_device(o.workspace) || (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0))
@@ -195,11 +192,8 @@ int pgs_provenance(const uint32_t* vals, uint64_t m, uint64_t n, uint32_t P, uin
   if (!on_device(vals) || (run_out && !on_device(run_out)) || (index_out && !on_device(index_out)))
     return PGS_ERR_INVALID;
   if (ceil_div(m, kSearchNT) > 0x7FFFFFFFull) return PGS_ERR_UNSUPPORTED;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, vals) != cudaSuccess) return PGS_ERR_CUDA;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess) return PGS_ERR_CUDA;
-  if (cur != a.device && cudaSetDevice(a.device) != cudaSuccess) return PGS_ERR_CUDA;
+  DeviceGuard dg;
+  PGS_TRY(dg.use_device_of(vals));
   const uint64_t Peff = n == 0 ? 1 : std::max<uint64_t>(1, std::min<uint64_t>(P, n));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   k_provenance<<<(unsigned)ceil_div(m, kSearchNT), kSearchNT, 0, st>>>(vals, m, n, Peff, run_out, index_out);

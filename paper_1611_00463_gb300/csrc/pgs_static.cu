@@ -5,12 +5,13 @@
 // allocator.  For them the temporary storage lives in one file-scope device
 // array, so the call allocates nothing.
 //
-// The array is PGS_STATIC_SCRATCH_BYTES (4 MiB) on every GPU that loads the
+// The array is PGS_STATIC_SCRATCH_BYTES (8 MiB) on every GPU that loads the
 // library, held until the process exits; it bounds the request to
 // n <= PGS_STATIC_MAX_KEYS keys on P <= PGS_STATIC_MAX_P partitions.  All calls
 // share it and it keeps the last call's contents (the pipeline writes every
 // byte it reads, so nothing has to start at zero); two calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on it.
+#include <algorithm>
 #include <mutex>
 
 #include "pgs_host.cuh"
@@ -57,21 +58,21 @@ extern "C" int pgs_sort_static(void* keys, uint32_t* vals, uint64_t n, uint32_t 
   if (P == 0) return PGS_ERR_INVALID;
   if (n == 0) return PGS_OK;
   if (!keys) return PGS_ERR_INVALID;
-  if (n > PGS_STATIC_MAX_KEYS || P > PGS_STATIC_MAX_P) return PGS_ERR_UNSUPPORTED;
+  const uint64_t P_eff = std::max<uint64_t>(1, std::min<uint64_t>(P, n));   // the clamp every sort applies
+  if (n > PGS_STATIC_MAX_KEYS || P_eff > PGS_STATIC_MAX_P) return PGS_ERR_UNSUPPORTED;
   Shape p = single_shape(n, P, vals != nullptr, o);
   Buffers b;
   const size_t need = carve(p, nullptr, &b);
-  if (need > PGS_STATIC_SCRATCH_BYTES) return PGS_ERR_UNSUPPORTED;
+  if (need > PGS_STATIC_SCRATCH_BYTES) return PGS_ERR_UNSUPPORTED;   // never within the limits (tested)
 
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, keys) != cudaSuccess) {
-    cudaGetLastError();
-    return PGS_ERR_INVALID;
-  }
-  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return PGS_ERR_INVALID;
-  PGS_CUDA(cudaSetDevice(a.device));
+  DeviceGuard dg;
+  int device = -1;
+  rc = DeviceGuard::device_of(keys, &device);
+  if (rc) return rc;
+  rc = dg.use(device);
+  if (rc) return rc;
   void* scratch = nullptr;
-  rc = scratch_address(a.device, &scratch);
+  rc = scratch_address(device, &scratch);
   if (rc) return rc;
   o.workspace = scratch;
   o.workspace_bytes = PGS_STATIC_SCRATCH_BYTES;

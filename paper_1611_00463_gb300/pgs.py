@@ -22,6 +22,7 @@ EXCHANGE = {"auto": 0, "scatter": 1, "fused": 2}
 SPLITTERS = {"sampled": 0, "learned": 1}
 COPY_BACK = {"groups": 0, "end": 1}
 GRAPH_CACHE = {"auto": 0, "off": 1}
+FAULT_INJECT = {"off": 0, "wait_timeout": 1}     # testing only (pgs_config.fault_inject)
 DTYPES = {"u32": PGS_U32, "u64": PGS_U64, "f32": PGS_F32}
 KEY_TORCH = {"u32": torch.int32, "u64": torch.int64, "f32": torch.int32}
 MLP_FLOATS = 1 * 32 + 32 + 32 * 32 + 32 + 32 * 1 + 1
@@ -51,7 +52,7 @@ class pgs_config(ctypes.Structure):
         ("merge_ways", ctypes.c_int32),
         ("copy_back", ctypes.c_int32),
         ("graph_cache", ctypes.c_int32),
-        ("reserved2", ctypes.c_int32),
+        ("fault_inject", ctypes.c_int32),
     ]
 
 
@@ -244,7 +245,7 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
                 stats: torch.Tensor | None = None, timer: Timer | None = None,
                 model: torch.Tensor | None = None, model_out: torch.Tensor | None = None,
                 tile_variant: int = 0, merge_ways: int = 0, copy_back: str = "groups",
-                graph_cache: str = "auto") -> pgs_config:
+                graph_cache: str = "auto", spin_limit: int = 0, fault_inject: str = "off") -> pgs_config:
     """The options of a call.  The struct holds raw device addresses, so it
     also keeps a reference to every tensor (and the timer) it points to: they
     live as long as the config does, and `make_config(workspace=workspace(...))`
@@ -273,6 +274,8 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
     c.merge_ways = merge_ways
     c.copy_back = COPY_BACK[copy_back]
     c.graph_cache = GRAPH_CACHE[graph_cache]
+    c.spin_limit = spin_limit
+    c.fault_inject = FAULT_INJECT[fault_inject]
     return c
 
 
@@ -351,6 +354,7 @@ def pgs_provenance(vals: torch.Tensor, n: int, P: int, run_out: torch.Tensor | N
 
 STATIC_MAX_KEYS = 1 << 16
 STATIC_MAX_P = 64
+STATIC_SCRATCH_BYTES = 8 << 20
 
 
 def pgs_sort_static(keys: torch.Tensor, vals: torch.Tensor | None, P: int, cfg: pgs_config | None = None,

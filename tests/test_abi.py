@@ -209,3 +209,28 @@ def test_binding_structs_match_the_c_compiler():
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_static_limits_match_header_and_every_option_fits(lib):
+    """pgs_sort_static promises that every option combination fits its scratch
+    array within its n and P limits: the workspace the same sort would need
+    (host-only size query, payload included) stays within the array for every
+    key type, splitter mode, merge width, exchange, sample count and size."""
+    import itertools
+    from paper_1611_00463_gb300 import pgs
+    hdr = open(os.path.join(ROOT, "include", "pgs.h")).read()
+    assert re.search(r"#define PGS_STATIC_MAX_KEYS \(1u << 16\)", hdr) and pgs.STATIC_MAX_KEYS == 1 << 16
+    assert re.search(r"#define PGS_STATIC_MAX_P 64u", hdr) and pgs.STATIC_MAX_P == 64
+    assert re.search(r"#define PGS_STATIC_SCRATCH_BYTES \(8u << 20\)", hdr) and pgs.STATIC_SCRATCH_BYTES == 8 << 20
+    worst = 0
+    for dt, spl, mw, ex, g, s, eps in itertools.product(["u32", "u64", "f32"], ["sampled", "learned"], [2, 4],
+                                                        ["auto", "scatter"], [False, True], [0, 1, 4097, 2**32 - 1],
+                                                        [0.0, 1e-6]):
+        cfg = pgs.make_config(dtype=dt, splitters=spl, merge_ways=mw, exchange=ex, guaranteed=g,
+                              samples_per_run=s, eps=eps)
+        for n in [1 << 16, (1 << 16) - 1, 60_000, 4353, 4352 * 8 + 1, 1]:
+            for P in [64, 63, 33, 2, 1]:
+                b = pgs.pgs_workspace_bytes(n, P, cfg)
+                assert 0 < b <= pgs.STATIC_SCRATCH_BYTES, (dt, spl, mw, ex, g, s, eps, n, P, b)
+                worst = max(worst, b)
+    assert worst > pgs.STATIC_SCRATCH_BYTES // 2        # the grid reaches the expensive combinations

@@ -138,6 +138,25 @@ def test_guaranteed_mode_bound():
     assert got["stats"]["max_bucket"] < (1 + eps) * n / P
 
 
+@pytest.mark.parametrize("name", ["exponential_u32", "zipf_dup_f32"])
+def test_guaranteed_mode_bound_ragged_blocks(name):
+    # s = ceil(64 / 0.05) = 1280 does not divide the run length 32768: blocks
+    # hold 25 or 26 keys and the bound is -P (s-1)/s <= e_b - b m < P m / s,
+    # so every bucket < (1 + eps) m + P.
+    n, P, eps = 1 << 21, 64, 0.05
+    dtype = "f32" if name == "zipf_dup_f32" else "u32"
+    keys = inputs.workload(name, n=n)[1]
+    m = n // P
+    s = max(O.paper_samples_per_run(P, 4), O.guaranteed_samples_per_run(P, eps))
+    assert s == 1280 and m % s != 0
+    got = _gpu(keys, inputs.index_payload(n), P, dtype, guaranteed=True)
+    ref = O.buckets(keys, P, dtype, samples_per_run=s)
+    assert np.array_equal(got["e"], ref["e"])
+    d = got["e"].astype(np.int64) - np.arange(P + 1) * m
+    assert np.all(d * s >= -P * (s - 1)) and np.all(d * s < P * m)
+    assert got["stats"]["max_bucket"] < (1 + eps) * m + P
+
+
 def test_in_place_equals_copy():
     from tests.gpu_helpers import gpu_sort
     n = 30_011

@@ -130,6 +130,55 @@ def test_balance_bound_heavy_duplicates_random():
         _equal_runs_bound_check(keys, P, s)
 
 
+def _ragged_bound_check(keys, P, s, dtype="u32"):
+    """Equal runs of n keys, s samples per run with s not dividing n (blocks of
+    floor or ceil n/s keys).  The run's first floor(k n / s) keys are at or
+    before its k-th sample and fewer than floor((k+1) n / s) are before the
+    next, so t_b's stable rank R_b satisfies b n - P (s-1)/s <= R_b + 1 <=
+    b n + P n / s, and the clamp keeps e_b between b n and R_b:
+    -P (s-1)/s <= e_b - b n < P n / s, every bucket < (1 + P/s) n + P."""
+    n = len(keys) // P
+    assert n * P == len(keys) and s <= n
+    res = O.buckets(keys, P, dtype, samples_per_run=s)
+    d = res["e"] - np.arange(P + 1) * n
+    assert np.all(d * s >= -P * (s - 1))
+    assert np.all(d * s < P * n)
+    sizes = np.diff(res["e"])
+    assert np.all(sizes * s < n * s + P * n + P * (s - 1))
+    assert np.all(sizes * s > n * s - P * n - P * (s - 1))
+    return res
+
+
+@pytest.mark.parametrize("kind", ["random", "few", "equal", "sorted", "reverse", "extremes"])
+@pytest.mark.parametrize("P,s,n", [(4, 3, 64), (8, 5, 128), (16, 7, 64), (7, 6, 35), (32, 60, 256), (5, 64, 100)])
+def test_balance_bound_ragged_blocks(kind, P, s, n):
+    assert n % s != 0
+    N = P * n
+    keys = inputs.uniform_u32(N, 5) if kind == "random" else inputs.structured_u32(kind, N, seed=P * 100 + s)
+    _ragged_bound_check(keys, P, s)
+
+
+def test_balance_bound_ragged_blocks_adversarial():
+    # Heavy duplicates, and keys that put each run's samples at the short end
+    # of the blocks: the lower side of the bound is reached only when s does
+    # not divide n, so a check written for s | n (e_b >= b n) would fail here.
+    g = np.random.default_rng(17)
+    below = 0
+    for _ in range(400):
+        P = int(g.integers(2, 12))
+        n = int(g.integers(3, 40))
+        s = int(g.integers(2, n + 1))
+        if n % s == 0:
+            continue
+        distinct = int(g.integers(1, 6))
+        keys = g.integers(0, distinct, size=P * n).astype(np.uint32)
+        if g.random() < 0.5:
+            keys = np.arange(P * n, dtype=np.uint32) % (n * P // max(1, distinct))
+        res = _ragged_bound_check(keys, P, s)
+        below += int(np.any(res["e"] - np.arange(P + 1) * n < 0))
+    assert below > 0, "no case fell below b n: the test does not reach the ragged side of the bound"
+
+
 def test_all_equal_keys_exact_sizes():
     for N, P in [(100, 7), (1000, 16), (12, 12), (5, 3)]:
         keys = np.full(N, 42, dtype=np.uint32)
