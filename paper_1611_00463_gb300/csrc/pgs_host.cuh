@@ -473,7 +473,7 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
   const uint64_t tiles_ub = ceil_div(len, tile) + std::min(npairs, live_pairs);
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, tile), [&] {
     k_partition_split<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, b.pairs, b.tbegin, npairs, b.split, tile,
-                                                                    idx_in);
+                                                                    idx_in, b.err);
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
   const uint64_t* total = b.tbegin + npairs;
@@ -502,11 +502,12 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
   PGS_TRY(scan_u64(c, b.ccount, b.coff, nquads, b.scan_sums, b.scan_sums2, step));
   const uint64_t chunks_ub = ceil_div(len, kMerge4Cut) + std::min(nquads, live_quads);
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, kMerge4Cut), [&] {
-    k_cuts4<K><<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(ks, b.quads, b.coff, nquads, b.cuts_a, kMerge4Cut);
+    k_cuts4<K><<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(ks, b.quads, b.coff, nquads, b.cuts_a, kMerge4Cut,
+                                                           b.err);
   }));
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 96 * ceil_div(len, kMerge4Cut), [&] {
     k_cuts4_sort<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_a, b.quads, b.coff, nquads, b.cuts_b,
-                                                             kMerge4Cut);
+                                                             kMerge4Cut, b.err);
   }));
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 128 * ceil_div(len, kMerge4Cut), [&] {
     k_chunks4<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_b, b.quads, b.coff, nquads, b.chunks4,
@@ -815,7 +816,7 @@ struct Pipeline {
       --left;
       PGS_TRY(launch(c, PGS_KERNEL_SCATTER, 5, 2 * n * kv, [&] {
         k_scatter<K, V><<<(unsigned)stiles, kScatterNT, sizeof(ScatterSmem<K>), st>>>(
-            cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, f32_out());
+            cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, f32_out(), b.err);
       }));
       idx_ok = false;
       flip();
@@ -870,8 +871,17 @@ struct Pipeline {
   int merge_buckets_to_host(const HostGroups& hg) {
     const uint32_t R = sh.R;
     std::vector<uint64_t> e(R + 1);
+    uint32_t err = 0;
     PGS_CUDA(cudaMemcpyAsync(e.data(), b.e, (R + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    PGS_CUDA(cudaMemcpyAsync(&err, b.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     PGS_CUDA(cudaStreamSynchronize(st));
+    // The bounds size the copies to the caller's host buffers: after a failed
+    // kernel they may be anything, so nothing is copied back.
+    if (err & kErrWaitTimeout) return PGS_ERR_TIMEOUT;
+    if (err) return PGS_ERR_CUDA;
+    bool ok = e[0] == 0 && e[R] == sh.n;
+    for (uint32_t r = 0; r < R && ok; ++r) ok = e[r] <= e[r + 1];
+    if (!ok) return PGS_ERR_CUDA;
     const Saved s0 = save();
     // Group g's copy back is issued once group g + 1's merges are enqueued (a
     // copy to pageable memory may hold the host until it is done).

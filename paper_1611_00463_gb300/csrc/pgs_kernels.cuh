@@ -501,7 +501,8 @@ __device__ __forceinline__ uint64_t last_le_from(const uint64_t* __restrict__ t,
 template <typename K>
 __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restrict__ pairs,
                                   const uint64_t* __restrict__ tbegin, uint64_t npairs, TileSplit* split,
-                                  uint32_t tile, const K* __restrict__ kidx) {
+                                  uint32_t tile, const K* __restrict__ kidx, const uint32_t* err) {
+  if (poisoned(err)) return;
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t total = tbegin[npairs];
   if (i >= total) return;
@@ -543,7 +544,7 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
     const uint64_t total = *total_ptr;
     uint32_t na = 0, nb = 0;
     TileSplit t{};
-    if (tile < total) {
+    if (tile < total && !poisoned(err)) {
       t = split[tile];
       bool same = false;
       TileSplit nx{};
@@ -742,7 +743,8 @@ __device__ __forceinline__ uint64_t upper_bound_g(const K* x, uint64_t n, K v) {
 // X cuts at X positions T, 2T, ..., then the Y cuts.
 template <typename K>
 __global__ void k_cuts4(const K* __restrict__ src, const Quad* __restrict__ quads, const uint64_t* __restrict__ coff,
-                        uint64_t nquads, Cut4* cuts, uint32_t T) {
+                        uint64_t nquads, Cut4* cuts, uint32_t T, const uint32_t* err) {
+  if (poisoned(err)) return;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= coff[nquads]) return;
   const uint64_t qi = last_le<uint64_t>(coff, (uint32_t)nquads, t);
@@ -790,7 +792,9 @@ __global__ void k_cuts4(const K* __restrict__ src, const Quad* __restrict__ quad
 // other side's cuts of smaller rank (ranks are distinct: they are the stable
 // ranks of distinct elements).
 static __global__ void k_cuts4_sort(const Cut4* __restrict__ in, const Quad* __restrict__ quads,
-                                    const uint64_t* __restrict__ coff, uint64_t nquads, Cut4* out, uint32_t T) {
+                                    const uint64_t* __restrict__ coff, uint64_t nquads, Cut4* out, uint32_t T,
+                                    const uint32_t* err) {
+  if (poisoned(err)) return;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= coff[nquads]) return;
   const Cut4 c = in[t];
@@ -828,6 +832,7 @@ struct Chunk4 {               // one chunk of a four-way round: the four source 
 static __global__ void k_chunks4(const Cut4* __restrict__ cuts, const Quad* __restrict__ quads,
                                  const uint64_t* __restrict__ coff, uint64_t nquads, Chunk4* chunks,
                                  uint32_t max_chunk, uint32_t* err) {
+  if (poisoned(err)) return;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= coff[nquads]) return;
   const Cut4 lo = cuts[t];
@@ -906,7 +911,7 @@ k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __res
   const uint64_t t = blockIdx.x;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    if (t < *total) {
+    if (t < *total && !poisoned(err)) {
       const Chunk4 ch = chunks[t];
       uint32_t kbytes = 0, vbytes = 0;
       Span16 ks[4], vs[4];
@@ -1325,7 +1330,8 @@ template <typename K, bool VALS>
 __global__ void __launch_bounds__(kScatterNT)
 k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
           uint32_t* __restrict__ vdst, const uint64_t* __restrict__ off, const uint64_t* __restrict__ seg_src,
-          const uint64_t* __restrict__ first_seg, uint64_t n, uint64_t Q, int f32_out) {
+          const uint64_t* __restrict__ first_seg, uint64_t n, uint64_t Q, int f32_out, const uint32_t* err) {
+  if (poisoned(err)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sm = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
   const uint64_t o = blockIdx.x * (uint64_t)kScatterTile;

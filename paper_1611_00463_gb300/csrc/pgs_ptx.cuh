@@ -10,6 +10,16 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;   // default limit, 2 s: far ab
 constexpr uint32_t kErrWaitTimeout = 1u;           // error word bit: a bounded wait expired
 constexpr uint32_t kErrBadTile = 2u;               // error word bit: a merge tile did not fit its buffer
 
+// True once any kernel of the call has set the device error word.  Every
+// kernel whose addresses depend on the data (merge-path searches, bulk copies,
+// the exchange) returns at once when it is set: a failed tile leaves its
+// output unsorted, and the invariants those addresses rest on (sorted lists,
+// monotone cuts) no longer hold.  The rest of the call then does nothing
+// beyond the statistics, which report the error.
+__device__ __forceinline__ bool poisoned(const uint32_t* err) {
+  return *reinterpret_cast<const volatile uint32_t*>(err) != 0u;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
