@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the number of keys (smaller cases)")
     ap.add_argument("--P", type=int, default=None)
     ap.add_argument("--exchange", default="auto", choices=["auto", "scatter", "fused"])
-    ap.add_argument("--merge-ways", type=int, default=0, choices=[0, 2, 4], help="tree levels per pass (0 = default)")
+    ap.add_argument("--merge-ways", type=int, default=0, choices=[0, 2, 4], help="lists merged per pass (0 = the library default, 4)")
     ap.add_argument("--tile-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="merge tile shape (0 = default; see pgs_config.tile_variant)")
     ap.add_argument("--samples-per-run", type=int, default=0, help="regular samples per run (0 = the paper's budget)")
@@ -305,7 +305,7 @@ def config_block(args, dtype, n, P, stats):
         "n": n, "P": P, "key": dtype, "payload": "u32 index",
         "l2": "inputs larger than L2 (no flush between steps)",
         "exchange": args.exchange,
-        "merge_ways": args.merge_ways or 2,
+        "merge_ways": args.merge_ways or 4,
         "samples_per_run_option": getattr(args, "samples_per_run", 0) or "paper budget",
         "tile_variant": getattr(args, "tile_variant", 0),
         "splitters": args.splitters,

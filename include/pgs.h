@@ -165,9 +165,10 @@ typedef struct pgs_config {
                                  training one; rejected (sampled cuts kept) if its signs do not make
                                  it monotone */
   float*    model_out;        /* optional device buffer of PGS_MLP_WORDS words: the model used */
-  int32_t   merge_ways;       /* levels of the Fig. 2 merge tree per pass over the data: 2 (one level,
-                                 pairwise rounds, default; 0 means 2) or 4 (two levels per pass: fewer
-                                 passes, more shared-memory work per chunk) */
+  int32_t   merge_ways;       /* lists merged per pass over the data (Fig. 2 tree levels per pass):
+                                 4 (two levels per pass, default; 0 means 4) or 2 (one level, pairwise
+                                 rounds).  Four-way tiles hold exactly their share of outputs: tile
+                                 boundaries come from the key index the previous pass wrote */
   int32_t   copy_back;         /* pgs_copy_back, pgs_sort_host only; default GROUPS */
   int32_t   graph_cache;       /* pgs_graph_cache, device and batched sorts; default AUTO */
   int32_t   fault_inject;      /* testing only, 0 = off.  PGS_FAULT_WAIT_TIMEOUT: the first tile of the

@@ -46,7 +46,7 @@ struct Options {
   const float* model = nullptr;
   float* model_out = nullptr;
   int tile_variant = 0;       // merge tile shape (see kMergeShapes)
-  int merge_ways = 2;         // tree levels per pass: 2-way (one level) or 4-way (two levels)
+  int merge_ways = 4;         // list merged per pass: 4 (two tree levels, default) or 2 (one level)
   int copy_back = PGS_COPY_BACK_GROUPS;   // pgs_sort_host: bucket groups after a host wait, or all at the end
   int graph_cache = PGS_GRAPH_CACHE_AUTO; // pgs_sort / pgs_sort_copy: replay repeated calls from a CUDA graph
   uint64_t spin_limit = 0;    // ns of %globaltimer a device-side wait may take; 0 = kWaitLimitNs
@@ -73,7 +73,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->model = cfg->model;
   o->model_out = cfg->model_out;
   o->tile_variant = cfg->tile_variant;
-  o->merge_ways = cfg->merge_ways == 0 ? 2 : cfg->merge_ways;
+  o->merge_ways = cfg->merge_ways == 0 ? 4 : cfg->merge_ways;
   o->copy_back = cfg->copy_back;
   o->graph_cache = cfg->graph_cache;
   o->spin_limit = cfg->spin_limit;
@@ -123,7 +123,7 @@ struct Shape {
   bool scatter = false;      // step 5 as its own pass (else fused into step 6's first round)
   bool four = false;         // four-way rounds (two tree levels per pass)
   uint64_t max_quads = 1;
-  uint64_t max_chunks = 1;
+  uint64_t max_tiles4 = 1;   // tiles of the largest four-way round
   int run_rounds = 0;        // merge rounds growing block-sorted tiles into runs (step 1)
   int bucket_rounds = 0;     // merge rounds of steps 3 and 6: ceil(log2 Pmax)
   uint64_t max_pairs = 1;
@@ -151,10 +151,12 @@ inline void finish_shape(Shape& sh) {
   uint64_t mp = std::max<uint64_t>(sh.R, sh.Q);
   if (sh.run_rounds > 0) mp = std::max<uint64_t>(mp, (uint64_t)sh.R * ceil_div(sh.maxlen, 2ull * kTile));
   sh.max_pairs = std::max<uint64_t>(mp, 1);
-  sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeMinTile) + sh.max_pairs + 1;
   sh.max_quads = std::max<uint64_t>(sh.Q, 1);
   if (sh.run_rounds > 1) sh.max_quads = std::max<uint64_t>(sh.max_quads, (uint64_t)sh.R * ceil_div(sh.maxlen, 4ull * kTile));
-  sh.max_chunks = sh.max_quads + ceil_div(std::max<uint64_t>(sh.n, 1), kMerge4Cut) + 1;
+  if (sh.four) sh.max_pairs = std::max<uint64_t>(sh.max_pairs, 2 * sh.max_quads);   // the index-sample merges
+  sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeMinTile) + sh.max_pairs + 1;
+  sh.max_tiles4 = ceil_div(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) + sh.max_quads, kMerge4Q) +
+                  sh.max_quads + 1;
   sh.scan_len = std::max<uint64_t>(std::max<uint64_t>(sh.max_pairs, sh.Q), sh.max_quads);
   auto passes_for = [&](int levels) { return sh.four ? levels / 2 + levels % 2 : levels; };
   int bucket_passes = 0;
@@ -193,7 +195,8 @@ struct Buffers {
   Pair* pairs; uint64_t *tcount, *tbegin;
   TileSplit* split;
   void* kidx;                // key index of the last pass: the key at every 64th position
-  Quad* quads; uint64_t *ccount, *coff; Cut4 *cuts_a, *cuts_b; Chunk4* chunks4;
+  Quad* quads; uint64_t *tcount4, *tbegin4; Split4* splits4; void* xs;   // four-way rounds
+  uint64_t max_tiles4 = 0;
   uint64_t *scan_sums, *scan_sums2;
   uint64_t* first_seg;
   // batch tables
@@ -243,16 +246,16 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->kidx = c.take<char>(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) * sh.w);
   if (sh.four) {
     b->quads = c.take<Quad>(sh.max_quads);
-    b->ccount = c.take<uint64_t>(sh.max_quads);
-    b->coff = c.take<uint64_t>(sh.max_quads + 1);
-    b->cuts_a = c.take<Cut4>(sh.max_chunks);
-    b->cuts_b = c.take<Cut4>(sh.max_chunks);
-    b->chunks4 = c.take<Chunk4>(sh.max_chunks);
+    b->tcount4 = c.take<uint64_t>(sh.max_quads);
+    b->tbegin4 = c.take<uint64_t>(sh.max_quads + 1);
+    b->splits4 = c.take<Split4>(sh.max_tiles4);
+    b->max_tiles4 = sh.max_tiles4;
+    b->xs = c.take<char>(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) * sh.w);
   } else {
-    b->chunks4 = nullptr;
     b->quads = nullptr;
-    b->ccount = b->coff = nullptr;
-    b->cuts_a = b->cuts_b = nullptr;
+    b->tcount4 = b->tbegin4 = nullptr;
+    b->splits4 = nullptr;
+    b->xs = nullptr;
   }
   const uint64_t chunks = ceil_div(sh.scan_len, kScanChunk);
   b->scan_sums = c.take<uint64_t>(chunks + 1);
@@ -441,6 +444,7 @@ inline int set_smem_attrs() {
   PGS_TRY((set_merge_attr<K, V, kMergeShapes[3].nt, kMergeShapes[3].vt>()));
   PGS_CUDA(cudaFuncSetAttribute(k_merge4<K, V, kMerge4NT, kMerge4VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes));
+  static_assert(merge4_max_tile(kMerge4Q) <= (uint32_t)(kMerge4NT * kMerge4VT), "four-way tiles fit the CTA");
   PGS_CUDA(cudaFuncSetAttribute(k_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ScatterSmem<K>)));
   PGS_CUDA(cudaFuncSetAttribute(k_mlp_grad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -493,31 +497,35 @@ inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t*
   });
 }
 
-// One four-way round over quads already described in b.quads / b.ccount:
-// cuts, their order by rank, then one CTA per chunk.
+// One four-way round over the quads that the caller's quads kernel described
+// in b.quads / b.tcount4, with the index-sample pairs in b.pairs / b.tcount
+// (tile counts at the current merge tile shape).  idx_in: the key index of ks
+// (required); idx_out: where the round writes the key index of kd (NULL: not
+// written).  live_quads bounds the quads that can be non-empty.
 template <typename K, bool V>
 inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t nquads,
-                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, K* idx_out,
+                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, const K* idx_in, K* idx_out,
                         uint64_t live_quads = ~0ull) {
-  PGS_TRY(scan_u64(c, b.ccount, b.coff, nquads, b.scan_sums, b.scan_sums2, step));
-  const uint64_t chunks_ub = ceil_div(len, kMerge4Cut) + std::min(nquads, live_quads);
-  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, kMerge4Cut), [&] {
-    k_cuts4<K><<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(ks, b.quads, b.coff, nquads, b.cuts_a, kMerge4Cut,
-                                                           b.err);
-  }));
-  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 96 * ceil_div(len, kMerge4Cut), [&] {
-    k_cuts4_sort<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_a, b.quads, b.coff, nquads, b.cuts_b,
-                                                             kMerge4Cut, b.err);
-  }));
-  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 128 * ceil_div(len, kMerge4Cut), [&] {
-    k_chunks4<<<grid_for(chunks_ub, 256), 256, 0, c.st>>>(b.cuts_b, b.quads, b.coff, nquads, b.chunks4,
-                                                          2 * kMerge4Cut, b.err);
+  const uint64_t nq_live = std::min(nquads, live_quads);
+  const uint64_t samples = ceil_div(len, kIdxStride) + nq_live;   // index samples of the round, at most
+  K* xs = static_cast<K*>(b.xs);
+  // X' = merge(I_0, I_1) and Y' = merge(I_2, I_3) of every quad (keys only).
+  const int inject = c.inject_timeout;
+  c.inject_timeout = 0;
+  PGS_TRY((merge_round<K, false>(c, idx_in, nullptr, xs, nullptr, 2 * nquads, samples, b, 0, step, nullptr,
+                                 nullptr, 2 * nq_live)));
+  PGS_TRY(scan_u64(c, b.tcount4, b.tbegin4, nquads, b.scan_sums, b.scan_sums2, step));
+  const uint64_t tiles_ub = ceil_div(samples, kMerge4Q) + nq_live + 1;   // <= sh.max_tiles4
+  if (tiles_ub > b.max_tiles4) return PGS_ERR_CUDA;                        // plan bug: never expected
+  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * tiles_ub, [&] {
+    k_corank4<K><<<grid_for(tiles_ub, 256), 256, 0, c.st>>>(ks, idx_in, xs, b.quads, b.tbegin4, nquads, b.splits4,
+                                                            tiles_ub, kMerge4Q, b.err);
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
   constexpr size_t smem = Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes;
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
-    k_merge4<K, V, kMerge4NT, kMerge4VT><<<(unsigned)chunks_ub, kMerge4NT, smem, c.st>>>(
-        ks, vs, kd, vd, b.chunks4, b.coff + nquads, f32_out, b.err, idx_out, c.wait_ns);
+    k_merge4<K, V, kMerge4NT, kMerge4VT><<<(unsigned)tiles_ub, kMerge4NT, smem, c.st>>>(
+        ks, vs, kd, vd, b.splits4, b.quads, b.tbegin4 + nquads, tiles_ub, f32_out, b.err, idx_out, c.wait_ns, inject);
   });
 }
 
@@ -682,6 +690,17 @@ struct Pipeline {
   // every merge pass but the last (whose output no partition searches).
   const K* idx_in() const { return idx_ok ? static_cast<const K*>(b.kidx) : nullptr; }
   K* idx_out() const { return left > 0 ? static_cast<K*>(b.kidx) : nullptr; }
+  // A four-way round of the quads in b.quads from cur to oth (left already
+  // counts it).  Its tile boundaries come from the key index of cur, which
+  // every pass but the last writes for the next.
+  int quad_round(uint64_t nquads, uint64_t len, uint32_t step, uint64_t live_quads = ~0ull) {
+    if (!idx_ok) return PGS_ERR_CUDA;                   // plan bug: no index for this round
+    K* io = idx_out();
+    PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nquads, len, b, f32_out(), step,
+                                static_cast<const K*>(b.kidx), io, live_quads)));
+    idx_ok = io != nullptr;
+    return PGS_OK;
+  }
   // A pairwise round of the pairs in b.pairs from cur to oth (left already counts it).
   int pair_round(uint64_t npairs, uint64_t len, uint32_t step, uint64_t live_pairs = ~0ull) {
     K* io = idx_out();
@@ -697,11 +716,12 @@ struct Pipeline {
   int sort_runs(uint32_t r0, uint32_t Rg, uint64_t len) {
     const uint32_t tiles_per_run = (uint32_t)std::max<uint64_t>(1, ceil_div(sh.maxlen, kTile));
     const uint64_t* ro = b.run_off + r0;
+    K* io = idx_out();
     PGS_TRY(launch(c, PGS_KERNEL_BLOCK_SORT, 1, 2 * len * kv, [&] {
       k_block_sort<K, V><<<(unsigned)((uint64_t)Rg * tiles_per_run), kNT, sizeof(BlockSortSmem<K>), st>>>(
-          kin, vin, cur_k, cur_v, ro, tiles_per_run, f32, f32_out());
+          kin, vin, cur_k, cur_v, ro, tiles_per_run, f32, f32_out(), io);
     }));
-    idx_ok = false;
+    idx_ok = io != nullptr;
     uint64_t w = kTile;
     int levels = sh.run_rounds;
     while (levels > 0) {
@@ -709,11 +729,11 @@ struct Pipeline {
       if (sh.four && levels >= 2) {
         const uint64_t cmax = ceil_div(sh.maxlen, 4 * w);
         const uint64_t nq = cmax * Rg;
-        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 80 * nq, [&] {
-          k_quads_runs<<<grid_for(nq, 256), 256, 0, st>>>(b.quads, b.ccount, ro, Rg, w, cmax, kMerge4Cut);
+        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 112 * nq, [&] {
+          k_quads4_runs<<<grid_for(nq, 256), 256, 0, st>>>(b.quads, b.tcount4, b.pairs, b.tcount, ro, Rg, w, cmax,
+                                                           kMerge4Q, mtile);
         }));
-        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, nq, len, b, f32_out(), 1, idx_out())));
-        idx_ok = idx_out() != nullptr;
+        PGS_TRY(quad_round(nq, len, 1));
         w *= 4;
         levels -= 2;
       } else {
@@ -816,9 +836,9 @@ struct Pipeline {
       --left;
       PGS_TRY(launch(c, PGS_KERNEL_SCATTER, 5, 2 * n * kv, [&] {
         k_scatter<K, V><<<(unsigned)stiles, kScatterNT, sizeof(ScatterSmem<K>), st>>>(
-            cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, f32_out(), b.err);
+            cur_k, cur_v, oth_k, oth_v, b.off, b.seg_src, b.first_seg, n, sh.Q, f32_out(), b.err, idx_out());
       }));
-      idx_ok = false;
+      idx_ok = idx_out() != nullptr;
       flip();
       k0 = 0;
       return PGS_OK;
@@ -842,12 +862,11 @@ struct Pipeline {
     while (levels > 0) {
       --left;
       if (sh.four && levels >= 2) {
-        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 80 * Qg, [&] {
-          k_quads_buckets<<<grid_for(Qg, 256), 256, 0, st>>>(b.quads, b.ccount, g, b.off, q0, Qg, step, kMerge4Cut);
+        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 112 * Qg, [&] {
+          k_quads4_buckets<<<grid_for(Qg, 256), 256, 0, st>>>(b.quads, b.tcount4, b.pairs, b.tcount, g, b.off, q0,
+                                                              Qg, step, kMerge4Q, mtile);
         }));
-        PGS_TRY((merge4_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, Qg, len, b, f32_out(), 6, idx_out(),
-                                    bucket_live_pairs(Qg, 2 * step))));
-        idx_ok = idx_out() != nullptr;
+        PGS_TRY(quad_round(Qg, len, 6, bucket_live_pairs(Qg, 2 * step)));
         step *= 4;
         levels -= 2;
       } else {

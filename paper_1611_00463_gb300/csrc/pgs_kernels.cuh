@@ -17,9 +17,20 @@ constexpr int kNT = 256;             // threads per CTA of the sort and merge ke
 constexpr int kVT = 17;              // items per thread; odd, so blocked smem access is conflict free
 constexpr int kTile = kNT * kVT;     // 4352 keys per block-sort tile and per merge tile
 constexpr int kMergeMinTile = 64 * 17;            // smallest merge tile of the tunable shapes
-constexpr int kMerge4NT = 256;                    // four-way rounds: threads per CTA
-constexpr int kMerge4VT = 9;                      // outputs per thread at most; a chunk holds <= 2304
-constexpr int kMerge4Cut = kMerge4NT * kMerge4VT / 2;   // X and Y are cut every 1152 elements
+// Four-way rounds: threads per CTA, outputs per thread at most (odd, so the
+// blocked staging is free of bank conflicts), and CTAs per SM to compile for.
+#ifndef PGS_MERGE4_NT
+#define PGS_MERGE4_NT 128
+#endif
+#ifndef PGS_MERGE4_VT
+#define PGS_MERGE4_VT 17
+#endif
+#ifndef PGS_MERGE4_MIN_BLOCKS
+#define PGS_MERGE4_MIN_BLOCKS 7
+#endif
+constexpr int kMerge4NT = PGS_MERGE4_NT;
+constexpr int kMerge4VT = PGS_MERGE4_VT;          // a tile holds <= NT x VT outputs (2176)
+constexpr uint32_t kMerge4Q = (kMerge4NT * kMerge4VT - 4 * 63) / 64;   // index samples per tile (30)
 constexpr int kScanNT = 1024;
 constexpr int kScanVT = 8;
 constexpr int kScanChunk = kScanNT * kScanVT;
@@ -145,8 +156,9 @@ __device__ __forceinline__ void serial_merge(const K* s, int ai, int a_end, int 
 // global position 64 e.  Every merge kernel that writes a tile of sorted
 // output [g0, g0 + cnt) also writes the entries whose positions fall inside
 // it, so after the pass the index covers all of the output; the next round's
-// partition bisects it before touching the keys themselves.  (The block sort
-// writes none: its lists, one tile each, are short enough to bisect directly.)
+// partition bisects it before touching the keys themselves, and a four-way
+// round places its tile boundaries with it.  The block sort and the exchange
+// write it too.
 constexpr uint64_t kIdxStride = 64;
 
 template <typename K>
@@ -166,7 +178,8 @@ struct BlockSortSmem {
 template <typename K, bool VALS>
 __global__ void __launch_bounds__(kNT)
 k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kout, uint32_t* vout,
-             const uint64_t* __restrict__ run_off, uint32_t tiles_per_run, int f32_in, int f32_out) {
+             const uint64_t* __restrict__ run_off, uint32_t tiles_per_run, int f32_in, int f32_out,
+             K* __restrict__ kidx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSortSmem<K>& sm = *reinterpret_cast<BlockSortSmem<K>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -234,6 +247,7 @@ k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kou
     sm.ids[tid * kVT + j] = (uint16_t)pos[j];
   }
   __syncthreads();
+  if (kidx) write_key_index(kidx, sm.keys, g0, cnt);
 #pragma unroll
   for (int i = 0; i < kVT; ++i) {
     int idx = i * kNT + tid;
@@ -398,6 +412,34 @@ __device__ __forceinline__ void store_tile_vec(T* g, const T* s, int cnt) {
     gb[c] = u.v;
   }
   for (int i = head + body * E + tid; i < cnt; i += NT) g[i] = s[i];
+}
+
+// Staging offset for a tile that will leave for global address g: element i
+// of the tile is staged at s[pad + i], where pad (< 16 / sizeof(T)) makes the
+// first 16-byte-aligned global element land on a 16-byte-aligned shared slot
+// (s itself 16-byte aligned), so the aligned body can leave by one bulk store.
+template <typename T>
+__device__ __forceinline__ int stage_pad(const T* g) {
+  constexpr int E = 16 / sizeof(T);
+  const int head = (int)(((16 - (reinterpret_cast<uintptr_t>(g) & 15)) & 15) / sizeof(T));
+  return (E - head) % E;
+}
+
+// Store cnt staged elements s[0, cnt) (s = the staging base plus stage_pad(g))
+// to g: the unaligned head and tail element by element, the 16-byte-aligned
+// body by one bulk store issued by thread 0.  Call after every thread has
+// staged its elements, run fence_proxy_async_smem() and passed a barrier;
+// thread 0 then commits and waits for the bulk reads before leaving.
+template <typename T, int NT>
+__device__ __forceinline__ void store_tile_bulk(T* g, const T* s, int cnt) {
+  constexpr int E = 16 / sizeof(T);
+  const int tid = threadIdx.x;
+  int head = (int)(((16 - (reinterpret_cast<uintptr_t>(g) & 15)) & 15) / sizeof(T));
+  if (head > cnt) head = cnt;
+  const int body = ((cnt - head) / E) * E;
+  if (tid < head) g[tid] = s[tid];
+  for (int i = head + body + tid; i < cnt; i += NT) g[i] = s[i];
+  if (tid == 0 && body > 0) bulk_store(g + head, s + head, (uint32_t)(body * sizeof(T)));
 }
 
 // The partition kernel writes, per merge tile, where the tile's A and B ranges
@@ -629,8 +671,10 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
     }
   }
   __syncthreads();                                      // every thread is done reading the inputs
-  K* s_kout = s_kin;                                    // 16-byte aligned staging, cnt <= T items
-  uint32_t* s_vout = s_vin;
+  // Staged over the (now free) input buffers, shifted so that the tile's
+  // 16-byte-aligned body leaves by bulk store (cnt + pad <= T + 3 items).
+  K* s_kout = s_kin + stage_pad(kdst + s_out);
+  uint32_t* s_vout = VALS ? s_vin + stage_pad(vdst + s_out) : nullptr;
 #pragma unroll
   for (int j = 0; j < VT; ++j) {
     if (j < mine) {
@@ -643,74 +687,104 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
     const int j0 = (int)((0u - (uint32_t)s_out - (uint32_t)diag) & (uint32_t)(kIdxStride - 1));
     if (j0 < mine) kidx[(s_out + (uint64_t)(diag + j0)) / kIdxStride] = s_kout[diag + j0];
   }
+  fence_proxy_async_smem();                             // the staging is read by the bulk copy engine
   __syncthreads();
-  store_tile_vec<K, NT>(kdst + s_out, s_kout, cnt);
-  if (VALS) store_tile_vec<uint32_t, NT>(vdst + s_out, s_vout, cnt);
+  store_tile_bulk<K, NT>(kdst + s_out, s_kout, cnt);
+  if (VALS) store_tile_bulk<uint32_t, NT>(vdst + s_out, s_vout, cnt);
+  if (tid == 0) {
+    bulk_commit();
+    bulk_wait_read();
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Four-way merge round: two levels of the Fig. 2 tree in one pass over HBM.
-// Lists A, B, C, D (in stable order) merge into X = merge(A, B), Y = merge(C,
-// D), then merge(X, Y).  The output is cut into chunks at every T-th element
-// of X and of Y (the way step 4 cuts runs at splitters): an X cut at X
-// position m takes the merge-path split of (A, B) at m, and its value's
-// lower bounds in C and D (equal keys of C and D come after it); a Y cut
-// takes the split of (C, D) and upper bounds in A and B.  Sorted by stable
-// rank, consecutive cuts bound a chunk with at most T elements of X and at
-// most T of Y, split exactly; a CTA merges the chunk's four pieces in shared
-// memory (A+B and C+D, then X+Y) and stores it.
+// A quad is four adjacent lists L0..L3 (A, B, C, D, in stable order) that
+// merge into X = merge(A, B), Y = merge(C, D), then merge(X, Y); ties go to
+// the earlier list, so the output is the stable four-way merge, ordered by
+// (key, list, position).
+//
+// Tiles with exact co-ranks.  The key index holds the keys at the global
+// positions 64 e of the round's input, so list j's index entries I_j are the
+// keys at its local positions o_j + 64 k (o_j < 64), and a quad's entries are
+// contiguous.  A small pairwise round over the index merges I_0 with I_1 into
+// X' and I_2 with I_3 into Y'; merging X' and Y' would order every index
+// sample of the quad by (key, list, position).  A tile boundary sits just
+// before the sample s at every Q-th position q of that order.  Let kappa_j be
+// the number of list-j samples before s and v its key: the boundary's co-rank
+// in s's own list is s's position o + 64 kappa, in an earlier list the number
+// of keys <= v, in a later one the number of keys < v.  The samples fix each
+// of those to a window of at most 64 positions, (o_j + 64 kappa_j - 64,
+// o_j + 64 kappa_j], finished by a short bisection of the keys.  Summing over
+// the lists, a boundary's output rank lies in [sum_j o_j + 64 q - 189,
+// sum_j o_j + 64 q], so a tile between two boundaries Q samples apart holds
+// 64 Q - 189 to 64 Q + 189 outputs, and the first and last tiles of a quad at
+// most 64 Q + 252 (tests/test_corank4.py checks all of it by brute force).
 // ---------------------------------------------------------------------------
 
-struct Quad {                 // four lists in stable order -> [out, out + sum n)
-  uint64_t s[4];              // first element of each list
+struct Quad {                 // four adjacent lists in stable order -> [out, out + sum n)
+  uint64_t s[4];              // first element of each list (global position in the round's input)
   uint64_t n[4];              // list lengths
   uint64_t out;
 };
 
-struct Cut4 {                 // a chunk boundary: its stable rank in the quad, the four list positions
-  uint64_t rank;
+// A tile boundary: the four lists' first positions (global) and the output
+// position they start at, and the quad they belong to.
+struct Split4 {
   uint64_t p[4];
+  uint64_t out;
   uint64_t quad;
 };
 
-__device__ __forceinline__ uint64_t quad_cuts(const Quad& q, uint32_t T) {
-  const uint64_t nx = q.n[0] + q.n[1], ny = q.n[2] + q.n[3];
-  if (nx + ny == 0) return 0;
-  const uint64_t cx = nx ? (nx + T - 1) / T - 1 : 0;
-  const uint64_t cy = ny ? (ny + T - 1) / T - 1 : 0;
-  return 1 + cx + cy;                                   // the start, X cuts, Y cuts
-}
+// The largest tile the boundaries can make for Q samples per tile: 64 Q + 4 x 63.
+constexpr uint32_t merge4_max_tile(uint32_t Q) { return 64u * Q + 4u * 63u; }
 
-__device__ __forceinline__ void put_quad(Quad* quads, uint64_t* ccount, uint64_t p, const uint64_t b[5],
-                                         uint64_t out, uint32_t T) {
+__device__ __forceinline__ uint64_t idx_entry(uint64_t pos) { return (pos + kIdxStride - 1) / kIdxStride; }
+
+// Describes quad p (lists [b[i], b[i+1]), output at b[0]) for the round: the
+// quad, its tile count ceil(M / Q) for its M index samples (0 for an empty
+// quad, 1 for a non-empty quad with no sample), and the two pairs of the
+// index-sample merge, slots 2p (I_0 + I_1 -> X') and 2p + 1 (I_2 + I_3 -> Y'),
+// in index-entry coordinates, with their tile counts at merge tile `mtile`.
+__device__ __forceinline__ void put_quad4(Quad* quads, uint64_t* tcount4, Pair* spairs, uint64_t* stcount,
+                                          uint64_t p, const uint64_t b[5], uint32_t Q, uint32_t mtile) {
   Quad q;
+  uint64_t E[5];
+  for (int i = 0; i < 5; ++i) E[i] = idx_entry(b[i]);
   for (int i = 0; i < 4; ++i) {
     q.s[i] = b[i];
     q.n[i] = b[i + 1] - b[i];
   }
-  q.out = out;
+  q.out = b[0];
   quads[p] = q;
-  ccount[p] = quad_cuts(q, T);
+  const uint64_t M = E[4] - E[0];
+  tcount4[p] = b[4] == b[0] ? 0 : (M == 0 ? 1 : (M + Q - 1) / Q);
+  spairs[2 * p] = Pair{E[0], E[1] - E[0], E[1], E[2] - E[1], E[0]};
+  spairs[2 * p + 1] = Pair{E[2], E[3] - E[2], E[3], E[4] - E[3], E[2]};
+  stcount[2 * p] = (E[2] - E[0] + mtile - 1) / mtile;
+  stcount[2 * p + 1] = (E[4] - E[2] + mtile - 1) / mtile;
 }
 
 // Run formation: blocks [j 4w + i w, j 4w + (i+1) w) of every run, i = 0..3.
-static __global__ void k_quads_runs(Quad* quads, uint64_t* ccount, const uint64_t* __restrict__ run_off, uint32_t R,
-                                    uint64_t w, uint64_t cmax, uint32_t T) {
+static __global__ void k_quads4_runs(Quad* quads, uint64_t* tcount4, Pair* spairs, uint64_t* stcount,
+                                     const uint64_t* __restrict__ run_off, uint32_t R, uint64_t w, uint64_t cmax,
+                                     uint32_t Q, uint32_t mtile) {
   uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (p >= (uint64_t)R * cmax) return;
   const uint64_t r = p / cmax, j = p % cmax;
   const uint64_t rs = run_off[r], re = run_off[r + 1];
   uint64_t b[5];
   for (int i = 0; i < 5; ++i) b[i] = umin(rs + j * 4 * w + i * w, re);
-  put_quad(quads, ccount, p, b, b[0], T);
+  put_quad4(quads, tcount4, spairs, stcount, p, b, Q, mtile);
 }
 
 // Bucket merge: groups of `step` segments; group g of a bucket starts at
-// segment 4 g step (slot = global segment index; other slots empty).
-static __global__ void k_quads_buckets(Quad* quads, uint64_t* ccount, Geo g, const uint64_t* __restrict__ off,
-                                       uint64_t q0, uint64_t Q, uint32_t step, uint32_t T) {
+// segment 4 g step (slot = global segment index q0 + t; other slots empty).
+static __global__ void k_quads4_buckets(Quad* quads, uint64_t* tcount4, Pair* spairs, uint64_t* stcount, Geo g,
+                                        const uint64_t* __restrict__ off, uint64_t q0, uint64_t Qg, uint32_t step,
+                                        uint32_t Q, uint32_t mtile) {
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t >= Q) return;
+  if (t >= Qg) return;
   const uint64_t q = q0 + t;
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
   const uint64_t P = g.P[i];
@@ -723,270 +797,300 @@ static __global__ void k_quads_buckets(Quad* quads, uint64_t* ccount, Geo g, con
   } else {
     for (int k = 0; k < 5; ++k) b[k] = off[base + umin(j + (uint64_t)k * step, P)];
   }
-  put_quad(quads, ccount, t, b, b[0], T);
+  put_quad4(quads, tcount4, spairs, stcount, t, b, Q, mtile);
 }
 
+// One thread per tile: the tile's first boundary.  Tile j of a quad starts
+// just before the sample at position j Q of the quad's sample order (j = 0:
+// the quad's start).  kidx: the index of the round's input; xs: X' and Y' at
+// the quad's index entries [E_0, E_2) and [E_2, E_4).
 template <typename K>
-__device__ __forceinline__ uint64_t lower_bound_g(const K* x, uint64_t n, K v) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] < v) lo = mid + 1; else hi = mid; }
-  return lo;
-}
-template <typename K>
-__device__ __forceinline__ uint64_t upper_bound_g(const K* x, uint64_t n, K v) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] <= v) lo = mid + 1; else hi = mid; }
-  return lo;
-}
-
-// One thread per cut (unsorted): local index 0 is the quad start, 1..cx the
-// X cuts at X positions T, 2T, ..., then the Y cuts.
-template <typename K>
-__global__ void k_cuts4(const K* __restrict__ src, const Quad* __restrict__ quads, const uint64_t* __restrict__ coff,
-                        uint64_t nquads, Cut4* cuts, uint32_t T, const uint32_t* err) {
+__global__ void k_corank4(const K* __restrict__ src, const K* __restrict__ kidx, const K* __restrict__ xs,
+                          const Quad* __restrict__ quads, const uint64_t* __restrict__ tbegin4, uint64_t nquads,
+                          Split4* splits, uint64_t cap, uint32_t Q, uint32_t* err) {
   if (poisoned(err)) return;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t >= coff[nquads]) return;
-  const uint64_t qi = last_le<uint64_t>(coff, (uint32_t)nquads, t);
+  const uint64_t total = tbegin4[nquads];
+  if (t == 0 && total > cap) atomicOr(err, kErrBadTile);   // more tiles than the grid and buffer hold
+  if (t >= total || t >= cap) return;
+  const uint64_t guess = (uint64_t)(((unsigned __int128)t * nquads) / total);
+  const uint64_t qi = last_le_from(tbegin4, nquads, t, guess);
   const Quad q = quads[qi];
-  const uint64_t l = t - coff[qi];
-  const uint64_t nx = q.n[0] + q.n[1];
-  const uint64_t cx = nx ? (nx + T - 1) / T - 1 : 0;
-  const K* A = src + q.s[0];
-  const K* B = src + q.s[1];
-  const K* C = src + q.s[2];
-  const K* D = src + q.s[3];
-  Cut4 c;
-  c.quad = qi;
-  if (l == 0) {
-    c.rank = 0;
-    c.p[0] = c.p[1] = c.p[2] = c.p[3] = 0;
-  } else if (l <= cx) {
-    const uint64_t m = l * T;
-    const uint64_t a = merge_path<K, uint64_t>(A, q.n[0], B, q.n[1], m);
-    const uint64_t b = m - a;
-    const bool from_a = a < q.n[0] && (b >= q.n[1] || A[a] <= B[b]);
-    const K v = from_a ? A[a] : B[b];
-    c.p[0] = a;
-    c.p[1] = b;
-    c.p[2] = lower_bound_g<K>(C, q.n[2], v);
-    c.p[3] = lower_bound_g<K>(D, q.n[3], v);
-    c.rank = m + c.p[2] + c.p[3];
-  } else {
-    const uint64_t m = (l - cx) * T;
-    const uint64_t cc = merge_path<K, uint64_t>(C, q.n[2], D, q.n[3], m);
-    const uint64_t d = m - cc;
-    const bool from_c = cc < q.n[2] && (d >= q.n[3] || C[cc] <= D[d]);
-    const K v = from_c ? C[cc] : D[d];
-    c.p[2] = cc;
-    c.p[3] = d;
-    c.p[0] = upper_bound_g<K>(A, q.n[0], v);
-    c.p[1] = upper_bound_g<K>(B, q.n[1], v);
-    c.rank = m + c.p[0] + c.p[1];
+  const uint64_t j = t - tbegin4[qi];
+  Split4 sp;
+  sp.quad = qi;
+  uint64_t c[4] = {0, 0, 0, 0};
+  if (j > 0) {
+    uint64_t E[5], m[4], o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) E[i] = idx_entry(q.s[i]);
+    E[4] = idx_entry(q.s[3] + q.n[3]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      m[i] = E[i + 1] - E[i];
+      o[i] = E[i] * kIdxStride - q.s[i];
+    }
+    const uint64_t qpos = j * (uint64_t)Q;                 // < E[4] - E[0] by the tile count
+    const K* X = xs + E[0];
+    const K* Y = xs + E[2];
+    const uint64_t nx = E[2] - E[0], ny = E[4] - E[2];
+    const uint64_t x = merge_path<K, uint64_t>(X, nx, Y, ny, qpos);
+    const uint64_t y = qpos - x;
+    const K* I0 = kidx + E[0];
+    const K* I1 = kidx + E[1];
+    const K* I2 = kidx + E[2];
+    const K* I3 = kidx + E[3];
+    const uint64_t a = merge_path<K, uint64_t>(I0, m[0], I1, m[1], x);
+    const uint64_t cc = merge_path<K, uint64_t>(I2, m[2], I3, m[3], y);
+    const uint64_t kap[4] = {a, x - a, cc, y - cc};
+    // The sample at position qpos: X'[x] or Y'[y], and the list it came from.
+    const bool from_x = x < nx && (y >= ny || X[x] <= Y[y]);
+    int own;
+    K v;
+    if (from_x) {
+      v = X[x];
+      own = (a < m[0] && (x - a >= m[1] || I0[a] <= I1[x - a])) ? 0 : 1;
+    } else {
+      v = Y[y];
+      own = (cc < m[2] && (y - cc >= m[3] || I2[cc] <= I3[y - cc])) ? 2 : 3;
+    }
+    // Co-ranks: exact in s's own list; a bisection of a window of <= 64 keys
+    // in the others (all three in lockstep, so their loads overlap).
+    uint64_t lo[4], hi[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (i == own) {
+        lo[i] = hi[i] = o[i] + kIdxStride * kap[i];
+      } else {
+        lo[i] = kap[i] ? o[i] + kIdxStride * (kap[i] - 1) + 1 : 0;
+        hi[i] = kap[i] < m[i] ? o[i] + kIdxStride * kap[i] : q.n[i];
+      }
+    }
+#pragma unroll 1
+    for (int it = 0; it < 7; ++it) {                       // windows of <= 64 keys: 7 halvings end them
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (lo[i] < hi[i]) {
+          const uint64_t mid = (lo[i] + hi[i]) >> 1;
+          const K kv = src[q.s[i] + mid];
+          const bool before = i < own ? (kv <= v) : (kv < v);
+          if (before) lo[i] = mid + 1; else hi[i] = mid;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = lo[i];
   }
-  cuts[t] = c;
-}
-
-// Sort the cuts of every quad by rank: X cuts and Y cuts are each in rank
-// order already, so a cut's place is its own index plus the number of the
-// other side's cuts of smaller rank (ranks are distinct: they are the stable
-// ranks of distinct elements).
-static __global__ void k_cuts4_sort(const Cut4* __restrict__ in, const Quad* __restrict__ quads,
-                                    const uint64_t* __restrict__ coff, uint64_t nquads, Cut4* out, uint32_t T,
-                                    const uint32_t* err) {
-  if (poisoned(err)) return;
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t >= coff[nquads]) return;
-  const Cut4 c = in[t];
-  const uint64_t qi = c.quad;
-  const uint64_t base = coff[qi];
-  const uint64_t l = t - base;
-  if (l == 0) {
-    out[base] = c;
-    return;
-  }
-  const Quad q = quads[qi];
-  const uint64_t nx = q.n[0] + q.n[1];
-  const uint64_t cx = nx ? (nx + T - 1) / T - 1 : 0;
-  const uint64_t ncut = coff[qi + 1] - base;
-  const uint64_t cy = ncut - 1 - cx;
-  // Other side: X cuts at [base+1, base+1+cx), Y cuts at [base+1+cx, base+ncut).
-  const bool is_x = l <= cx;
-  const Cut4* other = in + base + 1 + (is_x ? cx : 0);
-  const uint64_t no = is_x ? cy : cx;
-  uint64_t lo = 0, hi = no;                            // other cuts with rank < c.rank
-  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (other[mid].rank < c.rank) lo = mid + 1; else hi = mid; }
-  const uint64_t own = is_x ? l - 1 : l - 1 - cx;
-  out[base + 1 + own + lo] = c;
-}
-
-struct Chunk4 {               // one chunk of a four-way round: the four source ranges and the output start
-  uint64_t s[4];
-  uint32_t n[4];
-  uint64_t out;
-};
-
-// Chunk t spans sorted cuts t and t+1 (or the quad's end).  A chunk whose
-// pieces would not be ranges of their lists or would not fit max_chunk
-// elements (impossible for sorted lists) is emptied and flagged.
-static __global__ void k_chunks4(const Cut4* __restrict__ cuts, const Quad* __restrict__ quads,
-                                 const uint64_t* __restrict__ coff, uint64_t nquads, Chunk4* chunks,
-                                 uint32_t max_chunk, uint32_t* err) {
-  if (poisoned(err)) return;
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t >= coff[nquads]) return;
-  const Cut4 lo = cuts[t];
-  const Quad q = quads[lo.quad];
-  const bool last = t + 1 >= coff[lo.quad + 1];
-  Chunk4 c;
   uint64_t sum = 0;
-  bool bad = false;
+#pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint64_t hi = last ? q.n[i] : cuts[t + 1].p[i];
-    bad = bad || hi < lo.p[i] || hi > q.n[i];
-    c.s[i] = q.s[i] + lo.p[i];
-    c.n[i] = (uint32_t)(hi - lo.p[i]);
-    sum += hi - lo.p[i];
+    sp.p[i] = q.s[i] + c[i];
+    sum += c[i];
   }
-  if (bad || sum > max_chunk) {
-    atomicOr(err, kErrBadTile);
-    for (int i = 0; i < 4; ++i) { c.s[i] = q.s[i]; c.n[i] = 0; }
-  }
-  c.out = q.out + lo.rank;
-  chunks[t] = c;
+  sp.out = q.out + sum;
+  splits[t] = sp;
 }
 
 template <typename K, bool VALS, int NT, int VT>
 struct Merge4Layout {
-  static constexpr int M = NT * VT;                                   // largest chunk (2 T)
-  static constexpr size_t kin = 16;
-  static constexpr size_t vin = kin + (size_t)M * sizeof(K) + 128;
-  static constexpr size_t kmid = vin + (VALS ? (size_t)M * 4 + 128 : 0);
-  static constexpr size_t vmid = kmid + (size_t)M * sizeof(K);
-  static constexpr size_t bytes = vmid + (VALS ? (size_t)M * 4 : 0);
-  static_assert(M % 4 == 0, "16-byte aligned staging");
+  static constexpr int C = NT * VT;                                   // outputs per tile at most
+  static constexpr size_t kin = 16;                                   // after the mbarrier
+  // Four pieces, each widened by up to 15 bytes on either side, plus the key
+  // one slot past the last piece that a serial merge may read.
+  static constexpr size_t vin = kin + (size_t)C * sizeof(K) + 4 * 32 + 16;
+  static constexpr size_t bytes = vin + (VALS ? (size_t)C * 4 + 4 * 32 + 16 : 0);
+  static_assert(C % 4 == 0, "16-byte aligned staging");
 };
 
-// Merge VT outputs of merge(a[0..na), b[0..nb)) starting at output `diag` into
-// out[diag..]; payloads follow their keys (source payload arrays va, vb).
-template <typename K, bool VALS, int VT>
-__device__ __forceinline__ void merge_into(const K* a, const uint32_t* va, int na, const K* b, const uint32_t* vb,
-                                           int nb, int diag, int count, K* out, uint32_t* vout, int f32_out) {
-  if (count <= 0) return;
-  int ai = merge_path<K, int>(a, na, b, nb, diag);
-  int bi = diag - ai;
-  K ak = ai < na ? a[ai] : key_max<K>();
-  K bk = bi < nb ? b[bi] : key_max<K>();
-#pragma unroll
-  for (int j = 0; j < VT; ++j) {
-    if (j < count) {
-      const bool take_a = (bi >= nb) || (ai < na && ak <= bk);
-      out[diag + j] = from_order<K>(take_a ? ak : bk, f32_out);
-      if (VALS) vout[diag + j] = take_a ? va[ai] : vb[bi];
-      if (take_a) {
-        ++ai;
-        ak = ai < na ? a[ai] : key_max<K>();
-      } else {
-        ++bi;
-        bk = bi < nb ? b[bi] : key_max<K>();
-      }
-    }
-  }
-}
+// One CTA per tile of a four-way round: the tile's four pieces arrive by bulk
+// copy; every thread merges VT outputs of [X | Y] (level 1: A with B, C with
+// D) into registers, the CTA writes X and Y compactly over its input staging,
+// every thread merges VT outputs of merge(X, Y) (level 2), and the tile is
+// staged once more in place and leaves with 16-byte stores.  A thread whose
+// level-1 outputs straddle the end of X switches from the (A, B) merge to the
+// (C, D) merge in mid-loop.
+// CTAs per SM the four-way tile is compiled for: with 8-byte keys and
+// payloads the compiler's 93 registers would hold it to 5.
+template <typename K, bool VALS>
+constexpr int merge4_min_blocks() { return PGS_MERGE4_MIN_BLOCKS; }
 
 template <typename K, bool VALS, int NT, int VT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, (merge4_min_blocks<K, VALS>()))
 k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
-         uint32_t* __restrict__ vdst, const Chunk4* __restrict__ chunks, const uint64_t* __restrict__ total,
-         int f32_out, uint32_t* err, K* __restrict__ kidx, uint64_t wait_ns) {
+         uint32_t* __restrict__ vdst, const Split4* __restrict__ splits, const Quad* __restrict__ quads,
+         const uint64_t* __restrict__ total_ptr, uint64_t cap, int f32_out, uint32_t* err, K* __restrict__ kidx,
+         uint64_t wait_ns, int inject_timeout) {
   using L = Merge4Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  char* s_kin = reinterpret_cast<char*>(smem_raw + L::kin);
-  char* s_vin = reinterpret_cast<char*>(smem_raw + L::vin);
-  K* s_kmid = reinterpret_cast<K*>(smem_raw + L::kmid);
-  uint32_t* s_vmid = reinterpret_cast<uint32_t*>(smem_raw + L::vmid);
-  __shared__ uint64_t s_lo[4], s_cnt[4], s_out;
-  __shared__ uint32_t s_off_k[4], s_off_v[4];
-  const uint64_t t = blockIdx.x;
+  K* sk = reinterpret_cast<K*>(smem_raw + L::kin);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(smem_raw + L::vin);
+  __shared__ int s_n[4], s_ko[4], s_vo[4];                // piece lengths; element offsets in sk and sv
+  __shared__ uint64_t s_out;
+  const uint64_t tile = blockIdx.x;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    if (t < *total && !poisoned(err)) {
-      const Chunk4 ch = chunks[t];
-      uint32_t kbytes = 0, vbytes = 0;
-      Span16 ks[4], vs[4];
-      for (int i = 0; i < 4; ++i) {
-        s_lo[i] = ch.s[i];
-        s_cnt[i] = ch.n[i];
-        ks[i] = widen16(ksrc + s_lo[i], (uint32_t)s_cnt[i]);
-        s_off_k[i] = kbytes + ks[i].skip * (uint32_t)sizeof(K);
-        kbytes += ks[i].bytes;
-        if (VALS) {
-          vs[i] = widen16(vsrc + s_lo[i], (uint32_t)s_cnt[i]);
-          s_off_v[i] = vbytes + vs[i].skip * 4u;
-          vbytes += vs[i].bytes;
-        }
+    const uint64_t total = umin(*total_ptr, cap);
+    int n[4] = {0, 0, 0, 0};
+    uint64_t p0[4] = {0, 0, 0, 0};
+    if (tile < total && !poisoned(err)) {
+      const Split4 lo = splits[tile];
+      uint64_t p1[4];
+      if (tile + 1 < total && splits[tile + 1].quad == lo.quad) {
+        const Split4 hi = splits[tile + 1];
+        for (int i = 0; i < 4; ++i) p1[i] = hi.p[i];
+      } else {
+        const Quad q = quads[lo.quad];
+        for (int i = 0; i < 4; ++i) p1[i] = q.s[i] + q.n[i];
       }
-      s_out = ch.out;
+      uint64_t sum = 0;
+      bool bad = false;
+      for (int i = 0; i < 4; ++i) {
+        bad = bad || p1[i] < lo.p[i];
+        sum += p1[i] - lo.p[i];
+      }
+      if (bad || sum > (uint64_t)L::C) {
+        atomicOr(err, kErrBadTile);                     // inconsistent boundaries: skip, never copy
+      } else {
+        for (int i = 0; i < 4; ++i) {
+          p0[i] = lo.p[i];
+          n[i] = (int)(p1[i] - lo.p[i]);
+        }
+        s_out = lo.out;
+      }
+    }
+    uint32_t kbytes = 0, vbytes = 0;
+    Span16 ks[4], vs[4];
+    for (int i = 0; i < 4; ++i) {
+      ks[i] = widen16(ksrc + p0[i], (uint32_t)n[i]);
+      s_ko[i] = (int)((kbytes / sizeof(K)) + ks[i].skip);
+      kbytes += ks[i].bytes;
+      if (VALS) {
+        vs[i] = widen16(vsrc + p0[i], (uint32_t)n[i]);
+        s_vo[i] = (int)(vbytes / 4 + vs[i].skip);
+        vbytes += vs[i].bytes;
+      }
+      s_n[i] = n[i];
+    }
+    if (n[0] + n[1] + n[2] + n[3] > 0) {
       mbar_init(bar, 1);
       fence_barrier_init();
       mbar_arrive_expect_tx(bar, kbytes + vbytes);
-      uint32_t ko = 0, vo = 0;
-      for (int i = 0; i < 4; ++i) {
-        if (ks[i].bytes) bulk_load(s_kin + ko, ks[i].base, ks[i].bytes, bar);
-        ko += ks[i].bytes;
-        if (VALS) {
-          if (vs[i].bytes) bulk_load(s_vin + vo, vs[i].base, vs[i].bytes, bar);
-          vo += vs[i].bytes;
+      // Fault injection (testing only): tile 0 announces its bytes but issues
+      // no copy, so nothing is in flight and its wait runs out.
+      if (!(inject_timeout && tile == 0)) {
+        uint32_t ko = 0, vo = 0;
+        for (int i = 0; i < 4; ++i) {
+          if (ks[i].bytes) bulk_load(reinterpret_cast<char*>(sk) + ko, ks[i].base, ks[i].bytes, bar);
+          ko += ks[i].bytes;
+          if (VALS) {
+            if (vs[i].bytes) bulk_load(reinterpret_cast<char*>(sv) + vo, vs[i].base, vs[i].bytes, bar);
+            vo += vs[i].bytes;
+          }
         }
       }
-    } else {
-      for (int i = 0; i < 4; ++i) s_cnt[i] = 0;
     }
   }
   __syncthreads();
-  const int na = (int)s_cnt[0], nb = (int)s_cnt[1], nc = (int)s_cnt[2], nd = (int)s_cnt[3];
-  const int nx = na + nb, ny = nc + nd, cnt = nx + ny;
-  if (cnt == 0) return;
-  if (!mbar_wait(bar, 0, wait_ns)) {
+  const int na = s_n[0], nb = s_n[1], nc = s_n[2], nd = s_n[3];
+  const int nx = na + nb, cnt = nx + nc + nd;
+  if (cnt == 0) return;                                 // tile beyond the round's total, or skipped
+  if (!mbar_wait(bar, 0, wait_ns)) {                    // gave up: flag it, let copies in flight land, leave
     if (tid == 0) atomicOr(err, kErrWaitTimeout);
     mbar_wait(bar, 0, wait_ns);
     return;
   }
-  const K* A = reinterpret_cast<const K*>(s_kin + s_off_k[0]);
-  const K* B = reinterpret_cast<const K*>(s_kin + s_off_k[1]);
-  const K* C = reinterpret_cast<const K*>(s_kin + s_off_k[2]);
-  const K* D = reinterpret_cast<const K*>(s_kin + s_off_k[3]);
-  const uint32_t* vA = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[0]) : nullptr;
-  const uint32_t* vB = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[1]) : nullptr;
-  const uint32_t* vC = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[2]) : nullptr;
-  const uint32_t* vD = VALS ? reinterpret_cast<const uint32_t*>(s_vin + s_off_v[3]) : nullptr;
-  // Every thread takes an equal share of the chunk (odd, so blocked staging
-  // writes stay conflict free), whatever the chunk's size.
-  const int per = ((cnt + NT - 1) / NT) | 1;
-  // Level 1: X = merge(A, B) into mid[0, nx), Y = merge(C, D) into mid[nx, cnt).
+  const int d0 = min(tid * VT, cnt);
+  const int mine = min(VT, cnt - d0);
+  K ok[VT];
+  uint32_t ov[VT];
+  // Level 1: outputs [d0, d0 + mine) of [X | Y].  The merge state indexes the
+  // staged keys; dva / dvb map a key slot of the current A / B piece to its
+  // payload slot.  A read one slot past a piece lands in the next piece or the
+  // slack after the last one; the index tests decide, never that key.
   {
-    const int d0 = min(tid * per, cnt), d1 = min(d0 + per, cnt);
-    if (d0 < nx) merge_into<K, VALS, VT>(A, vA, na, B, vB, nb, d0, min(d1, nx) - d0, s_kmid, s_vmid, 0);
-    if (d1 > nx) {
-      const int y0 = max(d0, nx) - nx;
-      merge_into<K, VALS, VT>(C, vC, nc, D, vD, nd, y0, d1 - max(d0, nx), s_kmid + nx,
-                              VALS ? s_vmid + nx : nullptr, 0);
+    const int cx = max(0, min(mine, nx - d0));          // outputs taken from X
+    int ai, a_end, bi, b_end, dva, dvb;
+    auto start = [&](int pa, int la, int pb, int lb, int diag, int via, int vib) {
+      const int s = merge_path<K, int>(sk + pa, la, sk + pb, lb, diag);
+      ai = pa + s;
+      a_end = pa + la;
+      bi = pb + (diag - s);
+      b_end = pb + lb;
+      dva = via - pa;
+      dvb = vib - pb;
+    };
+    if (cx > 0) start(s_ko[0], na, s_ko[1], nb, d0, s_vo[0], s_vo[1]);
+    else start(s_ko[2], nc, s_ko[3], nd, d0 - nx, s_vo[2], s_vo[3]);
+    K ak = sk[ai];
+    K bk = sk[bi];
+#pragma unroll
+    for (int j = 0; j < VT; ++j) {
+      if (j < mine) {
+        if (j == cx && j > 0) {                         // this thread's outputs cross from X into Y
+          start(s_ko[2], nc, s_ko[3], nd, 0, s_vo[2], s_vo[3]);
+          ak = sk[ai];
+          bk = sk[bi];
+        }
+        const bool take_b = (bi < b_end) && ((ai >= a_end) || (bk < ak));
+        ok[j] = take_b ? bk : ak;
+        if (VALS) ov[j] = sv[take_b ? bi + dvb : ai + dva];
+        if (take_b) ++bi; else ++ai;
+        const K nx_key = sk[take_b ? bi : ai];
+        if (take_b) bk = nx_key; else ak = nx_key;
+      }
+    }
+  }
+  __syncthreads();                                      // every thread is done reading the pieces
+#pragma unroll
+  for (int j = 0; j < VT; ++j) {
+    if (j < mine) {
+      sk[d0 + j] = ok[j];
+      if (VALS) sv[d0 + j] = ov[j];
     }
   }
   __syncthreads();
-  // Level 2: merge(X, Y) into the (now free) input staging.
-  K* s_kout = reinterpret_cast<K*>(s_kin);
-  uint32_t* s_vout = reinterpret_cast<uint32_t*>(s_vin);
+  // Level 2: outputs [d0, d0 + mine) of merge(X, Y); X = sk[0, nx), Y = sk[nx, cnt).
   {
-    const int d0 = min(tid * per, cnt);
-    merge_into<K, VALS, VT>(s_kmid, s_vmid, nx, s_kmid + nx, VALS ? s_vmid + nx : nullptr, ny, d0,
-                            min(per, cnt - d0), s_kout, s_vout, f32_out);
+    const int s = merge_path<K, int>(sk, nx, sk + nx, cnt - nx, d0);
+    int ai = s, bi = nx + (d0 - s);
+    K ak = sk[ai];
+    K bk = sk[bi];
+#pragma unroll
+    for (int j = 0; j < VT; ++j) {
+      if (j < mine) {
+        const bool take_b = (bi < cnt) && ((ai >= nx) || (bk < ak));
+        ok[j] = take_b ? bk : ak;
+        if (VALS) ov[j] = sv[take_b ? bi : ai];
+        if (take_b) ++bi; else ++ai;
+        const K nx_key = sk[take_b ? bi : ai];
+        if (take_b) bk = nx_key; else ak = nx_key;
+      }
+    }
   }
   __syncthreads();
-  store_tile_vec<K, NT>(kdst + s_out, s_kout, cnt);
-  if (VALS) store_tile_vec<uint32_t, NT>(vdst + s_out, s_vout, cnt);
-  if (kidx) write_key_index(kidx, s_kout, s_out, cnt);
+  K* ko = sk + stage_pad(kdst + s_out);                 // staging shifted for the bulk store
+  uint32_t* vo = VALS ? sv + stage_pad(vdst + s_out) : nullptr;
+#pragma unroll
+  for (int j = 0; j < VT; ++j) {
+    if (j < mine) {
+      ko[d0 + j] = from_order<K>(ok[j], f32_out);
+      if (VALS) vo[d0 + j] = ov[j];
+    }
+  }
+  static_assert(VT < kIdxStride, "at most one index entry per thread");
+  if (kidx) {
+    const int j0 = (int)((0u - (uint32_t)s_out - (uint32_t)d0) & (uint32_t)(kIdxStride - 1));
+    if (j0 < mine) kidx[(s_out + (uint64_t)(d0 + j0)) / kIdxStride] = ko[d0 + j0];   // no index on the last pass
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  store_tile_bulk<K, NT>(kdst + s_out, ko, cnt);
+  if (VALS) store_tile_bulk<uint32_t, NT>(vdst + s_out, vo, cnt);
+  if (tid == 0) {
+    bulk_commit();
+    bulk_wait_read();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1330,7 +1434,8 @@ template <typename K, bool VALS>
 __global__ void __launch_bounds__(kScatterNT)
 k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
           uint32_t* __restrict__ vdst, const uint64_t* __restrict__ off, const uint64_t* __restrict__ seg_src,
-          const uint64_t* __restrict__ first_seg, uint64_t n, uint64_t Q, int f32_out, const uint32_t* err) {
+          const uint64_t* __restrict__ first_seg, uint64_t n, uint64_t Q, int f32_out, const uint32_t* err,
+          K* __restrict__ kidx) {
   if (poisoned(err)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sm = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
@@ -1368,6 +1473,10 @@ k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __re
     if (VALS) sm.vals[p] = vsrc[s];
   }
   __syncthreads();
+  if (kidx) {                                        // order-form keys, before any conversion
+    write_key_index(kidx, sm.keys, o, cnt);
+    __syncthreads();
+  }
   for (int p = threadIdx.x; p < cnt; p += blockDim.x) sm.keys[p] = from_order<K>(sm.keys[p], f32_out);
   __syncthreads();
   store_tile_vec<K, kScatterNT>(kdst + o, sm.keys, cnt);
