@@ -103,7 +103,7 @@ typedef enum { PGS_GRAPH_CACHE_AUTO = 0, PGS_GRAPH_CACHE_OFF = 1 } pgs_graph_cac
 /* Kernels of the pipeline, as reported by the launch timer. */
 typedef enum {
   PGS_KERNEL_BLOCK_SORT = 0,   /* step 1: shared-memory block sort of one tile */
-  PGS_KERNEL_MERGE = 1,        /* steps 1, 3, 6: merge-path merge of one round */
+  PGS_KERNEL_MERGE = 1,        /* steps 1, 3, 6: pairwise merge-path merge of one round */
   PGS_KERNEL_PARTITION = 2,    /* merge-path splits of one round */
   PGS_KERNEL_PAIRS = 3,        /* pair descriptors of one round */
   PGS_KERNEL_SCAN = 4,         /* device-wide exclusive scan */
@@ -114,7 +114,8 @@ typedef enum {
   PGS_KERNEL_OFFSETS = 9,      /* step 5 set-up: segment sizes and receive offsets */
   PGS_KERNEL_SCATTER = 10,     /* step 5: the exchange */
   PGS_KERNEL_STATS = 11,       /* load statistics */
-  PGS_KERNEL_COUNT = 12
+  PGS_KERNEL_MERGE4 = 12,      /* steps 1, 6: four-way merge of one pass (two tree levels) */
+  PGS_KERNEL_COUNT = 13
 } pgs_kernel;
 
 /* One timed launch.  `bytes` are the algorithmic bytes the launch must move

@@ -410,7 +410,7 @@ int pgs_timer_read(pgs_timer* t, pgs_launch_record* out, uint32_t max, uint32_t*
 const char* pgs_kernel_name(uint32_t kernel) {
   static const char* names[PGS_KERNEL_COUNT] = {"block_sort", "merge", "partition", "pairs", "scan",
                                                 "sample", "splitters", "cut_search", "investigator",
-                                                "offsets", "scatter", "stats"};
+                                                "offsets", "scatter", "stats", "merge4"};
   return kernel < PGS_KERNEL_COUNT ? names[kernel] : "unknown";
 }
 

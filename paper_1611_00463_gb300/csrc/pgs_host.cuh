@@ -523,7 +523,7 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
   constexpr size_t smem = Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes;
-  return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
+  return launch(c, PGS_KERNEL_MERGE4, step, bytes, [&] {
     k_merge4<K, V, kMerge4NT, kMerge4VT><<<(unsigned)tiles_ub, kMerge4NT, smem, c.st>>>(
         ks, vs, kd, vd, b.splits4, b.quads, b.tbegin4 + nquads, tiles_ub, f32_out, b.err, idx_out, c.wait_ns, inject);
   });

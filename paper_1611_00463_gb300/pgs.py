@@ -123,7 +123,7 @@ EXPORTS = {
 TILE_VARIANTS = 4
 
 KERNELS = ["block_sort", "merge", "partition", "pairs", "scan", "sample", "splitters", "cut_search",
-           "investigator", "offsets", "scatter", "stats"]
+           "investigator", "offsets", "scatter", "stats", "merge4"]
 
 
 class pgs_launch_record(ctypes.Structure):
