@@ -3,8 +3,10 @@
 `python bench.py --gpus N --steps K --warmup W` sorts the 256M-key workload
 (2^28 uint64 keys, half normal / half right-skewed lognormal, uint32 index
 payload, P = 128 logical partitions) once per step, out of place, with inputs
-resident in HBM, and prints one JSON line.  Under torchrun every rank sorts its
-own instance (weak scaling, no collective on the data path).
+resident in HBM, and prints one JSON line.  Under torchrun (N > 1) the ranks
+sort ONE global array of N x 2^28 keys, shard r on rank r, with the paper's
+distributed steps over NCCL (weak scaling); --replicas makes every rank sort
+its own instance instead.
 
 `--impl reference` times the CPU oracle instead, on a bounded sample of the same
 workload, on the host cores.
@@ -55,6 +57,8 @@ def parse():
                     help="time pgs_search of this many queries on the sorted workload instead")
     ap.add_argument("--sweep-samples", action="store_true",
                     help="time the sort at the paper's sample sizes 0.004X .. 1.4X (X = 256 KB / P) instead")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: every rank sorts its own array (default: one array sharded over the ranks)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-timer", action="store_true", help="skip per-launch events (profiling runs)")
@@ -602,6 +606,72 @@ def library_comparator(kin, vin, kout, vout, dtype, args, dev, world):
         return {"unavailable": str(ex).splitlines()[0][:200]}
 
 
+def run_sharded(args):
+    """--gpus N under torchrun: ONE global array of N x n keys, shard r (n keys,
+    the workload's generator with seed + r) on rank r, sorted by the paper's
+    distributed form (paper_1611_00463_gb300.sharded: local sort, sample and
+    count all-gathers over NCCL, investigator cuts, all-to-all of segments,
+    merge).  Rank b ends with bucket b.  Per-rank work is fixed as N grows
+    (weak scaling); the whole-job rate is N x n keys over the slowest rank."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1611_00463_gb300 import build as pbuild
+    from paper_1611_00463_gb300 import pgs
+    from paper_1611_00463_gb300.sharded import CudaSteps, sharded_sort
+
+    world, rank, local = dist_env()
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        pbuild.build()
+    dist.barrier()
+    pgs.load()
+    dtype, n, P, gen, seed = workload_shape(args)
+    keys_np = gen(n, seed + rank)
+    kin = pgs.as_device_keys(keys_np, dtype, dev)
+    vin = torch.from_numpy((inputs.index_payload(n) + np.uint32((rank * n) & 0xFFFFFFFF)).view(np.int32)).to(dev)
+    opts = dict(exchange=args.exchange, guaranteed=args.guaranteed, merge_ways=args.merge_ways,
+                tile_variant=args.tile_variant, samples_per_run=args.samples_per_run, investigator=args.investigator)
+    steps = CudaSteps(dtype, dev, **opts)
+    for _ in range(max(args.warmup, 0)):
+        out = sharded_sort(kin, vin, dtype=dtype, steps=steps)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        dist.barrier()
+        torch.cuda.synchronize(dev)
+        clocks.mark_start()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            out = sharded_sort(kin, vin, dtype=dtype, steps=steps)
+        torch.cuda.synchronize(dev)
+        dt = (time.perf_counter() - t0) / args.steps
+        clocks.mark_end()
+        dist.barrier()
+    dt = max_over_ranks(dt, dev, world)
+    e = out[2].cpu().numpy()
+    if rank == 0:
+        N = world * n
+        sizes = np.diff(e)
+        line = {
+            "metric": METRIC, "value": whole_job_rate(n, world, dt), "unit": "Gkeys/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": f"{args.workload}: one global array of {world} x {n} {dtype} keys + uint32 "
+                                   f"payload, shard r on rank r (seed + r), sorted across the ranks",
+                       "n_per_rank": n, "N": N, "P": world, "parallelism": f"sharded{world}",
+                       "collectives": "NCCL all-gather (sizes, samples, counts), all-to-all-v (segments)",
+                       "l2": "inputs larger than L2"},
+            "max_over_mean_bucket": float(sizes.max() / (N / world)),
+            "roofline": None, "e2e": None, "cpu_baseline": None,
+            "clocks": clocks.summary(),
+            "timing": "host clock around K steps between barriers and device synchronisation, max over ranks",
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.sweep_samples:
@@ -613,6 +683,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if dist_env()[0] > 1 and not args.replicas:
+        run_sharded(args)
         return
     import torch
     import torch.distributed as dist

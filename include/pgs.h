@@ -339,6 +339,81 @@ size_t pgs_fit_workspace_bytes(uint64_t m, uint32_t P, const pgs_config* cfg);
 int pgs_fit_splitters(const void* samples, uint64_t m, uint32_t P, void* stream,
                       const pgs_config* cfg, void* splitters_out, float* model_out);
 
+/* ---------------------------------------------------------------------------
+ * Sharded sort: one global array spread over G ranks (processes, one GPU
+ * each), sorted by the six steps of Section IV with the ranks as the paper's
+ * processors.  Rank r holds shard r; the global input is the shards in rank
+ * order, so the result is the stable sort of that concatenation and rank b
+ * ends with bucket b, the stable ranks [e_b, e_{b+1}).  The library runs each
+ * rank's steps on its GPU; the caller moves data between the ranks with its
+ * own collectives:
+ *   1. pgs_sort_copy the shard (any P; the result is the sorted shard);
+ *   2. pgs_rank_samples (s = pgs_samples_per_run(G, cfg)); all-gather the
+ *      samples in rank order;
+ *   3. pgs_fit_splitters(all samples, G) -> the G-1 splitters, identical on
+ *      every rank (no broadcast needed);
+ *   4. pgs_rank_counts; all-gather the counts in rank order;
+ *      pgs_rank_cuts -> the cut matrix and bucket bounds, identical on every
+ *      rank (step 4's investigator, Section IV-B);
+ *   5. all-to-all: rank r sends its sorted positions [cut[r][b], cut[r][b+1])
+ *      to rank b, which receives them in rank order (sizes known from the cut
+ *      matrix on every rank: Section IV-C);
+ *   6. pgs_merge_lists of the G received segments -> bucket b.
+ * ------------------------------------------------------------------------- */
+
+/* Regular samples per run (per rank) for P runs: the paper's budget
+ * floor(262144 / (P * key_bytes)), or at least ceil(P / eps) in guaranteed
+ * mode (Section IV-B); 0 for P = 1 or an invalid request.  Host-only. */
+uint64_t pgs_samples_per_run(uint32_t P, const pgs_config* cfg);
+
+/* Step 2 on one rank (Section IV): from the rank's sorted keys (device, n
+ * keys of cfg->dtype) write sr = min(s, n) regular samples, the keys at
+ * positions floor((i+1) n / sr) - 1, to samples_out (device, sr keys).
+ * Asynchronous on stream. */
+int pgs_rank_samples(const void* sorted, uint64_t n, uint32_t s, void* samples_out, void* stream,
+                     const pgs_config* cfg);
+
+/* Step 4's binary searches on one rank (Section IV-B): for each splitter t_b,
+ * b = 1..G-1 (device, G-1 keys, as pgs_fit_splitters writes them), the number
+ * of the rank's sorted keys (device, n keys) ordered before t_b and equal to
+ * it.  counts_out (device, 2 (G-1) uint64): [lb_1..lb_{G-1}, cnt_1..cnt_{G-1}].
+ * Nothing is written for G = 1.  Asynchronous on stream. */
+int pgs_rank_counts(const void* sorted, uint64_t n, const void* splitters, uint32_t G, uint64_t* counts_out,
+                    void* stream, const pgs_config* cfg);
+
+/* Device workspace of pgs_rank_cuts for G ranks (0 for an invalid request). */
+size_t pgs_rank_cuts_workspace_bytes(uint32_t G, const pgs_config* cfg);
+
+/* Step 4's investigator over all ranks (Section IV-B, Fig. 5), the same on
+ * every rank: counts_all (device, G rows of 2 (G-1) uint64 in rank order, each
+ * as pgs_rank_counts writes it), shard_sizes (HOST, G uint64), the splitters
+ * (device, G-1 keys).  Writes cut_out (device, G x (G+1) uint64, row r: rank
+ * r sends its sorted positions [cut[r][b], cut[r][b+1]) to rank b) and
+ * bounds_out (device, G+1 uint64: bucket b = global stable ranks [e_b,
+ * e_{b+1})), with cfg->investigator's rule on global stable ranks (the target
+ * floor(b N / G), N = sum of the shard sizes).  Needs cfg->workspace of
+ * pgs_rank_cuts_workspace_bytes(G, cfg).  Synchronises stream (the shard
+ * sizes are uploaded from the host). */
+int pgs_rank_cuts(const uint64_t* counts_all, const uint64_t* shard_sizes, uint32_t G, const void* splitters,
+                  uint64_t* cut_out, uint64_t* bounds_out, void* stream, const pgs_config* cfg);
+
+/* Device workspace of pgs_merge_lists for n keys in k lists (0: invalid). */
+size_t pgs_merge_workspace_bytes(uint64_t n, uint32_t k, const pgs_config* cfg);
+
+/* Step 6 on one rank (Section IV-C: the receiver merges what it received with
+ * the balanced merge of Fig. 2): the stable merge of k sorted lists that lie
+ * one after another in keys_in (list j = [offsets[j], offsets[j+1]); offsets
+ * HOST, k+1 uint64, offsets[0] = 0, non-decreasing), earlier lists first on
+ * equal keys, into keys_out (and vals_in into vals_out; both NULL or both
+ * set).  Inputs are only read; inputs and outputs must not overlap.  Four-way
+ * passes while two tree levels remain (cfg->merge_ways), else pairwise.
+ * Needs cfg->workspace of pgs_merge_workspace_bytes(n, k, cfg); cfg->stats
+ * (optional) receives the passes, launches and device error word.
+ * Synchronises stream once (the offsets are uploaded), then runs
+ * asynchronously. */
+int pgs_merge_lists(const void* keys_in, const uint32_t* vals_in, const uint64_t* offsets, uint32_t k,
+                    void* keys_out, uint32_t* vals_out, void* stream, const pgs_config* cfg);
+
 /* Bytes of device workspace pgs_search can use for n sorted keys (0: it uses
  * none at this size).  With that much cfg->workspace the search first bisects a
  * compact copy of every 64th key, which stays in L2, then one 64-key block of

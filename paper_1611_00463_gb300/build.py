@@ -15,7 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpgs.so")
 
-SOURCES = ["pgs_api.cu", "pgs_sort_u32.cu", "pgs_sort_u64.cu", "pgs_static.cu", "pgs_batch.cu", "pgs_search.cu"]
+SOURCES = ["pgs_api.cu", "pgs_sort_u32.cu", "pgs_sort_u64.cu", "pgs_static.cu", "pgs_batch.cu", "pgs_search.cu",
+           "pgs_rank.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

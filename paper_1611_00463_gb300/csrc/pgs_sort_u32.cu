@@ -1,5 +1,5 @@
 // 32-bit keys (uint32 and float32 in totalOrder form) of the sort pipeline.
-#include "pgs_host.cuh"
+#include "pgs_rank.cuh"
 
 namespace pgs {
 
@@ -45,6 +45,14 @@ int fill_random_u32(void* keys, uint32_t* vals, uint64_t n, uint64_t seed, cudaS
   k_fill_random<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(static_cast<uint32_t*>(keys), vals, n, seed);
   PGS_CUDA(cudaGetLastError());
   return PGS_OK;
+}
+
+int merge_lists_u32(const Shape& sh, const Options& o, const void* kin, const uint32_t* vin, void* kout,
+                    uint32_t* vout, const uint64_t* off, uint32_t k, cudaStream_t st) {
+  auto ki = static_cast<const uint32_t*>(kin);
+  auto ko = static_cast<uint32_t*>(kout);
+  if (vin) return run_merge_lists<uint32_t, true>(sh, o, ki, vin, ko, vout, off, k, st);
+  return run_merge_lists<uint32_t, false>(sh, o, ki, nullptr, ko, nullptr, off, k, st);
 }
 
 }  // namespace pgs

@@ -1,5 +1,5 @@
 // 64-bit keys of the sort pipeline.
-#include "pgs_host.cuh"
+#include "pgs_rank.cuh"
 
 namespace pgs {
 
@@ -45,6 +45,14 @@ int fill_random_u64(void* keys, uint32_t* vals, uint64_t n, uint64_t seed, cudaS
   k_fill_random<uint64_t><<<grid_for(n, 256), 256, 0, st>>>(static_cast<uint64_t*>(keys), vals, n, seed);
   PGS_CUDA(cudaGetLastError());
   return PGS_OK;
+}
+
+int merge_lists_u64(const Shape& sh, const Options& o, const void* kin, const uint32_t* vin, void* kout,
+                    uint32_t* vout, const uint64_t* off, uint32_t k, cudaStream_t st) {
+  auto ki = static_cast<const uint64_t*>(kin);
+  auto ko = static_cast<uint64_t*>(kout);
+  if (vin) return run_merge_lists<uint64_t, true>(sh, o, ki, vin, ko, vout, off, k, st);
+  return run_merge_lists<uint64_t, false>(sh, o, ki, nullptr, ko, nullptr, off, k, st);
 }
 
 }  // namespace pgs

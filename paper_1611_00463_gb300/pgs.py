@@ -117,6 +117,17 @@ EXPORTS = {
     "pgs_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "pgs_sort_batched_copy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_samples_per_run": (ctypes.c_uint64, [ctypes.c_uint32, ctypes.c_void_p]),
+    "pgs_rank_samples": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_rank_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_rank_cuts_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_void_p]),
+    "pgs_rank_cuts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pgs_merge_workspace_bytes": (ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p]),
+    "pgs_merge_lists": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pgs_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -439,6 +450,61 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Rank steps of the sharded sort (argument marshalling; the driver that runs
+# them with collectives is paper_1611_00463_gb300.sharded).
+# ---------------------------------------------------------------------------
+
+def pgs_samples_per_run(P: int, cfg: pgs_config | None = None) -> int:
+    return load().pgs_samples_per_run(P, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def pgs_rank_samples(sorted_keys: torch.Tensor, s: int, samples_out: torch.Tensor, cfg: pgs_config,
+                     stream=None) -> None:
+    _check(load().pgs_rank_samples(_ptr(sorted_keys), sorted_keys.numel(), s, _ptr(samples_out), _stream(stream),
+                                   ctypes.byref(cfg)), "pgs_rank_samples")
+
+
+def pgs_rank_counts(sorted_keys: torch.Tensor, splitters: torch.Tensor, G: int, counts_out: torch.Tensor,
+                    cfg: pgs_config, stream=None) -> None:
+    _check(load().pgs_rank_counts(_ptr(sorted_keys) if sorted_keys.numel() else None, sorted_keys.numel(),
+                                  _ptr(splitters), G, _ptr(counts_out), _stream(stream), ctypes.byref(cfg)),
+           "pgs_rank_counts")
+
+
+def pgs_rank_cuts_workspace_bytes(G: int, cfg: pgs_config | None = None) -> int:
+    return load().pgs_rank_cuts_workspace_bytes(G, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def pgs_rank_cuts(counts_all: torch.Tensor, shard_sizes, splitters: torch.Tensor, cut_out: torch.Tensor,
+                  bounds_out: torch.Tensor, cfg: pgs_config, stream=None) -> None:
+    """shard_sizes: host sequence of G sizes."""
+    import numpy as np
+    sizes = np.ascontiguousarray(np.asarray(shard_sizes, dtype=np.uint64))
+    G = len(sizes)
+    _check(load().pgs_rank_cuts(_ptr(counts_all) if G > 1 else None, sizes.ctypes.data, G,
+                                _ptr(splitters) if G > 1 else None, _ptr(cut_out), _ptr(bounds_out), _stream(stream),
+                                ctypes.byref(cfg)), "pgs_rank_cuts")
+
+
+def pgs_merge_workspace_bytes(n: int, k: int, cfg: pgs_config | None = None) -> int:
+    return load().pgs_merge_workspace_bytes(n, k, ctypes.byref(cfg) if cfg is not None else None)
+
+
+def pgs_merge_lists(keys_in: torch.Tensor, vals_in: torch.Tensor | None, offsets, keys_out: torch.Tensor,
+                    vals_out: torch.Tensor | None, cfg: pgs_config, stream=None) -> None:
+    """offsets: host sequence of k+1 list offsets into keys_in."""
+    import numpy as np
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+    k = len(off) - 1
+    n = int(off[-1]) if k >= 0 else 0
+    if keys_in.numel() < n or keys_out.numel() < n:
+        raise ValueError("length mismatch")
+    _check(load().pgs_merge_lists(_ptr(keys_in) if n else None, _ptr(vals_in) if n else None, off.ctypes.data, k,
+                                  _ptr(keys_out) if n else None, _ptr(vals_out) if n else None, _stream(stream),
+                                  ctypes.byref(cfg)), "pgs_merge_lists")
 
 
 def pgs_fit_workspace_bytes(m: int, P: int, cfg: pgs_config | None = None) -> int:
