@@ -238,18 +238,52 @@ def time_oracle(workload: str, P: int, sample_n: int, steps: int, warmup: int):
     return sample_n / dt / 1e9, dt, dtype
 
 
+def cpu_parallel_sort_rate(workload: str, n: int, P: int, steps: int, warmup: int):
+    """The oracle's stable sort on every host core (oracle/cpu_sort.c) over the
+    workload's full keys: (Gkeys/s, seconds per sort, threads, dtype)."""
+    from oracle import cpu_sort
+    dtype, keys, _ = inputs.workload(workload, n=n)
+    vals = inputs.index_payload(n)
+    T = cpu_sort.threads_available()
+    for _ in range(warmup):
+        cpu_sort.stable_sort(keys, vals, dtype, T)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        cpu_sort.stable_sort(keys, vals, dtype, T)
+    dt = (time.perf_counter() - t0) / steps
+    return n / dt / 1e9, dt, T, dtype
+
+
+def cpu_baseline_block(args, n, P, steps=1, warmup=0):
+    """cpu_baseline: the full workload on all host cores, with the one-thread
+    numpy oracle on a bounded sample beside it."""
+    from oracle import cpu_sort
+    v, dt, T, dtype = cpu_parallel_sort_rate(args.workload, n, P, steps, warmup)
+    sample_n = min(n, 1 << 24)
+    v1, dt1, _ = time_oracle(args.workload, P, sample_n, 1, 0)
+    return {"value": v, "unit": "Gkeys/s", "cores": T, "threads": T, "kind": "oracle",
+            "cpu_model": cpu_sort.cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"the whole workload ({n} {dtype} keys + uint32 payload): the oracle's stable sort on "
+                      f"(total-order key, input position), C, {T} threads (chunk merge sorts, then pairwise "
+                      f"merges split by merge path over all threads), {dt:.2f} s per sort",
+            "oracle_1thread": {"value": v1, "unit": "Gkeys/s",
+                               "sample": f"first {sample_n} keys: numpy oracle stable sort + steps 1-4 "
+                                         f"bucket vector, one thread, {dt1:.1f} s"}}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
     if args.workload == "batched":
         return run_reference_batched(args)
+    from oracle import cpu_sort
     dtype, n, P, _, _ = workload_shape(args)
-    sample_n = min(n, 1 << 23)
-    value, dt, _ = time_oracle(args.workload, P, sample_n, args.steps, args.warmup)
-    cpu = {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-           "sample": f"first {sample_n} keys of the workload (same generator and seed), P={P}: "
-                     "oracle stable sort + steps 1-4 bucket vector, numpy, one thread"}
+    value, dt, T, _ = cpu_parallel_sort_rate(args.workload, n, P, args.steps, args.warmup)
+    cpu = {"value": value, "unit": "Gkeys/s", "cores": T, "threads": T, "kind": "oracle",
+           "cpu_model": cpu_sort.cpu_model(), "nproc": os.cpu_count(),
+           "sample": f"the whole workload ({n} {dtype} keys + uint32 payload) every step: the oracle's stable "
+                     f"sort, C, {T} threads"}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
@@ -902,11 +936,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample_n = min(n, 1 << 24)
-        v, dt, _ = time_oracle(args.workload, P, sample_n, 1, 0)
-        cpu = {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {sample_n} keys of the workload (same generator), P={P}: oracle stable sort "
-                         f"+ steps 1-4 bucket vector, numpy, one thread, {dt:.1f} s"}
+        cpu = cpu_baseline_block(args, n, P)
 
     if rank == 0:
         line = {
