@@ -77,7 +77,11 @@ typedef enum { PGS_EXCHANGE_AUTO = 0, PGS_EXCHANGE_SCATTER = 1, PGS_EXCHANGE_FUS
 
 /* Splitter source.  SAMPLED: steps 2-3 of Section IV.  LEARNED: an MLP CDF
  * model trained on the same sample predicts bucket ids; the sampled splitters
- * judge it and take over when its imbalance exceeds 1 + eps. */
+ * judge it and take over when its imbalance exceeds 1 + eps.  For P > 64 no
+ * model is trained (about 64 linear pieces cannot place more bucket
+ * boundaries): the sampled cuts stand, stats report fallback = 1 and
+ * learned_over_mean = NaN, and model_out receives an invalid all-zero model;
+ * a caller-given cfg->model is still judged at any P. */
 typedef enum { PGS_SPLITTERS_SAMPLED = 0, PGS_SPLITTERS_LEARNED = 1 } pgs_splitter_mode;
 
 /* How pgs_sort_host copies its output back.  GROUPS (default): the host waits

@@ -538,6 +538,11 @@ int learned_cuts(const Shape& sh, const Options& o, const K* sorted, const K* ru
   cudaStream_t st = c.st;
   const uint32_t P = sh.R;
   const uint64_t S = sh.S;
+  if (!o.model && P > kLearnedMaxP) {                   // beyond the model's capacity: no training
+    return launch(c, PGS_KERNEL_SPLITTERS, 3, 8, [&] {
+      k_learned_skip<<<1, 256, 0, st>>>(b.fallback, b.learned_ratio, o.model_out);
+    });
+  }
   if (o.model) {
     PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 8 * kMlpWords, [&] {
       k_mlp_validate<<<1, 256, 0, st>>>(o.model, b.model);

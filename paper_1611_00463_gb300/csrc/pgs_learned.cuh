@@ -30,6 +30,14 @@ constexpr int kMlpSteps = 300;
 constexpr float kMlpLr = 0.01f;
 constexpr float kMlpOffDiag = -6.0f;
 constexpr int kMlpBatch = 128;              // training samples per CTA (3 CTAs of 72 KB per SM)
+// Largest P the model is trained for.  Its output is piecewise linear with at
+// most 32 layer-1 knots and 32 layer-2 clipping points, about 64 pieces, so it
+// cannot place P - 1 > 64 bucket boundaries within eps of their quantiles for
+// a general CDF (measured: no model passed the judge at P >= 64 on the
+// exponential, normal + lognormal or Zipf keys).  Above it no model is
+// trained, the sampled cuts stand (fallback) and the model's own imbalance is
+// reported as NaN (not evaluated).  A caller-given model is still judged.
+constexpr uint32_t kLearnedMaxP = 64;
 
 __device__ __forceinline__ bool same_half(int k, int j) { return (k < kMlpHalf) == (j < kMlpHalf); }
 
@@ -381,6 +389,17 @@ k_learned_search(const K* __restrict__ runs, const uint64_t* __restrict__ run_of
 // The learned bucket vector e_b = sum_r cut[r][b], and the decision: keep the
 // learned cuts only for a valid model whose largest bucket is at most
 // (1 + eps) n / P.
+// P above kLearnedMaxP: the sampled cuts stand, the model is not evaluated,
+// and a requested model output is an invalid (flag 0) all-zero model.
+static __global__ void k_learned_skip(uint32_t* fallback, float* ratio_out, float* model_out) {
+  if (threadIdx.x == 0) {
+    *fallback = 1u;
+    *ratio_out = __int_as_float(0x7FC00000);
+  }
+  if (model_out)
+    for (int i = threadIdx.x; i < kMlpWords; i += blockDim.x) model_out[i] = 0.0f;
+}
+
 static __global__ void k_learned_colsum(const uint64_t* __restrict__ cutL, uint32_t P, uint64_t* eL) {
   const uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (b > P) return;

@@ -43,7 +43,7 @@ def run_learned(keys, P, dtype, words=None, eps=0.05):
     vin = torch.from_numpy(vals.view(np.int32)).to(dev)
     kout, vout = torch.empty_like(kin), torch.empty_like(vin)
     model = None if words is None else torch.from_numpy(words.view(np.float32)).to(dev)
-    model_out = torch.zeros(pgs.MLP_WORDS, dtype=torch.float32, device=dev)
+    model_out = torch.full((pgs.MLP_WORDS,), 1.0, dtype=torch.float32, device=dev)   # every word is written
     cfg0 = pgs.make_config(dtype=dtype, splitters="learned", eps=eps)
     ws = pgs.workspace(n, P, cfg0, dev)
     bounds = torch.zeros(P + 1, dtype=torch.int64, device=dev)
@@ -174,3 +174,18 @@ def test_fit_splitters_learned_mode():
     x = O.mlp_inputs(srt, kmin, scale).astype(np.float64)
     y, _ = O.mlp_forward64(O.mlp_unpack(w), x)
     assert float(np.mean((y - (np.arange(m) + 0.5) / m) ** 2)) < 1e-3
+
+
+@pytest.mark.parametrize("P", [65, 128, 1024])
+def test_no_training_beyond_the_model_capacity(P):
+    """P > 64: no model is trained; the sampled cuts stand, the stats report
+    the fallback with the model's imbalance not evaluated (NaN), and the model
+    output is an invalid all-zero model.  The sort itself is the oracle's."""
+    n = 1 << 18
+    keys = inputs.exponential_u32(n, 17)
+    got = run_learned(keys, P, "u32")
+    st = got["stats"]
+    assert st["splitter_mode"] == 1 and st["fallback"] == 1 and np.isnan(st["learned_over_mean"])
+    assert reinterpret_words(got["model"])[-1] == 0 and not np.any(got["model"])
+    ref = O.buckets(keys, P, "u32")
+    assert np.array_equal(got["e"], ref["e"])
