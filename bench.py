@@ -343,7 +343,7 @@ def config_block(args, dtype, n, P, stats):
         "n": n, "P": P, "key": dtype, "payload": "u32 index",
         "l2": "inputs larger than L2 (no flush between steps)",
         "exchange": args.exchange,
-        "merge_ways": args.merge_ways or 4,
+        "merge_ways": args.merge_ways or (4 if n >= (1 << 23) else 2),
         "samples_per_run_option": getattr(args, "samples_per_run", 0) or "paper budget",
         "tile_variant": getattr(args, "tile_variant", 0),
         "splitters": args.splitters,

@@ -171,9 +171,11 @@ typedef struct pgs_config {
                                  it monotone */
   float*    model_out;        /* optional device buffer of PGS_MLP_WORDS words: the model used */
   int32_t   merge_ways;       /* lists merged per pass over the data (Fig. 2 tree levels per pass):
-                                 4 (two levels per pass, default; 0 means 4) or 2 (one level, pairwise
-                                 rounds).  Four-way tiles hold exactly their share of outputs: tile
-                                 boundaries come from the key index the previous pass wrote */
+                                 4 (two levels per pass), 2 (one level, pairwise rounds), or 0 (default):
+                                 four-way from 2^23 keys (for a batch: keys of all instances), pairwise
+                                 below, where the sort is bound by its launches.  Four-way tiles hold
+                                 exactly their share of outputs: tile boundaries come from the key index
+                                 the previous pass wrote */
   int32_t   copy_back;         /* pgs_copy_back, pgs_sort_host only; default GROUPS */
   int32_t   graph_cache;       /* pgs_graph_cache, device and batched sorts; default AUTO */
   int32_t   fault_inject;      /* testing only, 0 = off.  PGS_FAULT_WAIT_TIMEOUT: the first tile of the

@@ -97,7 +97,7 @@ int pgs_batch_create(const uint64_t* offsets, uint32_t num, const uint32_t* P, i
   sh.maxlen = maxlen;
   sh.s = 0;
   sh.scatter = o.exchange == PGS_EXCHANGE_SCATTER;
-  sh.four = o.merge_ways == 4;
+  sh.four = use_four_way(sh.n, o);
   finish_shape(sh);
 
   std::vector<uint64_t> run_off(R + 1);

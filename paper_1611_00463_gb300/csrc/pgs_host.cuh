@@ -46,7 +46,7 @@ struct Options {
   const float* model = nullptr;
   float* model_out = nullptr;
   int tile_variant = 0;       // merge tile shape (see kMergeShapes)
-  int merge_ways = 4;         // list merged per pass: 4 (two tree levels, default) or 2 (one level)
+  int merge_ways = 0;         // lists merged per pass: 4 (two tree levels), 2 (one level), 0 = by size
   int copy_back = PGS_COPY_BACK_GROUPS;   // pgs_sort_host: bucket groups after a host wait, or all at the end
   int graph_cache = PGS_GRAPH_CACHE_AUTO; // pgs_sort / pgs_sort_copy: replay repeated calls from a CUDA graph
   uint64_t spin_limit = 0;    // ns of %globaltimer a device-side wait may take; 0 = kWaitLimitNs
@@ -73,7 +73,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   o->model = cfg->model;
   o->model_out = cfg->model_out;
   o->tile_variant = cfg->tile_variant;
-  o->merge_ways = cfg->merge_ways == 0 ? 4 : cfg->merge_ways;
+  o->merge_ways = cfg->merge_ways;
   o->copy_back = cfg->copy_back;
   o->graph_cache = cfg->graph_cache;
   o->spin_limit = cfg->spin_limit;
@@ -84,7 +84,7 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   if (o->exchange < 0 || o->exchange > 2) return PGS_ERR_INVALID;
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
   if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;
-  if (o->merge_ways != 2 && o->merge_ways != 4) return PGS_ERR_INVALID;
+  if (o->merge_ways != 0 && o->merge_ways != 2 && o->merge_ways != 4) return PGS_ERR_INVALID;
   if (o->copy_back != PGS_COPY_BACK_GROUPS && o->copy_back != PGS_COPY_BACK_AT_END) return PGS_ERR_INVALID;
   if (o->graph_cache != PGS_GRAPH_CACHE_AUTO && o->graph_cache != PGS_GRAPH_CACHE_OFF) return PGS_ERR_INVALID;
   if (o->fault_inject != 0 && o->fault_inject != PGS_FAULT_WAIT_TIMEOUT) return PGS_ERR_INVALID;
@@ -131,6 +131,17 @@ struct Shape {
   uint64_t scan_len = 1;
   int passes = 0;            // full passes over the keys
 };
+
+// Keys from which merge_ways 0 uses four-way passes: below it the sort is
+// bound by its launches and the four-way round's extra planning launches (the
+// index-sample merge, the co-ranks) cost more than the passes they save
+// (measured on u32 and u64 keys at 2^20 .. 2^26: pairwise 1-4 % faster up to
+// 2^22 keys, four-way 5-16 % faster from 2^24).
+constexpr uint64_t kFourWayMinKeys = 1ull << 23;
+
+inline bool use_four_way(uint64_t n, const Options& o) {
+  return o.merge_ways == 4 || (o.merge_ways == 0 && n >= kFourWayMinKeys);
+}
 
 inline uint64_t samples_per_run(uint32_t P, int w, const Options& o) {
   uint64_t s = o.samples_per_run ? o.samples_per_run
@@ -181,7 +192,7 @@ inline Shape single_shape(uint64_t n, uint32_t P_req, bool vals, const Options& 
   sh.S = P > 1 ? (sh.s >= sh.maxlen ? n : (uint64_t)P * sh.s) : 0;
   sh.learned = o.splitter_mode == PGS_SPLITTERS_LEARNED && P > 1;
   sh.scatter = o.exchange == PGS_EXCHANGE_SCATTER;
-  sh.four = o.merge_ways == 4;
+  sh.four = use_four_way(n, o);
   finish_shape(sh);
   return sh;
 }

@@ -172,7 +172,7 @@ inline Shape merge_shape(uint64_t n, uint32_t k, bool vals, const Options& o) {
   sh.maxlen = kTile;                                    // no run formation
   sh.s = 0;
   sh.S = 0;
-  sh.four = o.merge_ways == 4;
+  sh.four = use_four_way(sh.n, o);
   finish_shape(sh);
   return sh;
 }
