@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(kNT)
 k_block_sort(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* kout, uint32_t* vout,
              const uint64_t* __restrict__ run_off, uint32_t tiles_per_run, int f32_in, int f32_out,
              K* __restrict__ kidx) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSortSmem<K>& sm = *reinterpret_cast<BlockSortSmem<K>*>(smem_raw);
   const int tid = threadIdx.x;
@@ -274,6 +275,7 @@ __device__ __forceinline__ void put_pair(Pair* pairs, uint64_t* tcount, uint64_t
 // Index space: run x pair slot (cmax slots per run, unused slots are empty).
 static __global__ void k_pairs_runs(Pair* pairs, uint64_t* tcount, const uint64_t* __restrict__ run_off,
                                     uint32_t R, uint64_t w, uint64_t cmax, uint32_t tile) {
+  pdl_enter();
   uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (p >= (uint64_t)R * cmax) return;
   uint64_t r = p / cmax, j = p % cmax;
@@ -295,6 +297,7 @@ static __global__ void k_pairs_runs(Pair* pairs, uint64_t* tcount, const uint64_
 //    tbl = segment offsets (bucket-major), slot = global segment.
 static __global__ void k_pairs_sample_lists(Pair* pairs, uint64_t* tcount, Geo g,
                                             const uint64_t* __restrict__ samp_off, uint32_t step, uint32_t tile) {
+  pdl_enter();
   uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (p >= g.R) return;
   const uint32_t i = g.run_inst[p];
@@ -312,6 +315,7 @@ static __global__ void k_pairs_sample_lists(Pair* pairs, uint64_t* tcount, Geo g
 // Slots [q0, q0 + Q) take part (whole buckets); slot q0 + t writes pair t.
 static __global__ void k_pairs_bucket_lists(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
                                             uint64_t q0, uint64_t Q, uint32_t step, uint32_t tile) {
+  pdl_enter();
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= Q) return;
   const uint64_t q = q0 + t;
@@ -335,6 +339,7 @@ static __global__ void k_pairs_bucket_lists(Pair* pairs, uint64_t* tcount, Geo g
 // Slots [q0, q0 + Q) take part (whole buckets); slot q0 + t writes pair t.
 static __global__ void k_pairs_fused(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
                                      const uint64_t* __restrict__ seg_src, uint64_t q0, uint64_t Q, uint32_t tile) {
+  pdl_enter();
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= Q) return;
   const uint64_t q = q0 + t;
@@ -544,6 +549,7 @@ template <typename K>
 __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restrict__ pairs,
                                   const uint64_t* __restrict__ tbegin, uint64_t npairs, TileSplit* split,
                                   uint32_t tile, const K* __restrict__ kidx, const uint32_t* err) {
+  pdl_enter();
   if (poisoned(err)) return;
   uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t total = tbegin[npairs];
@@ -572,6 +578,7 @@ __global__ void __launch_bounds__(NT, (merge_min_blocks<K, NT, VT>()))
 k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
              uint32_t* __restrict__ vdst, const TileSplit* __restrict__ split, const uint64_t* __restrict__ total_ptr,
              int f32_out, uint32_t* err, K* __restrict__ kidx, uint64_t wait_ns, int inject_timeout) {
+  pdl_enter();
   using L = Merge2Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -769,6 +776,7 @@ __device__ __forceinline__ void put_quad4(Quad* quads, uint64_t* tcount4, Pair* 
 static __global__ void k_quads4_runs(Quad* quads, uint64_t* tcount4, Pair* spairs, uint64_t* stcount,
                                      const uint64_t* __restrict__ run_off, uint32_t R, uint64_t w, uint64_t cmax,
                                      uint32_t Q, uint32_t mtile) {
+  pdl_enter();
   uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (p >= (uint64_t)R * cmax) return;
   const uint64_t r = p / cmax, j = p % cmax;
@@ -783,6 +791,7 @@ static __global__ void k_quads4_runs(Quad* quads, uint64_t* tcount4, Pair* spair
 static __global__ void k_quads4_buckets(Quad* quads, uint64_t* tcount4, Pair* spairs, uint64_t* stcount, Geo g,
                                         const uint64_t* __restrict__ off, uint64_t q0, uint64_t Qg, uint32_t step,
                                         uint32_t Q, uint32_t mtile) {
+  pdl_enter();
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (t >= Qg) return;
   const uint64_t q = q0 + t;
@@ -808,6 +817,7 @@ template <typename K>
 __global__ void k_corank4(const K* __restrict__ src, const K* __restrict__ kidx, const K* __restrict__ xs,
                           const Quad* __restrict__ quads, const uint64_t* __restrict__ tbegin4, uint64_t nquads,
                           Split4* splits, uint64_t cap, uint32_t Q, uint32_t* err) {
+  pdl_enter();
   if (poisoned(err)) return;
   const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t total = tbegin4[nquads];
@@ -920,6 +930,7 @@ k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __res
          uint32_t* __restrict__ vdst, const Split4* __restrict__ splits, const Quad* __restrict__ quads,
          const uint64_t* __restrict__ total_ptr, uint64_t cap, int f32_out, uint32_t* err, K* __restrict__ kidx,
          uint64_t wait_ns, int inject_timeout) {
+  pdl_enter();
   using L = Merge4Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -1134,6 +1145,7 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t x, uint64_t* t
 
 static __global__ void __launch_bounds__(kScanNT)
 k_scan_reduce(const uint64_t* __restrict__ in, uint64_t m, uint64_t* __restrict__ sums) {
+  pdl_enter();
   uint64_t base = blockIdx.x * (uint64_t)kScanChunk;
   uint64_t acc = 0;
 #pragma unroll
@@ -1150,6 +1162,7 @@ k_scan_reduce(const uint64_t* __restrict__ in, uint64_t m, uint64_t* __restrict_
 static __global__ void __launch_bounds__(kScanNT)
 k_scan_chunks(const uint64_t* __restrict__ in, uint64_t m, uint64_t* __restrict__ out,
               const uint64_t* __restrict__ offsets) {
+  pdl_enter();
   uint64_t base = blockIdx.x * (uint64_t)kScanChunk;
   uint64_t carry = offsets ? offsets[blockIdx.x] : 0;
   uint64_t v[kScanVT];
@@ -1179,6 +1192,7 @@ k_scan_chunks(const uint64_t* __restrict__ in, uint64_t m, uint64_t* __restrict_
 static __global__ void k_tables_single(uint64_t* koff, uint32_t* Pt, uint32_t* R0, uint64_t* mat, uint64_t* seg,
                                        uint64_t* st, uint64_t* run_off, uint32_t* run_inst, uint64_t n, uint32_t P,
                                        uint64_t s) {
+  pdl_enter();
   uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (r > P) return;
   run_off[r] = run_start(r, n, P);
@@ -1202,6 +1216,7 @@ static __global__ void k_tables_single(uint64_t* koff, uint32_t* Pt, uint32_t* R
 
 // Samples per run, s_r = min(s, n_r) (the scan of these gives every run's first sample).
 static __global__ void k_sample_counts(Geo g, uint64_t* counts) {
+  pdl_enter();
   uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (r >= g.R) return;
   counts[r] = umin(g.s[g.run_inst[r]], g.run_off[r + 1] - g.run_off[r]);
@@ -1210,6 +1225,7 @@ static __global__ void k_sample_counts(Geo g, uint64_t* counts) {
 template <typename K>
 __global__ void k_sample(const K* __restrict__ runs, Geo g, const uint64_t* __restrict__ samp_off,
                          K* __restrict__ samples, uint64_t S) {
+  pdl_enter();
   uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (j >= S) return;
   const uint32_t r = last_le<uint64_t>(samp_off, g.R, j);
@@ -1225,6 +1241,7 @@ __global__ void k_sample(const K* __restrict__ runs, Geo g, const uint64_t* __re
 template <typename K>
 __global__ void k_pick_splitters(const K* __restrict__ sorted, Geo g, const uint64_t* __restrict__ samp_off, K* t,
                                  K* user_out, int f32) {
+  pdl_enter();
   uint64_t beta = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (beta >= g.R) return;
   const uint32_t i = g.run_inst[beta];
@@ -1240,6 +1257,7 @@ __global__ void k_pick_splitters(const K* __restrict__ sorted, Geo g, const uint
 // The same pick on one sorted sample of m keys: out[b-1] = sorted[floor(b m / P) - 1].
 template <typename K>
 __global__ void k_pick_splitters_flat(const K* __restrict__ sorted, uint64_t m, uint32_t P, K* out, int f32) {
+  pdl_enter();
   uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x + 1;
   if (b >= P) return;
   out[b - 1] = from_order<K>(sorted[(b * m) / P - 1], f32);
@@ -1255,6 +1273,7 @@ __global__ void k_pick_splitters_flat(const K* __restrict__ sorted, uint64_t m, 
 template <typename K>
 __global__ void k_cut_search(const K* __restrict__ runs, Geo g, uint64_t Q, const K* __restrict__ t,
                              uint64_t* lb, uint64_t* cnt) {
+  pdl_enter();
   uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (q >= Q) return;
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
@@ -1285,6 +1304,7 @@ template <typename K>
 __global__ void __launch_bounds__(256)
 k_investigator(const uint64_t* __restrict__ lb, const uint64_t* __restrict__ cnt, const K* __restrict__ t, Geo g,
                int variant, uint64_t* cut, uint64_t* e) {
+  pdl_enter();
   const uint32_t beta = blockIdx.x;
   const uint32_t i = g.run_inst[beta];
   const uint32_t r0 = g.R0[i];
@@ -1372,6 +1392,7 @@ k_investigator(const uint64_t* __restrict__ lb, const uint64_t* __restrict__ cnt
 
 // cut[r][0] = 0, cut[r][P] = n_r for every run; e[0] = 0, e[P] = n_i.
 static __global__ void k_cut_edges(Geo g, uint64_t* cut, uint64_t* e) {
+  pdl_enter();
   uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (r >= g.R) return;
   const uint32_t i = g.run_inst[r];
@@ -1390,6 +1411,7 @@ static __global__ void k_cut_edges(Geo g, uint64_t* cut, uint64_t* e) {
 // cut[r][b+1] - cut[r][b] and the global position where they start.
 static __global__ void k_bucket_sizes(Geo g, uint64_t Q, const uint64_t* __restrict__ cut, uint64_t* sizes,
                                       uint64_t* src) {
+  pdl_enter();
   uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (q >= Q) return;
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
@@ -1411,6 +1433,7 @@ static __global__ void k_bucket_sizes(Geo g, uint64_t Q, const uint64_t* __restr
 
 static __global__ void k_scatter_part(const uint64_t* __restrict__ off, uint64_t Q, uint64_t n,
                                uint64_t* first_seg) {
+  pdl_enter();
   uint64_t tile = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   uint64_t o = tile * kScatterTile;
   if (o >= n) return;
@@ -1436,6 +1459,7 @@ k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __re
           uint32_t* __restrict__ vdst, const uint64_t* __restrict__ off, const uint64_t* __restrict__ seg_src,
           const uint64_t* __restrict__ first_seg, uint64_t n, uint64_t Q, int f32_out, const uint32_t* err,
           K* __restrict__ kidx) {
+  pdl_enter();
   if (poisoned(err)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sm = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
@@ -1487,6 +1511,7 @@ k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __re
 // payloads, for timing runs of the tuner.
 template <typename K>
 __global__ void k_fill_random(K* keys, uint32_t* vals, uint64_t n, uint64_t seed) {
+  pdl_enter();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint64_t z = (i + 1) * 0x9E3779B97F4A7C15ull + seed;
@@ -1518,6 +1543,7 @@ static __global__ void __launch_bounds__(256)
 k_stats(Geo g, const uint64_t* __restrict__ e, uint64_t n_total, uint32_t s, uint32_t mode, uint32_t passes,
         uint32_t launches, const uint32_t* err_word, const uint32_t* fallback_word,
         const float* learned_ratio, DevStats* st, uint64_t* user_bounds, float* max_ratio_out) {
+  pdl_enter();
   __shared__ uint64_t smax[256], smin[256];
   __shared__ float sratio[256];
   uint64_t mx = 0, mn = ~0ull;

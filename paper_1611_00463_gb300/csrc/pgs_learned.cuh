@@ -100,6 +100,7 @@ __device__ __forceinline__ float mlp_sign(int j) { return j < kMlpHalf ? 1.0f : 
 // samples of sorted index floor((2j + 1) S / 32), layer 2 close to the identity.
 template <typename K>
 __global__ void k_mlp_init(const K* __restrict__ sorted, uint64_t S, MlpState* st) {
+  pdl_enter();
   const uint64_t kmin = (uint64_t)sorted[0];
   const uint64_t span = (uint64_t)sorted[S - 1] - kmin;
   const float scale = span == 0 ? 0.0f : __fdiv_rn(1.0f, __double2float_rn(__ull2double_rn(span)));
@@ -151,6 +152,7 @@ struct MlpGradSmem {
 template <typename K>
 __global__ void __launch_bounds__(kMlpBatch)
 k_mlp_grad(const K* __restrict__ sorted, uint64_t S, const MlpState* __restrict__ st, float* part) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   MlpGradSmem& sm = *reinterpret_cast<MlpGradSmem*>(smem_raw);
   const int tid = threadIdx.x;
@@ -277,6 +279,7 @@ constexpr int kAdamParams = 32;
 constexpr int kAdamWarps = 8;
 static __global__ void __launch_bounds__(kAdamParams * kAdamWarps)
 k_mlp_adam(const float* __restrict__ part, uint32_t nparts, MlpState* st, uint32_t step, uint64_t S) {
+  pdl_enter();
   __shared__ float sums[kAdamWarps][kAdamParams];
   const int lane = threadIdx.x % kAdamParams, warp = threadIdx.x / kAdamParams;
   const int p = blockIdx.x * kAdamParams + lane;
@@ -307,6 +310,7 @@ k_mlp_adam(const float* __restrict__ part, uint32_t nparts, MlpState* st, uint32
 
 // Effective weights and normalisation of the trained model.
 static __global__ void k_mlp_finalize(const MlpState* __restrict__ st, float* model) {
+  pdl_enter();
   for (int p = threadIdx.x; p < kMlpW; p += blockDim.x) {
     const float r = st->raw[p];
     float w = r;
@@ -328,6 +332,7 @@ static __global__ void k_mlp_finalize(const MlpState* __restrict__ st, float* mo
 
 // A caller's model: copy it and mark it valid only if its signs make it monotone.
 static __global__ void k_mlp_validate(const float* __restrict__ given, float* model) {
+  pdl_enter();
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
@@ -364,6 +369,7 @@ template <typename K>
 __global__ void __launch_bounds__(kLearnedSearchNT)
 k_learned_search(const K* __restrict__ runs, const uint64_t* __restrict__ run_off, uint32_t P,
                  const float* __restrict__ model, uint64_t* cutL) {
+  pdl_enter();
   __shared__ float w[kMlpW];
   for (int p = threadIdx.x; p < kMlpW; p += blockDim.x) w[p] = model[p];
   __syncthreads();
@@ -392,6 +398,7 @@ k_learned_search(const K* __restrict__ runs, const uint64_t* __restrict__ run_of
 // P above kLearnedMaxP: the sampled cuts stand, the model is not evaluated,
 // and a requested model output is an invalid (flag 0) all-zero model.
 static __global__ void k_learned_skip(uint32_t* fallback, float* ratio_out, float* model_out) {
+  pdl_enter();
   if (threadIdx.x == 0) {
     *fallback = 1u;
     *ratio_out = __int_as_float(0x7FC00000);
@@ -401,6 +408,7 @@ static __global__ void k_learned_skip(uint32_t* fallback, float* ratio_out, floa
 }
 
 static __global__ void k_learned_colsum(const uint64_t* __restrict__ cutL, uint32_t P, uint64_t* eL) {
+  pdl_enter();
   const uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (b > P) return;
   uint64_t s = 0;
@@ -411,6 +419,7 @@ static __global__ void k_learned_colsum(const uint64_t* __restrict__ cutL, uint3
 static __global__ void __launch_bounds__(256)
 k_learned_judge(const uint64_t* __restrict__ eL, uint32_t P, uint64_t n, float eps, const float* __restrict__ model,
                 uint32_t* fallback, float* ratio_out) {
+  pdl_enter();
   __shared__ uint64_t smax[256];
   uint64_t mx = 0;
   for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) mx = umax(mx, eL[b + 1] - eL[b]);
@@ -431,6 +440,7 @@ k_learned_judge(const uint64_t* __restrict__ eL, uint32_t P, uint64_t n, float e
 // Order form of sorted user keys (float32 bits to their totalOrder image).
 template <typename K>
 __global__ void k_to_order(const K* __restrict__ in, K* out, uint64_t m, int f32) {
+  pdl_enter();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i < m) out[i] = to_order<K>(in[i], f32);
 }
@@ -438,6 +448,7 @@ __global__ void k_to_order(const K* __restrict__ in, K* out, uint64_t m, int f32
 // Keep the learned cuts and bucket vector unless the judge fell back.
 static __global__ void k_learned_select(const uint64_t* __restrict__ cutL, const uint64_t* __restrict__ eL, uint32_t P,
                                         const uint32_t* __restrict__ fallback, uint64_t* cut, uint64_t* e) {
+  pdl_enter();
   if (*fallback) return;
   uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (q < (uint64_t)P * (P + 1)) cut[q] = cutL[q];

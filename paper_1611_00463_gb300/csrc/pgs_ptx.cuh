@@ -10,6 +10,14 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;   // default limit, 2 s: far ab
 constexpr uint32_t kErrWaitTimeout = 1u;           // error word bit: a bounded wait expired
 constexpr uint32_t kErrBadTile = 2u;               // error word bit: a merge tile did not fit its buffer
 
+// Programmatic dependent launch: wait until the grids this one depends on
+// have completed and their memory is visible, then let this grid's own
+// dependents be scheduled.  Both are no-ops for a grid launched without it.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // True once any kernel of the call has set the device error word.  Every
 // kernel whose addresses depend on the data (merge-path searches, bulk copies,
 // the exchange) returns at once when it is set: a failed tile leaves its

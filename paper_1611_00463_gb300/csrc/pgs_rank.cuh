@@ -24,6 +24,7 @@ namespace pgs {
 // positions floor((i+1) n / sr) - 1 (the caller's bit patterns).
 template <typename K>
 __global__ void k_rank_samples(const K* __restrict__ sorted, uint64_t n, uint64_t sr, K* out) {
+  pdl_enter();
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (i >= sr) return;
   out[i] = sorted[(uint64_t)(((unsigned __int128)(i + 1) * n) / sr) - 1];
@@ -34,6 +35,7 @@ __global__ void k_rank_samples(const K* __restrict__ sorted, uint64_t n, uint64_
 template <typename K>
 __global__ void k_rank_counts(const K* __restrict__ sorted, uint64_t n, const K* __restrict__ spl, uint32_t G,
                               uint64_t* out, int f32) {
+  pdl_enter();
   const uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x + 1;
   if (b >= G) return;
   const K v = to_order<K>(spl[b - 1], f32);
@@ -56,6 +58,7 @@ __global__ void k_rank_counts(const K* __restrict__ sorted, uint64_t n, const K*
 // lb / cnt matrices of the investigator (entries b = 1..G-1 of each row).
 static __global__ void k_rank_unpack(const uint64_t* __restrict__ counts_all, uint32_t G, uint64_t* lb,
                                      uint64_t* cnt) {
+  pdl_enter();
   const uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (q >= (uint64_t)G * (G - 1)) return;
   const uint64_t r = q / (G - 1), b = q % (G - 1) + 1;
@@ -68,6 +71,7 @@ static __global__ void k_rank_unpack(const uint64_t* __restrict__ counts_all, ui
 // investigator reads them.
 template <typename K>
 __global__ void k_rank_splitters(const K* __restrict__ spl, uint32_t G, K* t, int f32) {
+  pdl_enter();
   const uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x + 1;
   if (b >= G) return;
   t[b] = to_order<K>(spl[b - 1], f32);
@@ -141,18 +145,18 @@ int run_rank_cuts(const uint64_t* counts_all, const uint64_t* host_sizes, uint32
   c.timer = o.timer;
   if (G > 1) {
     PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 16ull * G * (G - 1), [&] {
-      k_rank_unpack<<<grid_for((uint64_t)G * (G - 1), 256), 256, 0, st>>>(counts_all, G, lb, cnt);
+      klaunch(st, c.pdl, k_rank_unpack, grid_for((uint64_t)G * (G - 1), 256), 256, 0, counts_all, G, lb, cnt);
     }));
     PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 2ull * G * sizeof(K), [&] {
-      k_rank_splitters<K><<<grid_for(G, 256), 256, 0, st>>>(spl, G, t, f32);
+      klaunch(st, c.pdl, k_rank_splitters<K>, grid_for(G, 256), 256, 0, spl, G, t, f32);
     }));
   }
   PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24ull * G, [&] {
-    k_cut_edges<<<grid_for(G, 256), 256, 0, st>>>(g, cut_out, e_out);
+    klaunch(st, c.pdl, k_cut_edges, grid_for(G, 256), 256, 0, g, cut_out, e_out);
   }));
   if (G == 1) return PGS_OK;
   return launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24ull * G * (G + 1), [&] {
-    k_investigator<K><<<G, 256, 0, st>>>(lb, cnt, t, g, o.investigator, cut_out, e_out);
+    klaunch(st, c.pdl, k_investigator<K>, G, 256, 0, lb, cnt, t, g, o.investigator, cut_out, e_out);
   });
 }
 
@@ -181,6 +185,7 @@ inline Shape merge_shape(uint64_t n, uint32_t k, bool vals, const Options& o) {
 // round's partition and four-way boundaries read).
 template <typename K>
 __global__ void k_build_index(const K* __restrict__ src, uint64_t n, K* kidx, int f32) {
+  pdl_enter();
   const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (e * kIdxStride >= n) return;
   kidx[e] = to_order<K>(src[e * kIdxStride], f32);
@@ -190,6 +195,7 @@ __global__ void k_build_index(const K* __restrict__ src, uint64_t n, K* kidx, in
 // error word (pgs_get_stats reads them).
 static __global__ void k_merge_stats(DevStats* st, uint64_t n, uint32_t k, uint32_t passes, uint32_t launches,
                                      const uint32_t* err) {
+  pdl_enter();
   st->n = n;
   st->P = k;
   st->s = 0;
@@ -229,6 +235,7 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
   c.variant = o.tile_variant;
   c.wait_ns = o.spin_limit;
   c.inject_timeout = o.fault_inject == PGS_FAULT_WAIT_TIMEOUT;
+  c.pdl = n <= kPdlMaxKeys;
   Buffers b;
   carve(sh, o.workspace, &b);
   const int f32 = o.dtype == PGS_F32;
@@ -236,7 +243,7 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
   PGS_CUDA(cudaMemsetAsync(b.err, 0, sizeof(uint32_t), st));
   if (passes > 0) {
     PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 0, 16ull * (k + 1), [&] {
-      k_tables_single<<<grid_for(k + 1, 256), 256, 0, st>>>(b.koff, b.Pt, b.R0, b.mat, b.seg, b.st, b.run_off,
+      klaunch(st, c.pdl, k_tables_single, grid_for(k + 1, 256), 256, 0, b.koff, b.Pt, b.R0, b.mat, b.seg, b.st, b.run_off,
                                                             b.run_inst, n, k, 0);
     }));
     PGS_CUDA(cudaMemcpyAsync(b.off, host_off, (k + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
@@ -248,12 +255,12 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
     if (f32) {                                          // the rounds compare order-form keys
       K* conv = passes % 2 ? alt : kout;                // never a buffer the first round writes
       PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 6, 2 * n * sizeof(K), [&] {
-        k_to_order<K><<<grid_for(n, 256), 256, 0, st>>>(kin, conv, n, 1);
+        klaunch(st, c.pdl, k_to_order<K>, grid_for(n, 256), 256, 0, kin, conv, n, 1);
       }));
       src = conv;
     }
     PGS_TRY(launch(c, PGS_KERNEL_PARTITION, 6, 2 * ceil_div(n, kIdxStride) * sizeof(K), [&] {
-      k_build_index<K><<<grid_for(ceil_div(n, kIdxStride), 256), 256, 0, st>>>(src, n, kidx, 0);
+      klaunch(st, c.pdl, k_build_index<K>, grid_for(ceil_div(n, kIdxStride), 256), 256, 0, src, n, kidx, 0);
     }));
     const Geo g = b.geo(sh);
     uint32_t step = 1;
@@ -265,7 +272,7 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
       K* io = last ? nullptr : kidx;
       if (sh.four && levels >= 2) {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 112ull * k, [&] {
-          k_quads4_buckets<<<grid_for(k, 256), 256, 0, st>>>(b.quads, b.tcount4, b.pairs, b.tcount, g, b.off, 0, k,
+          klaunch(st, c.pdl, k_quads4_buckets, grid_for(k, 256), 256, 0, b.quads, b.tcount4, b.pairs, b.tcount, g, b.off, 0, k,
                                                              step, kMerge4Q, mtile);
         }));
         PGS_TRY((merge4_round<K, V>(c, src, vsrc, kd, vd, k, n, b, last ? f32 : 0, 6, kidx, io,
@@ -274,7 +281,7 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
         levels -= 2;
       } else {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32ull * k, [&] {
-          k_pairs_bucket_lists<<<grid_for(k, 256), 256, 0, st>>>(b.pairs, b.tcount, g, b.off, 0, k, step, mtile);
+          klaunch(st, c.pdl, k_pairs_bucket_lists, grid_for(k, 256), 256, 0, b.pairs, b.tcount, g, b.off, 0, k, step, mtile);
         }));
         PGS_TRY((merge_round<K, V>(c, src, vsrc, kd, vd, k, n, b, last ? f32 : 0, 6, kidx, io,
                                    ceil_div(k, 2ull * step) + 1)));
@@ -288,7 +295,7 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
   if (!o.stats) return PGS_OK;
   const uint32_t launches = c.launches + 1;
   return launch(c, PGS_KERNEL_STATS, 0, 64, [&] {
-    k_merge_stats<<<1, 1, 0, st>>>(static_cast<DevStats*>(o.stats), n, k, (uint32_t)passes, launches, b.err);
+    klaunch(st, c.pdl, k_merge_stats, 1, 1, 0, static_cast<DevStats*>(o.stats), n, k, (uint32_t)passes, launches, b.err);
   });
 }
 
