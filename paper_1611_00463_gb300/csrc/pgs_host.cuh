@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <type_traits>
 #include <vector>
 
 #include "pgs.h"
@@ -511,18 +512,30 @@ inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* 
 // live_pairs: an upper bound on the slots that can hold a non-empty pair (the
 // grid covers ceil(len / tile) tiles plus one partial tile per such pair;
 // empty CTAs beyond the round's total cost launch time).
-template <typename K, bool V>
-inline int merge_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
+template <typename K, bool V, typename Gen>
+inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, const K* idx_in = nullptr,
                        K* idx_out = nullptr, uint64_t live_pairs = ~0ull) {
   const MergeShape ms = kMergeShapes[c.variant];
   const uint32_t tile = (uint32_t)(ms.nt * ms.vt);
-  PGS_TRY(scan_u64(c, b.tcount, b.tbegin, npairs, b.scan_sums, b.scan_sums2, step));
   const uint64_t tiles_ub = ceil_div(len, tile) + std::min(npairs, live_pairs);
-  PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, tile), [&] {
-    klaunch(c.st, c.pdl, k_partition_split<K>, grid_for(tiles_ub, 256), 256, 0, ks, b.pairs, b.tbegin, npairs, b.split, tile,
-                                                                    idx_in, b.err);
-  }));
+  if (npairs <= kPlanMaxPairs && tiles_ub <= kPlanMaxTiles) {
+    // A small round: descriptors, their scan and the splits in one CTA.
+    PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * tiles_ub + 56 * npairs, [&] {
+      klaunch(c.st, c.pdl, k_plan_small<K, Gen>, 1, kPlanNT, 0, gen, ks, b.pairs, b.tcount, b.tbegin, npairs,
+              b.split, tile, idx_in, b.err);
+    }));
+  } else {
+    if (!std::is_same<Gen, GenNone>::value)
+      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, step, 48 * npairs, [&] {
+        klaunch(c.st, c.pdl, k_pairs<Gen>, grid_for(npairs, 256), 256, 0, gen, npairs);
+      }));
+    PGS_TRY(scan_u64(c, b.tcount, b.tbegin, npairs, b.scan_sums, b.scan_sums2, step));
+    PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * ceil_div(len, tile), [&] {
+      klaunch(c.st, c.pdl, k_partition_split<K>, grid_for(tiles_ub, 256), 256, 0, ks, b.pairs, b.tbegin, npairs,
+              b.split, tile, idx_in, b.err);
+    }));
+  }
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
   const uint64_t* total = b.tbegin + npairs;
   const int inject = c.inject_timeout;
@@ -556,8 +569,8 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
   // X' = merge(I_0, I_1) and Y' = merge(I_2, I_3) of every quad (keys only).
   const int inject = c.inject_timeout;
   c.inject_timeout = 0;
-  PGS_TRY((merge_round<K, false>(c, idx_in, nullptr, xs, nullptr, 2 * nquads, samples, b, 0, step, nullptr,
-                                 nullptr, 2 * nq_live)));
+  PGS_TRY((merge_round<K, false>(c, GenNone{}, idx_in, nullptr, xs, nullptr, 2 * nquads, samples, b, 0, step,
+                                 nullptr, nullptr, 2 * nq_live)));
   PGS_TRY(scan_u64(c, b.tcount4, b.tbegin4, nquads, b.scan_sums, b.scan_sums2, step));
   const uint64_t tiles_ub = ceil_div(samples, kMerge4Q) + nq_live + 1;   // <= sh.max_tiles4
   if (tiles_ub > b.max_tiles4) return PGS_ERR_CUDA;                        // plan bug: never expected
@@ -752,9 +765,10 @@ struct Pipeline {
     return PGS_OK;
   }
   // A pairwise round of the pairs in b.pairs from cur to oth (left already counts it).
-  int pair_round(uint64_t npairs, uint64_t len, uint32_t step, uint64_t live_pairs = ~0ull) {
+  template <typename Gen>
+  int pair_round(const Gen& gen, uint64_t npairs, uint64_t len, uint32_t step, uint64_t live_pairs = ~0ull) {
     K* io = idx_out();
-    PGS_TRY((merge_round<K, V>(c, cur_k, cur_v, oth_k, oth_v, npairs, len, b, f32_out(), step, idx_in(), io,
+    PGS_TRY((merge_round<K, V>(c, gen, cur_k, cur_v, oth_k, oth_v, npairs, len, b, f32_out(), step, idx_in(), io,
                                live_pairs)));
     idx_ok = io != nullptr;
     return PGS_OK;
@@ -789,10 +803,7 @@ struct Pipeline {
       } else {
         const uint64_t cmax = ceil_div(sh.maxlen, 2 * w);
         const uint64_t np = cmax * Rg;
-        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 32 * np, [&] {
-          klaunch(st, c.pdl, k_pairs_runs, grid_for(np, 256), 256, 0, b.pairs, b.tcount, ro, Rg, w, cmax, mtile);
-        }));
-        PGS_TRY(pair_round(np, len, 1));
+        PGS_TRY(pair_round(GenRuns{b.pairs, b.tcount, ro, Rg, w, cmax, mtile}, np, len, 1));
         w *= 2;
         levels -= 1;
       }
@@ -834,10 +845,8 @@ struct Pipeline {
     }));
     for (int k = 0; k < sh.bucket_rounds; ++k) {
       const uint32_t step = 1u << k;
-      PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 3, 32 * (uint64_t)R, [&] {
-        klaunch(st, c.pdl, k_pairs_sample_lists, grid_for(R, 256), 256, 0, b.pairs, b.tcount, g, b.samp_off, step, mtile);
-      }));
-      PGS_TRY((merge_round<K, false>(c, sa, nullptr, sb, nullptr, R, sh.S, b, 0, 3)));
+      PGS_TRY((merge_round<K, false>(c, GenSampleLists{b.pairs, b.tcount, g, b.samp_off, step, mtile}, sa, nullptr,
+                                     sb, nullptr, R, sh.S, b, 0, 3)));
       std::swap(sa, sb);
     }
     PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)R * sizeof(K), [&] {
@@ -893,11 +902,9 @@ struct Pipeline {
       k0 = 0;
       return PGS_OK;
     }
-    PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 5, 48 * sh.Q, [&] {
-      klaunch(st, c.pdl, k_pairs_fused, grid_for(sh.Q, 256), 256, 0, b.pairs, b.tcount, g, b.off, b.seg_src, 0, sh.Q, mtile);
-    }));
     --left;
-    PGS_TRY(pair_round(sh.Q, n, 6, bucket_live_pairs(sh.Q, 1)));
+    PGS_TRY(pair_round(GenFused{b.pairs, b.tcount, g, b.off, b.seg_src, 0, mtile}, sh.Q, n, 6,
+                       bucket_live_pairs(sh.Q, 1)));
     flip();
     k0 = 1;
     return PGS_OK;
@@ -920,11 +927,8 @@ struct Pipeline {
         step *= 4;
         levels -= 2;
       } else {
-        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32 * Qg, [&] {
-          klaunch(st, c.pdl, k_pairs_bucket_lists, grid_for(Qg, 256), 256, 0, b.pairs, b.tcount, g, b.off, q0, Qg, step,
-                                                                   mtile);
-        }));
-        PGS_TRY(pair_round(Qg, len, 6, bucket_live_pairs(Qg, step)));
+        PGS_TRY(pair_round(GenBucketLists{b.pairs, b.tcount, g, b.off, q0, step, mtile}, Qg, len, 6,
+                           bucket_live_pairs(Qg, step)));
         step *= 2;
         levels -= 1;
       }

@@ -270,22 +270,60 @@ __device__ __forceinline__ void put_pair(Pair* pairs, uint64_t* tcount, uint64_t
   tcount[p] = (hi - lo + tile - 1) / tile;
 }
 
+// Exclusive scan across the CTA (blockDim.x a multiple of 32, at most 1024);
+// every thread also gets the CTA total.  Ends with a barrier, so it may be
+// called back to back.
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t x, uint64_t* total) {
+  __shared__ uint64_t warp_sums[33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t inc = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint64_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane >= d) inc += y;
+  }
+  if (lane == 31) warp_sums[warp] = inc;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  if (warp == 0) {
+    uint64_t v = lane < nw ? warp_sums[lane] : 0;
+    uint64_t vi = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint64_t y = __shfl_up_sync(0xFFFFFFFFu, vi, d);
+      if (lane >= d) vi += y;
+    }
+    if (lane < nw) warp_sums[lane] = vi - v;
+    if (lane == 31) warp_sums[32] = vi;
+  }
+  __syncthreads();
+  uint64_t res = warp_sums[warp] + inc - x;
+  uint64_t tot = warp_sums[32];
+  __syncthreads();
+  if (total) *total = tot;
+  return res;
+}
+
+// Pair descriptors of one pairwise round.  A generator writes slot p of the
+// round's pair table (pairs[p], and its tile count at merge tile `tile`);
+// k_pairs runs one generator over all slots, and k_plan_small (below) runs it
+// inside the single CTA that also scans and splits a small round.
+
 // Run formation (step 1): inside every run, blocks [j 2w, j 2w + w) and
 // [j 2w + w, (j+1) 2w) merge; a run that is already one list is copied.
 // Index space: run x pair slot (cmax slots per run, unused slots are empty).
-static __global__ void k_pairs_runs(Pair* pairs, uint64_t* tcount, const uint64_t* __restrict__ run_off,
-                                    uint32_t R, uint64_t w, uint64_t cmax, uint32_t tile) {
-  pdl_enter();
-  uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (p >= (uint64_t)R * cmax) return;
-  uint64_t r = p / cmax, j = p % cmax;
-  uint64_t rs = run_off[r], re = run_off[r + 1];
-  uint64_t lo = umin(rs + j * 2 * w, re);
-  if (j > 0 && lo >= re) lo = re;                     // empty slot
-  uint64_t mid = umin(lo + w, re);
-  uint64_t hi = umin(lo + 2 * w, re);
-  put_pair(pairs, tcount, p, lo, mid, hi, tile);
-}
+struct GenRuns {
+  Pair* pairs; uint64_t* tcount; const uint64_t* run_off; uint32_t R; uint64_t w, cmax; uint32_t tile;
+  __device__ void operator()(uint64_t p) const {
+    const uint64_t r = p / cmax, j = p % cmax;
+    const uint64_t rs = run_off[r], re = run_off[r + 1];
+    uint64_t lo = umin(rs + j * 2 * w, re);
+    if (j > 0 && lo >= re) lo = re;                   // empty slot
+    const uint64_t mid = umin(lo + w, re);
+    const uint64_t hi = umin(lo + 2 * w, re);
+    put_pair(pairs, tcount, p, lo, mid, hi, tile);
+  }
+};
 
 // The Fig. 2 schedule over the P lists of one group: round `step` merges list
 // group [j, j+step) with [j+step, j+2 step) for j a multiple of 2 step.  Lists
@@ -295,66 +333,75 @@ static __global__ void k_pairs_runs(Pair* pairs, uint64_t* tcount, const uint64_
 //    tbl = sample offsets indexed by global run, slot = global run;
 //  - buckets (step 6): one group per bucket, lists = its P segments,
 //    tbl = segment offsets (bucket-major), slot = global segment.
-static __global__ void k_pairs_sample_lists(Pair* pairs, uint64_t* tcount, Geo g,
-                                            const uint64_t* __restrict__ samp_off, uint32_t step, uint32_t tile) {
-  pdl_enter();
-  uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (p >= g.R) return;
-  const uint32_t i = g.run_inst[p];
-  const uint32_t r0 = g.R0[i], P = g.P[i];
-  const uint32_t j = (uint32_t)p - r0;
-  const uint64_t end = samp_off[r0 + P];
-  if (j % (2 * step) != 0) {
-    put_pair(pairs, tcount, p, end, end, end, tile);
-    return;
+struct GenSampleLists {
+  Pair* pairs; uint64_t* tcount; Geo g; const uint64_t* samp_off; uint32_t step; uint32_t tile;
+  __device__ void operator()(uint64_t p) const {
+    const uint32_t i = g.run_inst[p];
+    const uint32_t r0 = g.R0[i], P = g.P[i];
+    const uint32_t j = (uint32_t)p - r0;
+    const uint64_t end = samp_off[r0 + P];
+    if (j % (2 * step) != 0) {
+      put_pair(pairs, tcount, p, end, end, end, tile);
+      return;
+    }
+    put_pair(pairs, tcount, p, samp_off[r0 + j], samp_off[r0 + min(j + step, P)],
+             samp_off[r0 + min(j + 2 * step, P)], tile);
   }
-  put_pair(pairs, tcount, p, samp_off[r0 + j], samp_off[r0 + min(j + step, P)],
-           samp_off[r0 + min(j + 2 * step, P)], tile);
-}
+};
 
 // Slots [q0, q0 + Q) take part (whole buckets); slot q0 + t writes pair t.
-static __global__ void k_pairs_bucket_lists(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
-                                            uint64_t q0, uint64_t Q, uint32_t step, uint32_t tile) {
-  pdl_enter();
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t >= Q) return;
-  const uint64_t q = q0 + t;
-  const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
-  const uint64_t P = g.P[i];
-  const uint64_t local = q - g.seg[i];
-  const uint64_t b = local / P, j = local % P;
-  const uint64_t base = g.seg[i] + b * P;           // first segment of bucket b
-  if (j % (2 * step) != 0) {
-    const uint64_t end = off[base + P];
-    put_pair(pairs, tcount, t, end, end, end, tile);
-    return;
+struct GenBucketLists {
+  Pair* pairs; uint64_t* tcount; Geo g; const uint64_t* off; uint64_t q0; uint32_t step; uint32_t tile;
+  __device__ void operator()(uint64_t t) const {
+    const uint64_t q = q0 + t;
+    const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
+    const uint64_t P = g.P[i];
+    const uint64_t local = q - g.seg[i];
+    const uint64_t b = local / P, j = local % P;
+    const uint64_t base = g.seg[i] + b * P;         // first segment of bucket b
+    if (j % (2 * step) != 0) {
+      const uint64_t end = off[base + P];
+      put_pair(pairs, tcount, t, end, end, end, tile);
+      return;
+    }
+    put_pair(pairs, tcount, t, off[base + j], off[base + umin(j + step, P)], off[base + umin(j + 2 * step, P)],
+             tile);
   }
-  put_pair(pairs, tcount, t, off[base + j], off[base + umin(j + step, P)], off[base + umin(j + 2 * step, P)],
-           tile);
-}
+};
 
 // Step 5 fused into the first round of step 6: segment j of bucket b (j even)
 // merges with segment j+1 straight from the sorted runs, where the exchange
 // would have copied them from, into the pair's place in bucket-major order.
 // Slots [q0, q0 + Q) take part (whole buckets); slot q0 + t writes pair t.
-static __global__ void k_pairs_fused(Pair* pairs, uint64_t* tcount, Geo g, const uint64_t* __restrict__ off,
-                                     const uint64_t* __restrict__ seg_src, uint64_t q0, uint64_t Q, uint32_t tile) {
-  pdl_enter();
-  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (t >= Q) return;
-  const uint64_t q = q0 + t;
-  const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
-  const uint64_t P = g.P[i];
-  const uint64_t j = (q - g.seg[i]) % P;
-  if (j % 2 != 0) {
-    pairs[t] = Pair{0, 0, 0, 0, 0};
-    tcount[t] = 0;
-    return;
+struct GenFused {
+  Pair* pairs; uint64_t* tcount; Geo g; const uint64_t* off; const uint64_t* seg_src; uint64_t q0; uint32_t tile;
+  __device__ void operator()(uint64_t t) const {
+    const uint64_t q = q0 + t;
+    const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
+    const uint64_t P = g.P[i];
+    const uint64_t j = (q - g.seg[i]) % P;
+    if (j % 2 != 0) {
+      pairs[t] = Pair{0, 0, 0, 0, 0};
+      tcount[t] = 0;
+      return;
+    }
+    const uint64_t na = off[q + 1] - off[q];
+    const uint64_t nb = j + 1 < P ? off[q + 2] - off[q + 1] : 0;
+    pairs[t] = Pair{seg_src[q], na, j + 1 < P ? seg_src[q + 1] : 0, nb, off[q]};
+    tcount[t] = (na + nb + tile - 1) / tile;
   }
-  const uint64_t na = off[q + 1] - off[q];
-  const uint64_t nb = j + 1 < P ? off[q + 2] - off[q + 1] : 0;
-  pairs[t] = Pair{seg_src[q], na, j + 1 < P ? seg_src[q + 1] : 0, nb, off[q]};
-  tcount[t] = (na + nb + tile - 1) / tile;
+};
+
+// The pair table is already written (the four-way round's index-sample pairs).
+struct GenNone {
+  __device__ void operator()(uint64_t) const {}
+};
+
+template <typename Gen>
+__global__ void k_pairs(Gen gen, uint64_t npairs) {
+  pdl_enter();
+  const uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (p < npairs) gen(p);
 }
 
 // ---------------------------------------------------------------------------
@@ -545,15 +592,14 @@ __device__ __forceinline__ uint64_t last_le_from(const uint64_t* __restrict__ t,
   return lo;
 }
 
+// The split of merge tile i of a round: its pair (a gallop from the guess
+// i npairs / total through the tile-count scan), then one merge-path search,
+// through the key index when both lists are long.
 template <typename K>
-__global__ void k_partition_split(const K* __restrict__ src, const Pair* __restrict__ pairs,
-                                  const uint64_t* __restrict__ tbegin, uint64_t npairs, TileSplit* split,
-                                  uint32_t tile, const K* __restrict__ kidx, const uint32_t* err) {
-  pdl_enter();
-  if (poisoned(err)) return;
-  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  uint64_t total = tbegin[npairs];
-  if (i >= total) return;
+__device__ __forceinline__ void partition_tile(uint64_t i, uint64_t total, const K* __restrict__ src,
+                                               const Pair* __restrict__ pairs, const uint64_t* __restrict__ tbegin,
+                                               uint64_t npairs, TileSplit* split, uint32_t tile,
+                                               const K* __restrict__ kidx) {
   const uint64_t guess = (uint64_t)(((unsigned __int128)i * npairs) / total);   // < npairs as i < total
   const uint64_t lo = last_le_from(tbegin, npairs, i, guess);                 // the tile's pair
   const Pair pr = pairs[lo];
@@ -562,6 +608,61 @@ __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restr
                           ? merge_path_indexed<K>(src, kidx, pr, d0)
                           : merge_path<K, uint64_t>(src + pr.a, pr.na, src + pr.b, pr.nb, d0);
   split[i] = TileSplit{pr.a + a0, pr.b + (d0 - a0), pr.out + d0, pr.a + pr.na, pr.b + pr.nb, lo};
+}
+
+template <typename K>
+__global__ void k_partition_split(const K* __restrict__ src, const Pair* __restrict__ pairs,
+                                  const uint64_t* __restrict__ tbegin, uint64_t npairs, TileSplit* split,
+                                  uint32_t tile, const K* __restrict__ kidx, const uint32_t* err) {
+  pdl_enter();
+  if (poisoned(err)) return;
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t total = tbegin[npairs];
+  if (i >= total) return;
+  partition_tile<K>(i, total, src, pairs, tbegin, npairs, split, tile, kidx);
+}
+
+// A small round planned by one CTA: the pair table (gen), its tile counts'
+// exclusive scan into tbegin, and every tile's split.  For rounds of at most
+// kPlanMaxPairs pairs and kPlanMaxTiles tiles (one split per thread), where
+// the three separate launches would cost more than the work.
+constexpr int kPlanNT = 1024;
+constexpr int kPlanVT = 8;
+constexpr uint64_t kPlanMaxPairs = (uint64_t)kPlanNT * kPlanVT;
+constexpr uint64_t kPlanMaxTiles = kPlanNT;
+
+template <typename K, typename Gen>
+__global__ void __launch_bounds__(kPlanNT)
+k_plan_small(Gen gen, const K* __restrict__ src, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin,
+             uint64_t npairs, TileSplit* split, uint32_t tile, const K* __restrict__ kidx, uint32_t* err) {
+  pdl_enter();
+  if (poisoned(err)) return;
+  const int tid = threadIdx.x;
+  for (uint64_t p = tid; p < npairs; p += kPlanNT) gen(p);
+  __syncthreads();                                    // the CTA's global writes are visible to itself
+  uint64_t v[kPlanVT];
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kPlanVT; ++k) {                 // blocked: thread t owns slots [t VT, t VT + VT)
+    const uint64_t idx = (uint64_t)tid * kPlanVT + k;
+    v[k] = idx < npairs ? tcount[idx] : 0;
+    acc += v[k];
+  }
+  uint64_t total;
+  uint64_t pre = block_exclusive_scan(acc, &total);
+#pragma unroll
+  for (int k = 0; k < kPlanVT; ++k) {
+    const uint64_t idx = (uint64_t)tid * kPlanVT + k;
+    if (idx < npairs) tbegin[idx] = pre;
+    pre += v[k];
+  }
+  if (tid == 0) tbegin[npairs] = total;
+  if (total > kPlanMaxTiles) {                        // the host's bound did not hold: never expected
+    if (tid == 0) atomicOr(err, kErrBadTile);
+    return;
+  }
+  __syncthreads();
+  if ((uint64_t)tid < total) partition_tile<K>(tid, total, src, pairs, tbegin, npairs, split, tile, kidx);
 }
 
 // CTAs per SM the merge tile is compiled for (0: the compiler's choice).
@@ -1108,40 +1209,6 @@ k_merge4(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __res
 // Device-wide exclusive scan of uint64 (reduce, scan of chunk sums, scan).
 // out[i] = sum_{j<i} in[j] for i in [0, m]; out[m] is the total.
 // ---------------------------------------------------------------------------
-
-// Exclusive scan across the CTA (blockDim.x a multiple of 32, at most 1024);
-// every thread also gets the CTA total.  Ends with a barrier, so it may be
-// called back to back.
-__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t x, uint64_t* total) {
-  __shared__ uint64_t warp_sums[33];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t inc = x;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint64_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-    if (lane >= d) inc += y;
-  }
-  if (lane == 31) warp_sums[warp] = inc;
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  if (warp == 0) {
-    uint64_t v = lane < nw ? warp_sums[lane] : 0;
-    uint64_t vi = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      uint64_t y = __shfl_up_sync(0xFFFFFFFFu, vi, d);
-      if (lane >= d) vi += y;
-    }
-    if (lane < nw) warp_sums[lane] = vi - v;
-    if (lane == 31) warp_sums[32] = vi;
-  }
-  __syncthreads();
-  uint64_t res = warp_sums[warp] + inc - x;
-  uint64_t tot = warp_sums[32];
-  __syncthreads();
-  if (total) *total = tot;
-  return res;
-}
 
 static __global__ void __launch_bounds__(kScanNT)
 k_scan_reduce(const uint64_t* __restrict__ in, uint64_t m, uint64_t* __restrict__ sums) {

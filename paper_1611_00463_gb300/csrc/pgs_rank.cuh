@@ -280,11 +280,8 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
         step *= 4;
         levels -= 2;
       } else {
-        PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 32ull * k, [&] {
-          klaunch(st, c.pdl, k_pairs_bucket_lists, grid_for(k, 256), 256, 0, b.pairs, b.tcount, g, b.off, 0, k, step, mtile);
-        }));
-        PGS_TRY((merge_round<K, V>(c, src, vsrc, kd, vd, k, n, b, last ? f32 : 0, 6, kidx, io,
-                                   ceil_div(k, 2ull * step) + 1)));
+        PGS_TRY((merge_round<K, V>(c, GenBucketLists{b.pairs, b.tcount, g, b.off, 0, step, mtile}, src, vsrc, kd,
+                                   vd, k, n, b, last ? f32 : 0, 6, kidx, io, ceil_div(k, 2ull * step) + 1)));
         step *= 2;
         levels -= 1;
       }
