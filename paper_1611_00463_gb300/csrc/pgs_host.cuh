@@ -215,6 +215,7 @@ struct Buffers {
   uint64_t *samp_counts, *samp_off;
   Pair* pairs; uint64_t *tcount, *tbegin;
   TileSplit* split;
+  TileJob* jobs;             // the same storage as split: a round uses one or the other
   void* kidx;                // key index of the last pass: the key at every 64th position
   Quad* quads; uint64_t *tcount4, *tbegin4; Split4* splits4; void* xs;   // four-way rounds
   uint64_t max_tiles4 = 0;
@@ -264,6 +265,7 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->tcount = c.take<uint64_t>(sh.max_pairs);
   b->tbegin = c.take<uint64_t>(sh.max_pairs + 1);
   b->split = c.take<TileSplit>(sh.max_tiles);
+  b->jobs = reinterpret_cast<TileJob*>(b->split);
   b->kidx = c.take<char>(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) * sh.w);
   if (sh.four) {
     b->quads = c.take<Quad>(sh.max_quads);
@@ -499,10 +501,10 @@ inline int set_smem_attrs() {
 
 template <typename K, bool V, int NT, int VT>
 inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t tiles,
-                              const Buffers& b, const uint64_t* total, int f32_out, K* idx_out, uint64_t wait_ns,
-                              int inject, cudaStream_t st, bool pdl) {
+                              const Buffers& b, bool jobs, const uint64_t* total, int f32_out, K* idx_out,
+                              uint64_t wait_ns, int inject, cudaStream_t st, bool pdl) {
   klaunch(st, pdl, k_merge_tile<K, V, NT, VT>, (unsigned)tiles, NT, Merge2Layout<K, V, NT, VT>::bytes, ks, vs, kd, vd,
-          b.split, total, f32_out, b.err, idx_out, wait_ns, inject);
+          jobs ? nullptr : b.split, jobs ? b.jobs : nullptr, total, f32_out, b.err, idx_out, wait_ns, inject);
 }
 
 // One pairwise merge round over pairs already described in b.pairs / b.tcount
@@ -519,11 +521,13 @@ inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, 
   const MergeShape ms = kMergeShapes[c.variant];
   const uint32_t tile = (uint32_t)(ms.nt * ms.vt);
   const uint64_t tiles_ub = ceil_div(len, tile) + std::min(npairs, live_pairs);
-  if (npairs <= kPlanMaxPairs && tiles_ub <= kPlanMaxTiles) {
-    // A small round: descriptors, their scan and the splits in one CTA.
+  const bool small = npairs <= kPlanMaxPairs && tiles_ub <= kPlanMaxTiles;
+  if (small) {
+    // A small round: descriptors, their scan and one job per tile in one CTA;
+    // each merge CTA then finds its own splits.
     PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * tiles_ub + 56 * npairs, [&] {
-      klaunch(c.st, c.pdl, k_plan_small<K, Gen>, 1, kPlanNT, 0, gen, ks, b.pairs, b.tcount, b.tbegin, npairs,
-              b.split, tile, idx_in, b.err);
+      klaunch(c.st, c.pdl, k_plan_jobs<Gen>, 1, kPlanNT, 0, gen, b.pairs, b.tcount, b.tbegin, npairs, b.jobs, tile,
+              b.err);
     }));
   } else {
     if (!std::is_same<Gen, GenNone>::value)
@@ -543,7 +547,7 @@ inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, 
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     switch (c.variant) {
 #define PGS_MERGE_SHAPE(i) kMergeShapes[i].nt, kMergeShapes[i].vt
-#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, total, f32_out, idx_out, c.wait_ns, inject, c.st, c.pdl
+#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, small, total, f32_out, idx_out, c.wait_ns, inject, c.st, c.pdl
       case 1: launch_merge_tile<K, V, PGS_MERGE_SHAPE(1)>(PGS_MERGE_ARGS); break;
       case 2: launch_merge_tile<K, V, PGS_MERGE_SHAPE(2)>(PGS_MERGE_ARGS); break;
       case 3: launch_merge_tile<K, V, PGS_MERGE_SHAPE(3)>(PGS_MERGE_ARGS); break;

@@ -306,8 +306,8 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t x, uint64_t* t
 
 // Pair descriptors of one pairwise round.  A generator writes slot p of the
 // round's pair table (pairs[p], and its tile count at merge tile `tile`);
-// k_pairs runs one generator over all slots, and k_plan_small (below) runs it
-// inside the single CTA that also scans and splits a small round.
+// k_pairs runs one generator over all slots, and k_plan_jobs (below) runs it
+// inside the single CTA that also scans a small round and writes its tile jobs.
 
 // Run formation (step 1): inside every run, blocks [j 2w, j 2w + w) and
 // [j 2w + w, (j+1) 2w) merge; a run that is already one list is copied.
@@ -505,6 +505,16 @@ struct TileSplit {
   uint64_t pair;          // index of the pair the tile belongs to
 };
 
+// A merge tile described by its pair and its first diagonal only: the merge
+// CTA finds the splits at both ends itself (warp_merge_path).  Small rounds
+// use it, so that their planning launch does no search.
+struct TileJob {
+  uint64_t a, na, b, nb;  // the pair's A and B lists
+  uint64_t out;           // where the pair's output starts
+  uint64_t d0;            // the tile's first output within the pair
+};
+static_assert(sizeof(TileJob) == sizeof(TileSplit), "jobs and splits share a buffer");
+
 // Merge path of a and b at diagonal d, searched only inside [lo, hi], which
 // must hold the answer.
 template <typename K>
@@ -513,6 +523,32 @@ __device__ __forceinline__ uint64_t merge_path_in(const K* a, const K* b, uint64
     const uint64_t mid = (lo + hi) >> 1;
     if (a[mid] <= b[d - 1 - mid]) lo = mid + 1;
     else hi = mid;
+  }
+  return lo;
+}
+
+// merge_path by one warp: each step the 32 lanes test 32 evenly spaced
+// candidates at once (two independent loads per lane), so a range of m
+// candidates takes about log_33(m) dependent steps instead of log_2(m); the
+// test is the one of merge_path, so the answer is the same.  Every lane of the
+// warp must call it with the same arguments; every lane gets the answer.
+template <typename K>
+__device__ __forceinline__ uint64_t warp_merge_path(const K* a, uint64_t na, const K* b, uint64_t nb, uint64_t d) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint64_t lo = d > nb ? d - nb : 0;                   // the answer lies in [lo, hi]
+  uint64_t hi = d < na ? d : na;
+  while (hi > lo) {
+    const uint64_t span = hi - lo;
+    const bool last = span <= 32;
+    // candidates strictly increasing in the lane, all inside [lo, hi)
+    const uint64_t m = last ? lo + lane : lo + ((uint64_t)(lane + 1) * span) / 33;
+    const bool take = (!last || lane < span) && (a[m] <= b[d - 1 - m]);
+    const int c = __popc(__ballot_sync(0xFFFFFFFFu, take));   // the test holds on a prefix of the lanes
+    if (last) return lo + (uint64_t)c;
+    const uint64_t below = __shfl_sync(0xFFFFFFFFu, m, c > 0 ? c - 1 : 0);
+    const uint64_t above = __shfl_sync(0xFFFFFFFFu, m, c < 32 ? c : 31);
+    if (c > 0) lo = below + 1;
+    if (c < 32) hi = above;
   }
   return lo;
 }
@@ -623,20 +659,22 @@ __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restr
 }
 
 // A small round planned by one CTA: the pair table (gen), its tile counts'
-// exclusive scan into tbegin, and every tile's split.  For rounds of at most
-// kPlanMaxPairs pairs and kPlanMaxTiles tiles (one split per thread), where
-// the three separate launches would cost more than the work.
+// exclusive scan into tbegin, and one job per tile (its pair and first
+// diagonal; the merge CTA searches its own splits).  For rounds of at most
+// kPlanMaxPairs pairs and kPlanMaxTiles tiles, where separate launches for
+// the table, the scan and the splits would cost more than the work.
 constexpr int kPlanNT = 1024;
 constexpr int kPlanVT = 8;
 constexpr uint64_t kPlanMaxPairs = (uint64_t)kPlanNT * kPlanVT;
 constexpr uint64_t kPlanMaxTiles = kPlanNT;
 
-template <typename K, typename Gen>
+template <typename Gen>
 __global__ void __launch_bounds__(kPlanNT)
-k_plan_small(Gen gen, const K* __restrict__ src, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin,
-             uint64_t npairs, TileSplit* split, uint32_t tile, const K* __restrict__ kidx, uint32_t* err) {
+k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin, uint64_t npairs, TileJob* jobs,
+            uint32_t tile, uint32_t* err) {
   pdl_enter();
   if (poisoned(err)) return;
+  __shared__ uint16_t s_tb[kPlanMaxPairs + 1];         // tbegin, while the total fits kPlanMaxTiles
   const int tid = threadIdx.x;
   for (uint64_t p = tid; p < npairs; p += kPlanNT) gen(p);
   __syncthreads();                                    // the CTA's global writes are visible to itself
@@ -650,19 +688,33 @@ k_plan_small(Gen gen, const K* __restrict__ src, const Pair* pairs, const uint64
   }
   uint64_t total;
   uint64_t pre = block_exclusive_scan(acc, &total);
-#pragma unroll
-  for (int k = 0; k < kPlanVT; ++k) {
-    const uint64_t idx = (uint64_t)tid * kPlanVT + k;
-    if (idx < npairs) tbegin[idx] = pre;
-    pre += v[k];
-  }
-  if (tid == 0) tbegin[npairs] = total;
   if (total > kPlanMaxTiles) {                        // the host's bound did not hold: never expected
     if (tid == 0) atomicOr(err, kErrBadTile);
     return;
   }
+#pragma unroll
+  for (int k = 0; k < kPlanVT; ++k) {
+    const uint64_t idx = (uint64_t)tid * kPlanVT + k;
+    if (idx < npairs) {
+      tbegin[idx] = pre;
+      s_tb[idx] = (uint16_t)pre;
+    }
+    pre += v[k];
+  }
+  if (tid == 0) {
+    tbegin[npairs] = total;
+    s_tb[npairs] = (uint16_t)total;
+  }
   __syncthreads();
-  if ((uint64_t)tid < total) partition_tile<K>(tid, total, src, pairs, tbegin, npairs, split, tile, kidx);
+  if ((uint64_t)tid < total) {
+    uint32_t lo = 0, hi = (uint32_t)npairs;             // the last slot whose first tile is <= tid
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (s_tb[mid] <= tid) lo = mid; else hi = mid;
+    }
+    const Pair pr = pairs[lo];
+    jobs[tid] = TileJob{pr.a, pr.na, pr.b, pr.nb, pr.out, (uint64_t)(tid - s_tb[lo]) * tile};
+  }
 }
 
 // CTAs per SM the merge tile is compiled for (0: the compiler's choice).
@@ -677,8 +729,9 @@ constexpr int merge_min_blocks() { return (sizeof(K) == 4 && NT == 128 && VT == 
 template <typename K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT, (merge_min_blocks<K, NT, VT>()))
 k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
-             uint32_t* __restrict__ vdst, const TileSplit* __restrict__ split, const uint64_t* __restrict__ total_ptr,
-             int f32_out, uint32_t* err, K* __restrict__ kidx, uint64_t wait_ns, int inject_timeout) {
+             uint32_t* __restrict__ vdst, const TileSplit* __restrict__ split, const TileJob* __restrict__ jobs,
+             const uint64_t* __restrict__ total_ptr, int f32_out, uint32_t* err, K* __restrict__ kidx,
+             uint64_t wait_ns, int inject_timeout) {
   pdl_enter();
   using L = Merge2Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -687,22 +740,54 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
   uint32_t* s_vin = reinterpret_cast<uint32_t*>(smem_raw + L::vin);
   __shared__ uint32_t s_na, s_nb;
   __shared__ uint64_t s_a, s_b, s_out;
+  __shared__ uint64_t s_cut[2];                         // job mode: A items before the tile's two ends
+  __shared__ int s_found[2];
 
   const uint64_t tile = blockIdx.x;
   const int tid = threadIdx.x;
+  static_assert(NT >= 64, "job mode searches with two warps");
+  if (jobs) {
+    // Warp 0 finds the split at the tile's first diagonal, warp 1 at its end.
+    // A warp that saw no failed kernel reads a job table the plan wrote for
+    // this round (the error word only ever gains bits).
+    if (tid < 64) {
+      const int w = tid >> 5;
+      const bool live = tile < *total_ptr && !poisoned(err);
+      if (live) {
+        const TileJob jb = jobs[tile];
+        const uint64_t n = jb.na + jb.nb;
+        const uint64_t d = w == 0 ? jb.d0 : umin(jb.d0 + (uint64_t)L::T, n);
+        const uint64_t cut = warp_merge_path<K>(ksrc + jb.a, jb.na, ksrc + jb.b, jb.nb, d);
+        if ((tid & 31) == 0) s_cut[w] = cut;
+      }
+      if ((tid & 31) == 0) s_found[w] = live ? 1 : 0;
+    }
+    __syncthreads();
+  }
   if (tid == 0) {
     const uint64_t total = *total_ptr;
     uint32_t na = 0, nb = 0;
     TileSplit t{};
-    if (tile < total && !poisoned(err)) {
-      t = split[tile];
-      bool same = false;
-      TileSplit nx{};
-      if (tile + 1 < total) {
-        nx = split[tile + 1];
-        same = nx.pair == t.pair;
+    const bool live = jobs ? (s_found[0] && s_found[1]) : (tile < total && !poisoned(err));
+    if (live) {
+      uint64_t a_hi, b_hi;
+      if (jobs) {
+        const TileJob jb = jobs[tile];
+        const uint64_t d1 = umin(jb.d0 + (uint64_t)L::T, jb.na + jb.nb);
+        t = TileSplit{jb.a + s_cut[0], jb.b + (jb.d0 - s_cut[0]), jb.out + jb.d0, 0, 0, 0};
+        a_hi = jb.a + s_cut[1];
+        b_hi = jb.b + (d1 - s_cut[1]);
+      } else {
+        t = split[tile];
+        bool same = false;
+        TileSplit nx{};
+        if (tile + 1 < total) {
+          nx = split[tile + 1];
+          same = nx.pair == t.pair;
+        }
+        a_hi = same ? nx.a : t.a_end;
+        b_hi = same ? nx.b : t.b_end;
       }
-      const uint64_t a_hi = same ? nx.a : t.a_end, b_hi = same ? nx.b : t.b_end;
       if (a_hi < t.a || b_hi < t.b || (a_hi - t.a) + (b_hi - t.b) > (uint64_t)L::T) {
         atomicOr(err, kErrBadTile);                     // inconsistent split: skip the tile, never copy
         t = TileSplit{};
