@@ -501,10 +501,11 @@ inline int set_smem_attrs() {
 
 template <typename K, bool V, int NT, int VT>
 inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t tiles,
-                              const Buffers& b, bool jobs, const uint64_t* total, int f32_out, K* idx_out,
-                              uint64_t wait_ns, int inject, cudaStream_t st, bool pdl) {
+                              const Buffers& b, bool jobs, const InlinePairs& ip, const uint64_t* total,
+                              int f32_out, K* idx_out, uint64_t wait_ns, int inject, cudaStream_t st, bool pdl) {
+  const bool table = jobs && ip.kind == 0;
   klaunch(st, pdl, k_merge_tile<K, V, NT, VT>, (unsigned)tiles, NT, Merge2Layout<K, V, NT, VT>::bytes, ks, vs, kd, vd,
-          jobs ? nullptr : b.split, jobs ? b.jobs : nullptr, total, f32_out, b.err, idx_out, wait_ns, inject);
+          jobs ? nullptr : b.split, table ? b.jobs : nullptr, ip, total, f32_out, b.err, idx_out, wait_ns, inject);
 }
 
 // One pairwise merge round over pairs already described in b.pairs / b.tcount
@@ -513,16 +514,27 @@ inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* 
 // idx_out: where the round writes the key index of kd (NULL: not written).
 // live_pairs: an upper bound on the slots that can hold a non-empty pair (the
 // grid covers ceil(len / tile) tiles plus one partial tile per such pair;
-// empty CTAs beyond the round's total cost launch time).
+// empty CTAs beyond the round's total cost launch time).  inl (single sorts'
+// run and sample rounds): the same pairs as gen, described by their offsets
+// table, for a small round's merge CTAs to work out themselves; inl_max_pair
+// bounds the keys of any one pair.
 template <typename K, bool V, typename Gen>
 inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, const K* idx_in = nullptr,
-                       K* idx_out = nullptr, uint64_t live_pairs = ~0ull) {
+                       K* idx_out = nullptr, uint64_t live_pairs = ~0ull, const InlinePairs* inl = nullptr,
+                       uint64_t inl_max_pair = 0) {
   const MergeShape ms = kMergeShapes[c.variant];
   const uint32_t tile = (uint32_t)(ms.nt * ms.vt);
-  const uint64_t tiles_ub = ceil_div(len, tile) + std::min(npairs, live_pairs);
+  uint64_t tiles_ub = ceil_div(len, tile) + std::min(npairs, live_pairs);
   const bool small = npairs <= kPlanMaxPairs && tiles_ub <= kPlanMaxTiles;
-  if (small) {
+  InlinePairs ip{};
+  if (small && inl) {
+    // No planning launch: grid = pair slots x the most tiles a pair can need.
+    ip = *inl;
+    ip.cm = (uint32_t)std::max<uint64_t>(1, ceil_div(inl_max_pair, tile));
+    const uint64_t slots = ip.kind == kRunPairs ? (uint64_t)ip.n_lists * ip.spr : ceil_div(ip.n_lists, 2ull * ip.step);
+    tiles_ub = slots * ip.cm;
+  } else if (small) {
     // A small round: descriptors, their scan and one job per tile in one CTA;
     // each merge CTA then finds its own splits.
     PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * tiles_ub + 56 * npairs, [&] {
@@ -547,7 +559,7 @@ inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, 
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     switch (c.variant) {
 #define PGS_MERGE_SHAPE(i) kMergeShapes[i].nt, kMergeShapes[i].vt
-#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, small, total, f32_out, idx_out, c.wait_ns, inject, c.st, c.pdl
+#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, small, ip, total, f32_out, idx_out, c.wait_ns, inject, c.st, c.pdl
       case 1: launch_merge_tile<K, V, PGS_MERGE_SHAPE(1)>(PGS_MERGE_ARGS); break;
       case 2: launch_merge_tile<K, V, PGS_MERGE_SHAPE(2)>(PGS_MERGE_ARGS); break;
       case 3: launch_merge_tile<K, V, PGS_MERGE_SHAPE(3)>(PGS_MERGE_ARGS); break;
@@ -770,10 +782,11 @@ struct Pipeline {
   }
   // A pairwise round of the pairs in b.pairs from cur to oth (left already counts it).
   template <typename Gen>
-  int pair_round(const Gen& gen, uint64_t npairs, uint64_t len, uint32_t step, uint64_t live_pairs = ~0ull) {
+  int pair_round(const Gen& gen, uint64_t npairs, uint64_t len, uint32_t step, uint64_t live_pairs = ~0ull,
+                 const InlinePairs* inl = nullptr, uint64_t inl_max_pair = 0) {
     K* io = idx_out();
     PGS_TRY((merge_round<K, V>(c, gen, cur_k, cur_v, oth_k, oth_v, npairs, len, b, f32_out(), step, idx_in(), io,
-                               live_pairs)));
+                               live_pairs, inl, inl_max_pair)));
     idx_ok = io != nullptr;
     return PGS_OK;
   }
@@ -807,7 +820,9 @@ struct Pipeline {
       } else {
         const uint64_t cmax = ceil_div(sh.maxlen, 2 * w);
         const uint64_t np = cmax * Rg;
-        PGS_TRY(pair_round(GenRuns{b.pairs, b.tcount, ro, Rg, w, cmax, mtile}, np, len, 1));
+        const InlinePairs inl{ro, w, kRunPairs, Rg, (uint32_t)cmax, 0, 0};
+        PGS_TRY(pair_round(GenRuns{b.pairs, b.tcount, ro, Rg, w, cmax, mtile}, np, len, 1, ~0ull,
+                           sh.I == 1 ? &inl : nullptr, 2 * w));
         w *= 2;
         levels -= 1;
       }
@@ -840,17 +855,29 @@ struct Pipeline {
     const uint32_t R = sh.R;
     K* sa = static_cast<K*>(b.samp_a);
     K* sb = static_cast<K*>(b.samp_b);
-    PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 16 * (uint64_t)R, [&] {
-      klaunch(st, c.pdl, k_sample_counts, grid_for(R, 256), 256, 0, g, b.samp_counts);
-    }));
-    PGS_TRY(scan_u64(c, b.samp_counts, b.samp_off, R, b.scan_sums, b.scan_sums2, 2));
-    PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 2 * sh.S * sizeof(K), [&] {
-      klaunch(st, c.pdl, k_sample<K>, grid_for(sh.S, 256), 256, 0, cur_k, g, b.samp_off, sa, sh.S);
-    }));
+    const bool single = sh.I == 1 && sh.s > 0;
+    if (single) {
+      PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 2 * sh.S * sizeof(K) + 16 * (uint64_t)R, [&] {
+        klaunch(st, c.pdl, k_sample_single<K>, grid_for(std::max<uint64_t>(sh.S, R + 1), 256), 256, 0, cur_k,
+                b.run_off, R, sh.s, sh.s >= sh.maxlen, b.samp_off, sa, sh.S);
+      }));
+    } else {
+      PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 16 * (uint64_t)R, [&] {
+        klaunch(st, c.pdl, k_sample_counts, grid_for(R, 256), 256, 0, g, b.samp_counts);
+      }));
+      PGS_TRY(scan_u64(c, b.samp_counts, b.samp_off, R, b.scan_sums, b.scan_sums2, 2));
+      PGS_TRY(launch(c, PGS_KERNEL_SAMPLE, 2, 2 * sh.S * sizeof(K), [&] {
+        klaunch(st, c.pdl, k_sample<K>, grid_for(sh.S, 256), 256, 0, cur_k, g, b.samp_off, sa, sh.S);
+      }));
+    }
     for (int k = 0; k < sh.bucket_rounds; ++k) {
       const uint32_t step = 1u << k;
+      // A single sort's runs hold at most s samples each.
+      const InlinePairs inl{b.samp_off, 0, kListPairs, R, 0, step, 0};
+      const uint64_t max_pair = std::min<uint64_t>(2ull * step, R) * std::max<uint64_t>(sh.s, 1);
       PGS_TRY((merge_round<K, false>(c, GenSampleLists{b.pairs, b.tcount, g, b.samp_off, step, mtile}, sa, nullptr,
-                                     sb, nullptr, R, sh.S, b, 0, 3)));
+                                     sb, nullptr, R, sh.S, b, 0, 3, nullptr, nullptr, ~0ull,
+                                     single ? &inl : nullptr, max_pair)));
       std::swap(sa, sb);
     }
     PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)R * sizeof(K), [&] {

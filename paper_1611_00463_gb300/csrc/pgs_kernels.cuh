@@ -515,6 +515,44 @@ struct TileJob {
 };
 static_assert(sizeof(TileJob) == sizeof(TileSplit), "jobs and splits share a buffer");
 
+// Pairs that a merge CTA of a single sort's small round works out itself from
+// an offsets table, so the round needs no planning launch.  CTA v takes tile
+// v % cm of pair slot v / cm (cm: the most tiles any pair can need):
+//  - kind kRunPairs: run formation, slot = run r x pair j (spr slots per run),
+//    blocks [j 2w, j 2w + w) and [j 2w + w, (j+1) 2w) of run [off[r], off[r+1]);
+//  - kind kListPairs: the Fig. 2 schedule over lists [off[j], off[j+1]),
+//    j < n_lists, at `step`: slot k merges list group [2 step k, 2 step k + step)
+//    with [2 step k + step, 2 step (k+1)).
+// The output of a pair starts where its first list does.
+constexpr uint32_t kRunPairs = 1, kListPairs = 2;
+struct InlinePairs {
+  const uint64_t* off;
+  uint64_t w;
+  uint32_t kind, n_lists, spr, step, cm;
+};
+
+__device__ __forceinline__ bool inline_job(const InlinePairs& ip, uint64_t v, uint64_t T, TileJob& jb) {
+  const uint64_t slot = v / ip.cm, k = v % ip.cm;
+  uint64_t lo, mid, hi;
+  if (ip.kind == kRunPairs) {
+    const uint64_t r = slot / ip.spr, j = slot % ip.spr;
+    if (r >= ip.n_lists) return false;
+    const uint64_t rs = ip.off[r], re = ip.off[r + 1];
+    lo = umin(rs + j * 2 * ip.w, re);
+    mid = umin(lo + ip.w, re);
+    hi = umin(lo + 2 * ip.w, re);
+  } else {
+    const uint64_t j = slot * 2 * ip.step;
+    if (j >= ip.n_lists) return false;
+    lo = ip.off[j];
+    mid = ip.off[umin(j + ip.step, ip.n_lists)];
+    hi = ip.off[umin(j + 2 * ip.step, ip.n_lists)];
+  }
+  if (k * T >= hi - lo) return false;
+  jb = TileJob{lo, mid - lo, mid, hi - mid, lo, k * T};
+  return true;
+}
+
 // Merge path of a and b at diagonal d, searched only inside [lo, hi], which
 // must hold the answer.
 template <typename K>
@@ -662,11 +700,14 @@ __global__ void k_partition_split(const K* __restrict__ src, const Pair* __restr
 // exclusive scan into tbegin, and one job per tile (its pair and first
 // diagonal; the merge CTA searches its own splits).  For rounds of at most
 // kPlanMaxPairs pairs and kPlanMaxTiles tiles, where separate launches for
-// the table, the scan and the splits would cost more than the work.
+// the table, the scan and the splits would cost more than the work.  (With
+// 8192 tiles a 2^24-key pairwise sort was measured 6-7 % slower than with the
+// separate partition kernel; 4096 covers the pairwise rounds of sorts up to
+// about 2^23 keys, and larger sorts merge four ways.)
 constexpr int kPlanNT = 1024;
 constexpr int kPlanVT = 8;
 constexpr uint64_t kPlanMaxPairs = (uint64_t)kPlanNT * kPlanVT;
-constexpr uint64_t kPlanMaxTiles = kPlanNT;
+constexpr uint64_t kPlanMaxTiles = 4096;             // larger rounds plan faster with the partition kernel
 
 template <typename Gen>
 __global__ void __launch_bounds__(kPlanNT)
@@ -706,14 +747,14 @@ k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin
     s_tb[npairs] = (uint16_t)total;
   }
   __syncthreads();
-  if ((uint64_t)tid < total) {
-    uint32_t lo = 0, hi = (uint32_t)npairs;             // the last slot whose first tile is <= tid
+  for (uint32_t t = tid; t < total; t += kPlanNT) {
+    uint32_t lo = 0, hi = (uint32_t)npairs;             // the last slot whose first tile is <= t
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) >> 1;
-      if (s_tb[mid] <= tid) lo = mid; else hi = mid;
+      if (s_tb[mid] <= t) lo = mid; else hi = mid;
     }
     const Pair pr = pairs[lo];
-    jobs[tid] = TileJob{pr.a, pr.na, pr.b, pr.nb, pr.out, (uint64_t)(tid - s_tb[lo]) * tile};
+    jobs[t] = TileJob{pr.a, pr.na, pr.b, pr.nb, pr.out, (uint64_t)(t - s_tb[lo]) * tile};
   }
 }
 
@@ -730,8 +771,8 @@ template <typename K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT, (merge_min_blocks<K, NT, VT>()))
 k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __restrict__ kdst,
              uint32_t* __restrict__ vdst, const TileSplit* __restrict__ split, const TileJob* __restrict__ jobs,
-             const uint64_t* __restrict__ total_ptr, int f32_out, uint32_t* err, K* __restrict__ kidx,
-             uint64_t wait_ns, int inject_timeout) {
+             InlinePairs ip, const uint64_t* __restrict__ total_ptr, int f32_out, uint32_t* err,
+             K* __restrict__ kidx, uint64_t wait_ns, int inject_timeout) {
   pdl_enter();
   using L = Merge2Layout<K, VALS, NT, VT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -746,15 +787,21 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
   const uint64_t tile = blockIdx.x;
   const int tid = threadIdx.x;
   static_assert(NT >= 64, "job mode searches with two warps");
-  if (jobs) {
+  const bool job_mode = jobs != nullptr || ip.kind != 0;
+  TileJob jb{};
+  if (job_mode) {
     // Warp 0 finds the split at the tile's first diagonal, warp 1 at its end.
     // A warp that saw no failed kernel reads a job table the plan wrote for
     // this round (the error word only ever gains bits).
     if (tid < 64) {
       const int w = tid >> 5;
-      const bool live = tile < *total_ptr && !poisoned(err);
+      bool live = !poisoned(err);
       if (live) {
-        const TileJob jb = jobs[tile];
+        if (ip.kind != 0) live = inline_job(ip, tile, (uint64_t)L::T, jb);
+        else if (tile < *total_ptr) jb = jobs[tile];
+        else live = false;
+      }
+      if (live) {
         const uint64_t n = jb.na + jb.nb;
         const uint64_t d = w == 0 ? jb.d0 : umin(jb.d0 + (uint64_t)L::T, n);
         const uint64_t cut = warp_merge_path<K>(ksrc + jb.a, jb.na, ksrc + jb.b, jb.nb, d);
@@ -765,14 +812,13 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
     __syncthreads();
   }
   if (tid == 0) {
-    const uint64_t total = *total_ptr;
+    const uint64_t total = job_mode ? 0 : *total_ptr;
     uint32_t na = 0, nb = 0;
     TileSplit t{};
-    const bool live = jobs ? (s_found[0] && s_found[1]) : (tile < total && !poisoned(err));
+    const bool live = job_mode ? (s_found[0] && s_found[1]) : (tile < total && !poisoned(err));
     if (live) {
       uint64_t a_hi, b_hi;
-      if (jobs) {
-        const TileJob jb = jobs[tile];
+      if (job_mode) {                                   // thread 0 holds warp 0's job
         const uint64_t d1 = umin(jb.d0 + (uint64_t)L::T, jb.na + jb.nb);
         t = TileSplit{jb.a + s_cut[0], jb.b + (jb.d0 - s_cut[0]), jb.out + jb.d0, 0, 0, 0};
         a_hi = jb.a + s_cut[1];
@@ -1384,6 +1430,30 @@ __global__ void k_sample(const K* __restrict__ runs, Geo g, const uint64_t* __re
   const uint64_t i = j - samp_off[r], sr = samp_off[r + 1] - samp_off[r];
   const uint64_t rs = g.run_off[r], nr = g.run_off[r + 1] - rs;
   const uint64_t pos = (uint64_t)(((unsigned __int128)(i + 1) * nr) / sr) - 1;   // exact for any s_r, n_r
+  samples[j] = runs[rs + pos];
+}
+
+// Step 2 of a single sort in one launch.  Run r gives min(s, n_r) samples,
+// and its length n_r is floor(n / P) or ceil(n / P): with s < ceil(n / P)
+// every run gives s (s <= floor(n / P)) and its samples start at r s; with
+// s >= ceil(n / P) every key is a sample and they start at run_off[r].  The
+// positions are k_sample's.  Thread j < S writes sample j, thread r <= R
+// writes samp_off[r].
+template <typename K>
+__global__ void k_sample_single(const K* __restrict__ runs, const uint64_t* __restrict__ run_off, uint32_t R,
+                                uint64_t s, bool all_keys, uint64_t* __restrict__ samp_off, K* __restrict__ samples,
+                                uint64_t S) {
+  pdl_enter();
+  const uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (j <= R) samp_off[j] = all_keys ? run_off[j] : j * s;
+  if (j >= S) return;
+  if (all_keys) {
+    samples[j] = runs[j];
+    return;
+  }
+  const uint64_t r = j / s, i = j % s;
+  const uint64_t rs = run_off[r], nr = run_off[r + 1] - rs;
+  const uint64_t pos = (uint64_t)(((unsigned __int128)(i + 1) * nr) / s) - 1;
   samples[j] = runs[rs + pos];
 }
 
