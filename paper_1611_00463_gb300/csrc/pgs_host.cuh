@@ -148,6 +148,9 @@ struct Shape {
 // (measured on u32 and u64 keys at 2^20 .. 2^26: pairwise 1-4 % faster up to
 // 2^22 keys, four-way 5-16 % faster from 2^24).
 constexpr uint64_t kFourWayMinKeys = 1ull << 23;
+// Cut searches by one warp per slot up to this many (run, splitter) slots:
+// 12.5 -> 6.0 us at 256 slots, but 0.04 -> 0.49 ms at 2^20 slots.
+constexpr uint64_t kCutWarpMaxSlots = 4096;
 
 inline bool use_four_way(uint64_t n, const Options& o) {
   return o.merge_ways == 4 || (o.merge_ways == 0 && n >= kFourWayMinKeys);
@@ -880,11 +883,7 @@ struct Pipeline {
                                      single ? &inl : nullptr, max_pair)));
       std::swap(sa, sb);
     }
-    PGS_TRY(launch(c, PGS_KERNEL_SPLITTERS, 3, 2 * (uint64_t)R * sizeof(K), [&] {
-      klaunch(st, c.pdl, k_pick_splitters<K>, grid_for(R, 256), 256, 0, sa, g, b.samp_off, static_cast<K*>(b.spl),
-                                                            static_cast<K*>(o.splitters), f32);
-    }));
-    *sorted_sample = sa;
+    *sorted_sample = sa;                                  // the pick of every (S/P)-th is fused into cuts()
     return PGS_OK;
   }
 
@@ -893,18 +892,26 @@ struct Pipeline {
   // judge.  Then the receive offset of every (bucket, run) segment (IV-C).
   int cuts(const K* sorted_sample) {
     const uint32_t R = sh.R;
-    PGS_TRY(launch(c, PGS_KERNEL_CUT_SEARCH, 4, 16 * sh.Q, [&] {
-      klaunch(st, c.pdl, k_cut_search<K>, grid_for(sh.Q, 256), 256, 0, cur_k, g, sh.Q, static_cast<const K*>(b.spl), b.lb,
-                                                           b.cnt);
-    }));
-    PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * (uint64_t)R, [&] {
-      klaunch(st, c.pdl, k_cut_edges, grid_for(R, 256), 256, 0, g, b.cut, b.e);
+    PGS_TRY(launch(c, PGS_KERNEL_CUT_SEARCH, 4, 16 * sh.Q + 2 * (uint64_t)R * sizeof(K), [&] {
+      K* spl = static_cast<K*>(b.spl);
+      K* user = static_cast<K*>(o.splitters);
+      if (sh.Q <= kCutWarpMaxSlots)
+        klaunch(st, c.pdl, k_cut_search<K, true>, grid_for(32 * sh.Q, 256), 256, 0, cur_k, g, sh.Q, sorted_sample,
+                b.samp_off, spl, user, f32, b.lb, b.cnt, b.cut, b.e);
+      else
+        klaunch(st, c.pdl, k_cut_search<K, false>, grid_for(sh.Q, 256), 256, 0, cur_k, g, sh.Q, sorted_sample,
+                b.samp_off, spl, user, f32, b.lb, b.cnt, b.cut, b.e);
     }));
     PGS_TRY(launch(c, PGS_KERNEL_INVESTIGATOR, 4, 24 * sh.MAT, [&] {
       klaunch(st, c.pdl, k_investigator<K>, R, 256, 0, b.lb, b.cnt, static_cast<const K*>(b.spl), g, o.investigator, b.cut,
                                            b.e);
     }));
     if (sh.learned) PGS_TRY((learned_cuts<K>(sh, o, sorted_sample, cur_k, c, b)));
+    if (sh.Q <= kSizesMax) {
+      return launch(c, PGS_KERNEL_OFFSETS, 5, 40 * sh.Q, [&] {
+        klaunch(st, c.pdl, k_bucket_offsets, 1, kSizesNT, 0, g, sh.Q, b.cut, b.sizes, b.seg_src, b.off);
+      });
+    }
     PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 32 * sh.Q, [&] {
       klaunch(st, c.pdl, k_bucket_sizes, grid_for(sh.Q, 256), 256, 0, g, sh.Q, b.cut, b.sizes, b.seg_src);
     }));

@@ -565,23 +565,22 @@ __device__ __forceinline__ uint64_t merge_path_in(const K* a, const K* b, uint64
   return lo;
 }
 
-// merge_path by one warp: each step the 32 lanes test 32 evenly spaced
-// candidates at once (two independent loads per lane), so a range of m
-// candidates takes about log_33(m) dependent steps instead of log_2(m); the
-// test is the one of merge_path, so the answer is the same.  Every lane of the
-// warp must call it with the same arguments; every lane gets the answer.
-template <typename K>
-__device__ __forceinline__ uint64_t warp_merge_path(const K* a, uint64_t na, const K* b, uint64_t nb, uint64_t d) {
+// The first index in [lo, hi) whose test fails, for a test that holds on a
+// prefix of [lo, hi) (hi if it holds everywhere), found by one warp: each
+// step the 32 lanes evaluate 32 evenly spaced candidates at once, so a range
+// of m candidates takes about log_33(m) dependent steps instead of log_2(m).
+// Every lane of the warp must call it with the same range and test; every
+// lane gets the answer.
+template <typename Test>
+__device__ __forceinline__ uint64_t warp_partition_point(uint64_t lo, uint64_t hi, const Test& test) {
   const uint32_t lane = threadIdx.x & 31u;
-  uint64_t lo = d > nb ? d - nb : 0;                   // the answer lies in [lo, hi]
-  uint64_t hi = d < na ? d : na;
   while (hi > lo) {
     const uint64_t span = hi - lo;
     const bool last = span <= 32;
     // candidates strictly increasing in the lane, all inside [lo, hi)
     const uint64_t m = last ? lo + lane : lo + ((uint64_t)(lane + 1) * span) / 33;
-    const bool take = (!last || lane < span) && (a[m] <= b[d - 1 - m]);
-    const int c = __popc(__ballot_sync(0xFFFFFFFFu, take));   // the test holds on a prefix of the lanes
+    const bool holds = (!last || lane < span) && test(m);
+    const int c = __popc(__ballot_sync(0xFFFFFFFFu, holds));   // the test holds on a prefix of the lanes
     if (last) return lo + (uint64_t)c;
     const uint64_t below = __shfl_sync(0xFFFFFFFFu, m, c > 0 ? c - 1 : 0);
     const uint64_t above = __shfl_sync(0xFFFFFFFFu, m, c < 32 ? c : 31);
@@ -589,6 +588,13 @@ __device__ __forceinline__ uint64_t warp_merge_path(const K* a, uint64_t na, con
     if (c < 32) hi = above;
   }
   return lo;
+}
+
+// merge_path by one warp (the same test, so the same answer).
+template <typename K>
+__device__ __forceinline__ uint64_t warp_merge_path(const K* a, uint64_t na, const K* b, uint64_t nb, uint64_t d) {
+  return warp_partition_point(d > nb ? d - nb : 0, d < na ? d : na,
+                              [&](uint64_t m) { return a[m] <= b[d - 1 - m]; });
 }
 
 __device__ __forceinline__ int64_t ceil_div64(int64_t t) {            // ceil(t / 64) for any sign
@@ -1457,26 +1463,7 @@ __global__ void k_sample_single(const K* __restrict__ runs, const uint64_t* __re
   samples[j] = runs[rs + pos];
 }
 
-// Step 3 of Section IV: with S_i samples, t_b = sorted sample at index
-// floor(b S_i / P_i) - 1, b = 1..P_i-1.  t is indexed by global run (slot b of
-// instance i is R0[i] + b; slot 0 unused).
-template <typename K>
-__global__ void k_pick_splitters(const K* __restrict__ sorted, Geo g, const uint64_t* __restrict__ samp_off, K* t,
-                                 K* user_out, int f32) {
-  pdl_enter();
-  uint64_t beta = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (beta >= g.R) return;
-  const uint32_t i = g.run_inst[beta];
-  const uint32_t r0 = g.R0[i];
-  const uint64_t b = beta - r0, P = g.P[i];
-  if (b == 0) return;
-  const uint64_t s0 = samp_off[r0], S = samp_off[r0 + P] - s0;
-  const K v = sorted[s0 + (b * S) / P - 1];
-  t[beta] = v;
-  if (user_out && g.I == 1) user_out[b - 1] = from_order<K>(v, f32);
-}
-
-// The same pick on one sorted sample of m keys: out[b-1] = sorted[floor(b m / P) - 1].
+// Step 3's pick on one sorted sample of m keys: out[b-1] = sorted[floor(b m / P) - 1], b = 1..P-1.
 template <typename K>
 __global__ void k_pick_splitters_flat(const K* __restrict__ sorted, uint64_t m, uint32_t P, K* out, int f32) {
   pdl_enter();
@@ -1490,31 +1477,72 @@ __global__ void k_pick_splitters_flat(const K* __restrict__ sorted, uint64_t m, 
 // ---------------------------------------------------------------------------
 
 // lb[r][b] = #{x in run r : x < t_b}, cnt[r][b] = #{x in run r : x == t_b},
-// b = 1..P-1, for every run of every instance (index space: the P x P
-// segments; entries with b = 0 do nothing).
-template <typename K>
-__global__ void k_cut_search(const K* __restrict__ runs, Geo g, uint64_t Q, const K* __restrict__ t,
-                             uint64_t* lb, uint64_t* cnt) {
+// b = 1..P-1, for every run of every instance; index space: the P x P
+// segments, one warp or one thread each (two searches).  Step 3's pick
+// is fused in: every warp reads its t_b from the sorted sample, and run 0's
+// warps store it (and the caller's copy of a single sort's splitters).  The
+// slots b = 0 write run r's fixed cuts cut[r][0] = 0 and cut[r][P] = n_r, and
+// run 0's also e[0] = 0 and e[P] = n_i.  t is indexed by global run (slot b
+// of instance i is R0[i] + b; slot 0 unused).
+// The first index in [lo, hi) whose test fails (test true on a prefix), by
+// one thread's bisection.
+template <typename Test>
+__device__ __forceinline__ uint64_t partition_point(uint64_t lo, uint64_t hi, const Test& test) {
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (test(mid)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// WARP: one warp per slot with warp_partition_point (few slots: the searches'
+// dependent loads bound the time); else one thread per slot with bisection
+// (many slots: a warp's 32 searches share its load instructions).
+template <typename K, bool WARP>
+__global__ void k_cut_search(const K* __restrict__ runs, Geo g, uint64_t Q, const K* __restrict__ sorted,
+                             const uint64_t* __restrict__ samp_off, K* t, K* user_out, int f32, uint64_t* lb,
+                             uint64_t* cnt, uint64_t* cut, uint64_t* e) {
   pdl_enter();
-  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t gt = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t q = WARP ? gt >> 5 : gt;
   if (q >= Q) return;
+  const bool lead = WARP ? (threadIdx.x & 31u) == 0 : true;
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
   const uint64_t P = g.P[i];
   const uint64_t local = q - g.seg[i];
   const uint64_t rl = local / P, b = local % P;
-  if (b == 0) return;
   const uint32_t r0 = g.R0[i];
   const uint64_t rs = g.run_off[r0 + rl], nr = g.run_off[r0 + rl + 1] - rs;
+  if (b == 0) {                                       // the fixed cuts of run rl: 0 and n_r
+    if (lead) {
+      uint64_t* row = cut + g.mat[i] + rl * (P + 1);
+      row[0] = 0;
+      row[P] = nr;
+      if (rl == 0) {
+        e[r0 + i] = 0;
+        e[r0 + i + P] = g.koff[i + 1] - g.koff[i];
+      }
+    }
+    return;
+  }
+  // Step 3's pick: t_b = the sorted sample at floor(b S / P) - 1.
+  const uint64_t s0 = samp_off[r0], S = samp_off[r0 + P] - s0;
+  const K v = sorted[s0 + (b * S) / P - 1];
+  if (rl == 0 && lead) {
+    t[r0 + b] = v;
+    if (user_out && g.I == 1) user_out[b - 1] = from_order<K>(v, f32);
+  }
   const K* x = runs + rs;
-  const K v = t[r0 + b];
-  uint64_t lo = 0, hi = nr;
-  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] < v) lo = mid + 1; else hi = mid; }
-  const uint64_t l = lo;
-  hi = nr;
-  while (lo < hi) { uint64_t mid = (lo + hi) >> 1; if (x[mid] <= v) lo = mid + 1; else hi = mid; }
-  const uint64_t at = g.mat[i] + rl * (P + 1) + b;
-  lb[at] = l;
-  cnt[at] = lo - l;
+  auto below = [&](uint64_t m) { return x[m] < v; };
+  auto not_above = [&](uint64_t m) { return x[m] <= v; };
+  const uint64_t l = WARP ? warp_partition_point(0, nr, below) : partition_point(0, nr, below);
+  const uint64_t u = WARP ? warp_partition_point(l, nr, not_above) : partition_point(l, nr, not_above);
+  if (lead) {
+    const uint64_t at = g.mat[i] + rl * (P + 1) + b;
+    lb[at] = l;
+    cnt[at] = u - l;
+  }
 }
 
 // One CTA per splitter b = 1..P_i-1 of every instance (CTAs of slot b = 0
@@ -1631,18 +1659,54 @@ static __global__ void k_cut_edges(Geo g, uint64_t* cut, uint64_t* e) {
 
 // Segments (bucket b, run r) of every instance, bucket-major: their sizes
 // cut[r][b+1] - cut[r][b] and the global position where they start.
-static __global__ void k_bucket_sizes(Geo g, uint64_t Q, const uint64_t* __restrict__ cut, uint64_t* sizes,
-                                      uint64_t* src) {
-  pdl_enter();
-  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (q >= Q) return;
+__device__ __forceinline__ uint64_t segment_size(const Geo& g, uint64_t q, const uint64_t* __restrict__ cut,
+                                                 uint64_t* src) {
   const uint32_t i = last_le<uint64_t>(g.seg, g.I, q);
   const uint64_t P = g.P[i];
   const uint64_t local = q - g.seg[i];
   const uint64_t b = local / P, rl = local % P;
   const uint64_t* c = cut + g.mat[i] + rl * (P + 1);
-  sizes[q] = c[b + 1] - c[b];
   src[q] = g.run_off[g.R0[i] + rl] + c[b];
+  return c[b + 1] - c[b];
+}
+
+static __global__ void k_bucket_sizes(Geo g, uint64_t Q, const uint64_t* __restrict__ cut, uint64_t* sizes,
+                                      uint64_t* src) {
+  pdl_enter();
+  uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  sizes[q] = segment_size(g, q, cut, src);
+}
+
+// The same sizes and their exclusive scan (the receive offsets, off[Q] = n)
+// in one CTA, for at most kSizesMax segments (beyond, the CTA's dependent
+// loads cost more than a second launch: 47 us for 16384 segments).
+constexpr int kSizesNT = 1024, kSizesVT = 4;
+constexpr uint64_t kSizesMax = (uint64_t)kSizesNT * kSizesVT;
+
+static __global__ void __launch_bounds__(kSizesNT)
+k_bucket_offsets(Geo g, uint64_t Q, const uint64_t* __restrict__ cut, uint64_t* sizes, uint64_t* src,
+                 uint64_t* off) {
+  pdl_enter();
+  const uint64_t q0 = (uint64_t)threadIdx.x * kSizesVT;   // blocked: thread t owns [t VT, t VT + VT)
+  uint64_t v[kSizesVT];
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kSizesVT; ++k) {
+    v[k] = q0 + k < Q ? segment_size(g, q0 + k, cut, src) : 0;
+    acc += v[k];
+  }
+  uint64_t total;
+  uint64_t pre = block_exclusive_scan(acc, &total);
+#pragma unroll
+  for (int k = 0; k < kSizesVT; ++k) {
+    if (q0 + k < Q) {
+      sizes[q0 + k] = v[k];
+      off[q0 + k] = pre;
+    }
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) off[Q] = total;
 }
 
 // ---------------------------------------------------------------------------
