@@ -4,7 +4,8 @@
 prints, per kernel, the number of launches, the total device time and its
 share of a launch list taken with `ncu --metrics gpu__time_duration.sum --csv`;
 `--whole-sorts` drops the launches after the last sort's closing statistics
-kernel (a list cut off by `ncu -c` mid-sort).
+kernel (a list cut off by `ncu -c` mid-sort); `--last-sort` lists the last
+whole sort's launches in order instead (each kernel's time and grid).
 `python -m paper_1611_00463_gb300.profiling metrics <raw.csv> [regex]` prints
 selected metrics of a `ncu -i <rep> --page raw --csv` export, per launch.
 """
@@ -52,6 +53,21 @@ def launches(path: str, whole_sorts: bool = False) -> str:
     return "\n".join(out)
 
 
+def last_sort(path: str) -> str:
+    rows = [r for r in _csv_rows(path) if r.get("Metric Name") == "gpu__time_duration.sum"]
+    ends = [i for i, r in enumerate(rows) if kernel_label(r["Kernel Name"]) == "k_stats"]
+    if not ends:
+        return "no whole sort in the list"
+    first = ends[-2] + 1 if len(ends) > 1 else 0
+    out, total = [], 0.0
+    for r in rows[first:ends[-1] + 1]:
+        us = float(r["Metric Value"]) * (1e-3 if r["Metric Unit"] == "ns" else 1.0)
+        total += us
+        out.append(f"{kernel_label(r['Kernel Name']):44s} {us:9.2f} us  grid {r.get('Grid Size', '')}")
+    out.append(f"{'total':44s} {total:9.2f} us  {len(out)} launches")
+    return "\n".join(out)
+
+
 def metrics(path: str, pattern: str = r"dram__bytes_(read|write)\.sum$|gpu__time_duration\.sum$|"
                                       r"dram__throughput\.avg\.pct_of_peak_sustained_elapsed|"
                                       r"sm__warps_active\.avg\.pct_of_peak_sustained_active|"
@@ -74,7 +90,9 @@ def metrics(path: str, pattern: str = r"dram__bytes_(read|write)\.sum$|gpu__time
 if __name__ == "__main__":
     if len(sys.argv) < 3 or sys.argv[1] not in ("launches", "metrics"):
         sys.exit(__doc__)
-    if sys.argv[1] == "launches":
+    if sys.argv[1] == "launches" and "--last-sort" in sys.argv[3:]:
+        print(last_sort(sys.argv[2]))
+    elif sys.argv[1] == "launches":
         print(launches(sys.argv[2], "--whole-sorts" in sys.argv[3:]))
     else:
         print(metrics(sys.argv[2], *sys.argv[3:]))
