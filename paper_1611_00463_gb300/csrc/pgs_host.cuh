@@ -140,6 +140,8 @@ struct Shape {
   uint64_t max_tiles = 1;
   uint64_t scan_len = 1;
   int passes = 0;            // full passes over the keys
+  uint32_t pre_rounds = 0;   // step 6 rounds planned with the bucket offsets (single small sorts)
+  uint64_t pre_stride = 0;   // jobs per pre-planned round, at most
 };
 
 // Keys from which merge_ways 0 uses four-way passes: below it the sort is
@@ -182,6 +184,14 @@ inline void finish_shape(Shape& sh) {
   sh.max_tiles4 = ceil_div(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) + sh.max_quads, kMerge4Q) +
                   sh.max_quads + 1;
   sh.scan_len = std::max<uint64_t>(std::max<uint64_t>(sh.max_pairs, sh.Q), sh.max_quads);
+  // Step 6 planned by the offsets kernel: one instance, pairwise rounds, the
+  // offsets in one CTA and every round small at any tile shape (a round has
+  // at most ceil(n / tile) + Q tiles).
+  sh.pre_rounds = 0;
+  sh.pre_stride = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeMinTile) + sh.Q;
+  if (sh.I == 1 && !sh.four && sh.Pmax > 1 && sh.Q <= kSizesMax && sh.Q <= kPlanMaxPairs &&
+      sh.pre_stride <= kPlanMaxTiles)
+    sh.pre_rounds = (uint32_t)sh.bucket_rounds;
   auto passes_for = [&](int levels) { return sh.four ? levels / 2 + levels % 2 : levels; };
   int bucket_passes = 0;
   if (sh.Pmax > 1) bucket_passes = sh.scatter ? 1 + passes_for(sh.bucket_rounds) : 1 + passes_for(sh.bucket_rounds - 1);
@@ -219,6 +229,9 @@ struct Buffers {
   Pair* pairs; uint64_t *tcount, *tbegin;
   TileSplit* split;
   TileJob* jobs;             // the same storage as split: a round uses one or the other
+  TileJob* pre_jobs;         // step 6 rounds planned with the bucket offsets (sh.pre_rounds x sh.pre_stride)
+  uint64_t* pre_tbegin;      // their tile-count scans (sh.pre_rounds x (Q + 1))
+  Pair* pre_pairs; uint64_t* pre_tcount; uint64_t* pre_offs;   // each planning CTA's scratch
   void* kidx;                // key index of the last pass: the key at every 64th position
   Quad* quads; uint64_t *tcount4, *tbegin4; Split4* splits4; void* xs;   // four-way rounds
   uint64_t max_tiles4 = 0;
@@ -269,6 +282,11 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->tbegin = c.take<uint64_t>(sh.max_pairs + 1);
   b->split = c.take<TileSplit>(sh.max_tiles);
   b->jobs = reinterpret_cast<TileJob*>(b->split);
+  b->pre_jobs = sh.pre_rounds ? c.take<TileJob>((uint64_t)sh.pre_rounds * sh.pre_stride) : nullptr;
+  b->pre_tbegin = sh.pre_rounds ? c.take<uint64_t>((uint64_t)sh.pre_rounds * (sh.Q + 1)) : nullptr;
+  b->pre_pairs = sh.pre_rounds ? c.take<Pair>((uint64_t)sh.pre_rounds * sh.Q) : nullptr;
+  b->pre_tcount = sh.pre_rounds ? c.take<uint64_t>((uint64_t)sh.pre_rounds * sh.Q) : nullptr;
+  b->pre_offs = sh.pre_rounds ? c.take<uint64_t>((uint64_t)sh.pre_rounds * (sh.Q + 1)) : nullptr;
   b->kidx = c.take<char>(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) * sh.w);
   if (sh.four) {
     b->quads = c.take<Quad>(sh.max_quads);
@@ -504,11 +522,12 @@ inline int set_smem_attrs() {
 
 template <typename K, bool V, int NT, int VT>
 inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t tiles,
-                              const Buffers& b, bool jobs, const InlinePairs& ip, const uint64_t* total,
-                              int f32_out, K* idx_out, uint64_t wait_ns, int inject, cudaStream_t st, bool pdl) {
-  const bool table = jobs && ip.kind == 0;
+                              const Buffers& b, bool jobs, const TileJob* table, const InlinePairs& ip,
+                              const uint64_t* total, int f32_out, K* idx_out, uint64_t wait_ns, int inject,
+                              cudaStream_t st, bool pdl) {
   klaunch(st, pdl, k_merge_tile<K, V, NT, VT>, (unsigned)tiles, NT, Merge2Layout<K, V, NT, VT>::bytes, ks, vs, kd, vd,
-          jobs ? nullptr : b.split, table ? b.jobs : nullptr, ip, total, f32_out, b.err, idx_out, wait_ns, inject);
+          jobs ? nullptr : b.split, jobs && ip.kind == 0 ? table : nullptr, ip, total, f32_out, b.err, idx_out,
+          wait_ns, inject);
 }
 
 // One pairwise merge round over pairs already described in b.pairs / b.tcount
@@ -520,18 +539,27 @@ inline void launch_merge_tile(const K* ks, const uint32_t* vs, K* kd, uint32_t* 
 // empty CTAs beyond the round's total cost launch time).  inl (single sorts'
 // run and sample rounds): the same pairs as gen, described by their offsets
 // table, for a small round's merge CTAs to work out themselves; inl_max_pair
-// bounds the keys of any one pair.
+// bounds the keys of any one pair.  pre (step 6 of a single small sort): the
+// round's jobs and tile-count scan, already planned by the offsets kernel.
+struct PrePlanned { const TileJob* jobs; const uint64_t* tbegin; };
+
 template <typename K, bool V, typename Gen>
 inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, K* kd, uint32_t* vd, uint64_t npairs,
                        uint64_t len, const Buffers& b, int f32_out, uint32_t step, const K* idx_in = nullptr,
                        K* idx_out = nullptr, uint64_t live_pairs = ~0ull, const InlinePairs* inl = nullptr,
-                       uint64_t inl_max_pair = 0) {
+                       uint64_t inl_max_pair = 0, const PrePlanned* pre = nullptr) {
   const MergeShape ms = kMergeShapes[c.variant];
   const uint32_t tile = (uint32_t)(ms.nt * ms.vt);
   uint64_t tiles_ub = ceil_div(len, tile) + std::min(npairs, live_pairs);
   const bool small = npairs <= kPlanMaxPairs && tiles_ub <= kPlanMaxTiles;
   InlinePairs ip{};
-  if (small && inl) {
+  const TileJob* table = b.jobs;
+  const uint64_t* total = b.tbegin + npairs;
+  if (pre) {
+    if (!small) return PGS_ERR_CUDA;                     // plan bug: pre-planned rounds are small
+    table = pre->jobs;
+    total = pre->tbegin + npairs;
+  } else if (small && inl) {
     // No planning launch: grid = pair slots x the most tiles a pair can need.
     ip = *inl;
     ip.cm = (uint32_t)std::max<uint64_t>(1, ceil_div(inl_max_pair, tile));
@@ -556,13 +584,13 @@ inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, 
     }));
   }
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
-  const uint64_t* total = b.tbegin + npairs;
   const int inject = c.inject_timeout;
   c.inject_timeout = 0;                                   // injected into one launch only
   return launch(c, PGS_KERNEL_MERGE, step, bytes, [&] {
     switch (c.variant) {
 #define PGS_MERGE_SHAPE(i) kMergeShapes[i].nt, kMergeShapes[i].vt
-#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, small, ip, total, f32_out, idx_out, c.wait_ns, inject, c.st, c.pdl
+#define PGS_MERGE_ARGS ks, vs, kd, vd, tiles_ub, b, small, table, ip, total, f32_out, idx_out, c.wait_ns, inject, c.st, \
+                       c.pdl
       case 1: launch_merge_tile<K, V, PGS_MERGE_SHAPE(1)>(PGS_MERGE_ARGS); break;
       case 2: launch_merge_tile<K, V, PGS_MERGE_SHAPE(2)>(PGS_MERGE_ARGS); break;
       case 3: launch_merge_tile<K, V, PGS_MERGE_SHAPE(3)>(PGS_MERGE_ARGS); break;
@@ -768,6 +796,10 @@ struct Pipeline {
   uint64_t bucket_live_pairs(uint64_t Qg, uint32_t step) const {
     return ceil_div(Qg, 2ull * step) + sh.R;
   }
+  // Step 6 round r (step 2^r) as the offsets kernel planned it.
+  PrePlanned pre_planned(uint32_t r) const {
+    return PrePlanned{b.pre_jobs + (uint64_t)r * sh.pre_stride, b.pre_tbegin + (uint64_t)r * (sh.Q + 1)};
+  }
   // The key index: read while it describes the round's input; written by
   // every merge pass but the last (whose output no partition searches).
   const K* idx_in() const { return idx_ok ? static_cast<const K*>(b.kidx) : nullptr; }
@@ -786,10 +818,10 @@ struct Pipeline {
   // A pairwise round of the pairs in b.pairs from cur to oth (left already counts it).
   template <typename Gen>
   int pair_round(const Gen& gen, uint64_t npairs, uint64_t len, uint32_t step, uint64_t live_pairs = ~0ull,
-                 const InlinePairs* inl = nullptr, uint64_t inl_max_pair = 0) {
+                 const InlinePairs* inl = nullptr, uint64_t inl_max_pair = 0, const PrePlanned* pre = nullptr) {
     K* io = idx_out();
     PGS_TRY((merge_round<K, V>(c, gen, cur_k, cur_v, oth_k, oth_v, npairs, len, b, f32_out(), step, idx_in(), io,
-                               live_pairs, inl, inl_max_pair)));
+                               live_pairs, inl, inl_max_pair, pre)));
     idx_ok = io != nullptr;
     return PGS_OK;
   }
@@ -908,8 +940,11 @@ struct Pipeline {
     }));
     if (sh.learned) PGS_TRY((learned_cuts<K>(sh, o, sorted_sample, cur_k, c, b)));
     if (sh.Q <= kSizesMax) {
-      return launch(c, PGS_KERNEL_OFFSETS, 5, 40 * sh.Q, [&] {
-        klaunch(st, c.pdl, k_bucket_offsets, 1, kSizesNT, 0, g, sh.Q, b.cut, b.sizes, b.seg_src, b.off);
+      PrePlan pp{b.pre_pairs, b.pre_tcount, b.pre_tbegin, b.pre_jobs, b.pre_offs, sh.pre_stride, sh.pre_rounds,
+                 mtile, sh.scatter ? 1 : 0};
+      return launch(c, PGS_KERNEL_OFFSETS, 5, 40 * sh.Q + 48 * sh.pre_stride * sh.pre_rounds, [&] {
+        klaunch(st, c.pdl, k_bucket_offsets, std::max<uint32_t>(1, sh.pre_rounds), kSizesNT, 0, g, sh.Q, b.cut,
+                b.sizes, b.seg_src, b.off, pp, b.err);
       });
     }
     PGS_TRY(launch(c, PGS_KERNEL_OFFSETS, 5, 32 * sh.Q, [&] {
@@ -941,8 +976,9 @@ struct Pipeline {
       return PGS_OK;
     }
     --left;
+    const PrePlanned pre0 = pre_planned(0);
     PGS_TRY(pair_round(GenFused{b.pairs, b.tcount, g, b.off, b.seg_src, 0, mtile}, sh.Q, n, 6,
-                       bucket_live_pairs(sh.Q, 1)));
+                       bucket_live_pairs(sh.Q, 1), nullptr, 0, sh.pre_rounds ? &pre0 : nullptr));
     flip();
     k0 = 1;
     return PGS_OK;
@@ -965,8 +1001,11 @@ struct Pipeline {
         step *= 4;
         levels -= 2;
       } else {
+        // The offsets kernel planned the round if it covers every bucket.
+        const PrePlanned pre = pre_planned((uint32_t)ceil_log2(step));
+        const bool use_pre = sh.pre_rounds && q0 == 0 && Qg == sh.Q;
         PGS_TRY(pair_round(GenBucketLists{b.pairs, b.tcount, g, b.off, q0, step, mtile}, Qg, len, 6,
-                           bucket_live_pairs(Qg, step)));
+                           bucket_live_pairs(Qg, step), nullptr, 0, use_pre ? &pre : nullptr));
         step *= 2;
         levels -= 1;
       }

@@ -715,12 +715,11 @@ constexpr int kPlanVT = 8;
 constexpr uint64_t kPlanMaxPairs = (uint64_t)kPlanNT * kPlanVT;
 constexpr uint64_t kPlanMaxTiles = 4096;             // larger rounds plan faster with the partition kernel
 
+// One round's plan by the whole CTA (kPlanNT threads); ends with a barrier,
+// so a CTA may plan several rounds one after the other.
 template <typename Gen>
-__global__ void __launch_bounds__(kPlanNT)
-k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin, uint64_t npairs, TileJob* jobs,
-            uint32_t tile, uint32_t* err) {
-  pdl_enter();
-  if (poisoned(err)) return;
+__device__ __forceinline__ void plan_round(const Gen& gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin,
+                                           uint64_t npairs, TileJob* jobs, uint32_t tile, uint32_t* err) {
   __shared__ uint16_t s_tb[kPlanMaxPairs + 1];         // tbegin, while the total fits kPlanMaxTiles
   const int tid = threadIdx.x;
   for (uint64_t p = tid; p < npairs; p += kPlanNT) gen(p);
@@ -736,7 +735,11 @@ k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin
   uint64_t total;
   uint64_t pre = block_exclusive_scan(acc, &total);
   if (total > kPlanMaxTiles) {                        // the host's bound did not hold: never expected
-    if (tid == 0) atomicOr(err, kErrBadTile);
+    if (tid == 0) {
+      atomicOr(err, kErrBadTile);
+      tbegin[npairs] = 0;                             // no tiles: the round's merge CTAs all leave
+    }
+    __syncthreads();
     return;
   }
 #pragma unroll
@@ -762,6 +765,16 @@ k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin
     const Pair pr = pairs[lo];
     jobs[t] = TileJob{pr.a, pr.na, pr.b, pr.nb, pr.out, (uint64_t)(t - s_tb[lo]) * tile};
   }
+  __syncthreads();                                    // pairs and s_tb are free for the next round
+}
+
+template <typename Gen>
+__global__ void __launch_bounds__(kPlanNT)
+k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin, uint64_t npairs, TileJob* jobs,
+            uint32_t tile, uint32_t* err) {
+  pdl_enter();
+  if (poisoned(err)) return;
+  plan_round(gen, pairs, tcount, tbegin, npairs, jobs, tile, err);
 }
 
 // CTAs per SM the merge tile is compiled for (0: the compiler's choice).
@@ -1666,7 +1679,7 @@ __device__ __forceinline__ uint64_t segment_size(const Geo& g, uint64_t q, const
   const uint64_t local = q - g.seg[i];
   const uint64_t b = local / P, rl = local % P;
   const uint64_t* c = cut + g.mat[i] + rl * (P + 1);
-  src[q] = g.run_off[g.R0[i] + rl] + c[b];
+  if (src) src[q] = g.run_off[g.R0[i] + rl] + c[b];
   return c[b + 1] - c[b];
 }
 
@@ -1680,33 +1693,65 @@ static __global__ void k_bucket_sizes(Geo g, uint64_t Q, const uint64_t* __restr
 
 // The same sizes and their exclusive scan (the receive offsets, off[Q] = n)
 // in one CTA, for at most kSizesMax segments (beyond, the CTA's dependent
-// loads cost more than a second launch: 47 us for 16384 segments).
+// loads cost more than a second launch: 47 us for 16384 segments).  With
+// pp.rounds > 0 (a single sort whose bucket rounds are all small) the kernel
+// also plans every round of step 6 as k_plan_jobs would, one CTA per round:
+// CTA r recomputes the offsets (CTA 0 stores them), keeps its copy in
+// pp.offs + r (Q + 1) and plans round r (step 2^r; round 0 fused with the
+// exchange unless pp.scatter) into pp.jobs + r pp.stride and pp.tbegin +
+// r (Q + 1), with its own pair scratch, so those rounds need no planning
+// launch and no CTA waits for another.
 constexpr int kSizesNT = 1024, kSizesVT = 4;
 constexpr uint64_t kSizesMax = (uint64_t)kSizesNT * kSizesVT;
+static_assert(kSizesNT == kPlanNT, "the offsets CTAs also plan rounds");
+
+struct PrePlan {
+  Pair* pairs; uint64_t* tcount; uint64_t* tbegin; TileJob* jobs; uint64_t* offs;
+  uint64_t stride; uint32_t rounds, tile; int scatter;
+};
 
 static __global__ void __launch_bounds__(kSizesNT)
 k_bucket_offsets(Geo g, uint64_t Q, const uint64_t* __restrict__ cut, uint64_t* sizes, uint64_t* src,
-                 uint64_t* off) {
+                 uint64_t* off, PrePlan pp, uint32_t* err) {
   pdl_enter();
+  __shared__ int s_skip;
+  const uint32_t r = blockIdx.x;
+  const bool store = r == 0;
   const uint64_t q0 = (uint64_t)threadIdx.x * kSizesVT;   // blocked: thread t owns [t VT, t VT + VT)
   uint64_t v[kSizesVT];
   uint64_t acc = 0;
 #pragma unroll
   for (int k = 0; k < kSizesVT; ++k) {
-    v[k] = q0 + k < Q ? segment_size(g, q0 + k, cut, src) : 0;
+    v[k] = q0 + k < Q ? segment_size(g, q0 + k, cut, store ? src : nullptr) : 0;
     acc += v[k];
   }
   uint64_t total;
   uint64_t pre = block_exclusive_scan(acc, &total);
+  uint64_t* my_off = r == 0 ? off : pp.offs + (uint64_t)r * (Q + 1);
 #pragma unroll
   for (int k = 0; k < kSizesVT; ++k) {
     if (q0 + k < Q) {
-      sizes[q0 + k] = v[k];
-      off[q0 + k] = pre;
+      if (store) sizes[q0 + k] = v[k];
+      my_off[q0 + k] = pre;
     }
     pre += v[k];
   }
-  if (threadIdx.x == 0) off[Q] = total;
+  if (threadIdx.x == 0) {
+    my_off[Q] = total;
+    s_skip = poisoned(err);                           // one decision for the whole CTA
+  }
+  if (pp.rounds == 0) return;
+  __syncthreads();                                    // the offsets (and src) are visible to the CTA
+  if (s_skip) return;                                 // a kernel failed: no plan (its merges leave)
+  Pair* pairs = pp.pairs + (uint64_t)r * Q;
+  uint64_t* tcount = pp.tcount + (uint64_t)r * Q;
+  uint64_t* tb = pp.tbegin + (uint64_t)r * (Q + 1);
+  TileJob* jobs = pp.jobs + (uint64_t)r * pp.stride;
+  if (r == 0 && !pp.scatter)
+    plan_round(GenFused{pairs, tcount, g, my_off, src, 0, pp.tile}, pairs, tcount, tb, Q, jobs, pp.tile, err);
+  else
+    plan_round(GenBucketLists{pairs, tcount, g, my_off, 0, 1u << r, pp.tile}, pairs, tcount, tb, Q, jobs, pp.tile,
+               err);
 }
 
 // ---------------------------------------------------------------------------

@@ -178,6 +178,7 @@ inline Shape merge_shape(uint64_t n, uint32_t k, bool vals, const Options& o) {
   sh.S = 0;
   sh.four = use_four_way(sh.n, o);
   finish_shape(sh);
+  sh.pre_rounds = 0;                                    // the rounds are planned one by one
   return sh;
 }
 
