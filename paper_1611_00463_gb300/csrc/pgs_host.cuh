@@ -235,6 +235,7 @@ struct Buffers {
   void* kidx;                // key index of the last pass: the key at every 64th position
   Quad* quads; uint64_t *tcount4, *tbegin4; Split4* splits4; void* xs;   // four-way rounds
   uint64_t max_tiles4 = 0;
+  uint64_t max_tiles = 0;    // entries of split / jobs
   uint64_t *scan_sums, *scan_sums2;
   uint64_t* first_seg;
   // batch tables
@@ -282,6 +283,7 @@ inline size_t carve(const Shape& sh, void* base, Buffers* b, size_t* tables_byte
   b->tbegin = c.take<uint64_t>(sh.max_pairs + 1);
   b->split = c.take<TileSplit>(sh.max_tiles);
   b->jobs = reinterpret_cast<TileJob*>(b->split);
+  b->max_tiles = sh.max_tiles;
   b->pre_jobs = sh.pre_rounds ? c.take<TileJob>((uint64_t)sh.pre_rounds * sh.pre_stride) : nullptr;
   b->pre_tbegin = sh.pre_rounds ? c.take<uint64_t>((uint64_t)sh.pre_rounds * (sh.Q + 1)) : nullptr;
   b->pre_pairs = sh.pre_rounds ? c.take<Pair>((uint64_t)sh.pre_rounds * sh.Q) : nullptr;
@@ -569,8 +571,8 @@ inline int merge_round(Ctx& c, const Gen& gen, const K* ks, const uint32_t* vs, 
     // A small round: descriptors, their scan and one job per tile in one CTA;
     // each merge CTA then finds its own splits.
     PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * tiles_ub + 56 * npairs, [&] {
-      klaunch(c.st, c.pdl, k_plan_jobs<Gen>, 1, kPlanNT, 0, gen, b.pairs, b.tcount, b.tbegin, npairs, b.jobs, tile,
-              b.err);
+      klaunch(c.st, c.pdl, k_plan_jobs<Gen>, 1, kPlanNT, 0, gen, b.pairs, b.tcount, b.tbegin, npairs, b.jobs,
+              b.max_tiles, tile, b.err);
     }));
   } else {
     if (!std::is_same<Gen, GenNone>::value)

@@ -715,11 +715,12 @@ constexpr int kPlanVT = 8;
 constexpr uint64_t kPlanMaxPairs = (uint64_t)kPlanNT * kPlanVT;
 constexpr uint64_t kPlanMaxTiles = 4096;             // larger rounds plan faster with the partition kernel
 
-// One round's plan by the whole CTA (kPlanNT threads); ends with a barrier,
-// so a CTA may plan several rounds one after the other.
+// One round's plan by the whole CTA (kPlanNT threads) into a job table of
+// cap entries (cap <= kPlanMaxTiles); ends with a barrier.
 template <typename Gen>
 __device__ __forceinline__ void plan_round(const Gen& gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin,
-                                           uint64_t npairs, TileJob* jobs, uint32_t tile, uint32_t* err) {
+                                           uint64_t npairs, TileJob* jobs, uint64_t cap, uint32_t tile,
+                                           uint32_t* err) {
   __shared__ uint16_t s_tb[kPlanMaxPairs + 1];         // tbegin, while the total fits kPlanMaxTiles
   const int tid = threadIdx.x;
   for (uint64_t p = tid; p < npairs; p += kPlanNT) gen(p);
@@ -734,7 +735,7 @@ __device__ __forceinline__ void plan_round(const Gen& gen, const Pair* pairs, co
   }
   uint64_t total;
   uint64_t pre = block_exclusive_scan(acc, &total);
-  if (total > kPlanMaxTiles) {                        // the host's bound did not hold: never expected
+  if (total > cap) {                                  // the host's bound did not hold: never expected
     if (tid == 0) {
       atomicOr(err, kErrBadTile);
       tbegin[npairs] = 0;                             // no tiles: the round's merge CTAs all leave
@@ -771,10 +772,10 @@ __device__ __forceinline__ void plan_round(const Gen& gen, const Pair* pairs, co
 template <typename Gen>
 __global__ void __launch_bounds__(kPlanNT)
 k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin, uint64_t npairs, TileJob* jobs,
-            uint32_t tile, uint32_t* err) {
+            uint64_t cap, uint32_t tile, uint32_t* err) {
   pdl_enter();
   if (poisoned(err)) return;
-  plan_round(gen, pairs, tcount, tbegin, npairs, jobs, tile, err);
+  plan_round(gen, pairs, tcount, tbegin, npairs, jobs, umin(cap, kPlanMaxTiles), tile, err);
 }
 
 // CTAs per SM the merge tile is compiled for (0: the compiler's choice).
@@ -1747,11 +1748,12 @@ k_bucket_offsets(Geo g, uint64_t Q, const uint64_t* __restrict__ cut, uint64_t* 
   uint64_t* tcount = pp.tcount + (uint64_t)r * Q;
   uint64_t* tb = pp.tbegin + (uint64_t)r * (Q + 1);
   TileJob* jobs = pp.jobs + (uint64_t)r * pp.stride;
+  const uint64_t cap = umin(pp.stride, kPlanMaxTiles);
   if (r == 0 && !pp.scatter)
-    plan_round(GenFused{pairs, tcount, g, my_off, src, 0, pp.tile}, pairs, tcount, tb, Q, jobs, pp.tile, err);
+    plan_round(GenFused{pairs, tcount, g, my_off, src, 0, pp.tile}, pairs, tcount, tb, Q, jobs, cap, pp.tile, err);
   else
-    plan_round(GenBucketLists{pairs, tcount, g, my_off, 0, 1u << r, pp.tile}, pairs, tcount, tb, Q, jobs, pp.tile,
-               err);
+    plan_round(GenBucketLists{pairs, tcount, g, my_off, 0, 1u << r, pp.tile}, pairs, tcount, tb, Q, jobs, cap,
+               pp.tile, err);
 }
 
 // ---------------------------------------------------------------------------
