@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="override the number of keys (smaller cases)")
     ap.add_argument("--P", type=int, default=None)
     ap.add_argument("--exchange", default="auto", choices=["auto", "scatter", "fused"])
-    ap.add_argument("--merge-ways", type=int, default=0, choices=[0, 2, 4], help="lists merged per pass (0 = the library default, 4)")
+    ap.add_argument("--merge-ways", type=int, default=0, choices=[0, 2, 4], help="lists merged per pass (0 = the library's choice: four-way from 2^23 keys)")
     ap.add_argument("--tile-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="merge tile shape (0 = default; see pgs_config.tile_variant)")
     ap.add_argument("--samples-per-run", type=int, default=0, help="regular samples per run (0 = the paper's budget)")

@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(kPlanNT)
 k_plan_jobs(Gen gen, const Pair* pairs, const uint64_t* tcount, uint64_t* tbegin, uint64_t npairs, TileJob* jobs,
             uint64_t cap, uint32_t tile, uint32_t* err) {
   pdl_enter();
-  if (poisoned(err)) return;
+  if (cta_poisoned(err)) return;
   plan_round(gen, pairs, tcount, tbegin, npairs, jobs, umin(cap, kPlanMaxTiles), tile, err);
 }
 
@@ -821,6 +821,7 @@ k_merge_tile(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* _
         else if (tile < *total_ptr) jb = jobs[tile];
         else live = false;
       }
+      live = __all_sync(0xFFFFFFFFu, live);             // the warp searches together or not at all
       if (live) {
         const uint64_t n = jb.na + jb.nb;
         const uint64_t d = w == 0 ? jb.d0 : umin(jb.d0 + (uint64_t)L::T, n);
@@ -1793,7 +1794,7 @@ k_scatter(const K* __restrict__ ksrc, const uint32_t* __restrict__ vsrc, K* __re
           const uint64_t* __restrict__ first_seg, uint64_t n, uint64_t Q, int f32_out, const uint32_t* err,
           K* __restrict__ kidx) {
   pdl_enter();
-  if (poisoned(err)) return;
+  if (cta_poisoned(err)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem<K>& sm = *reinterpret_cast<ScatterSmem<K>*>(smem_raw);
   const uint64_t o = blockIdx.x * (uint64_t)kScatterTile;

@@ -28,6 +28,16 @@ __device__ __forceinline__ bool poisoned(const uint32_t* err) {
   return *reinterpret_cast<const volatile uint32_t*>(err) != 0u;
 }
 
+// The same test decided once for the whole CTA (thread 0 reads, a barrier
+// shares it), for kernels that synchronise after an early exit.  Every
+// thread of the CTA must call it.
+__device__ __forceinline__ bool cta_poisoned(const uint32_t* err) {
+  __shared__ int s_poisoned;
+  if (threadIdx.x == 0) s_poisoned = poisoned(err) ? 1 : 0;
+  __syncthreads();
+  return s_poisoned != 0;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
