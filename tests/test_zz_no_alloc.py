@@ -49,12 +49,15 @@ def test_static_scratch_matches_workspace_sort_twice():
 @pytest.mark.parametrize("splitters", ["sampled", "learned"])
 @pytest.mark.parametrize("merge_ways", [2, 4])
 @pytest.mark.parametrize("dtype", ["u32", "u64"])
-def test_static_scratch_every_option_at_the_limits(dtype, merge_ways, splitters):
-    # n = 2^16 keys on P = 64 partitions is the largest request; learned
-    # splitters and four-way rounds need the most scratch.
+@pytest.mark.parametrize("P", [63, 64])
+def test_static_scratch_every_option_at_the_limits(dtype, merge_ways, splitters, P):
+    # n = 2^16 keys is the largest request.  P = 64 has the most partitions;
+    # P = 63 the most scratch with pairwise rounds (its bucket rounds are still
+    # small enough for the offsets kernel to plan them all, each in its own
+    # tables); learned splitters and four-way rounds need the most otherwise.
     import torch
     from tests.gpu_helpers import gpu_sort
-    n, P = 1 << 16, 64
+    n = 1 << 16
     keys = inputs.exponential_u32(n, 33) if dtype == "u32" else inputs.normal_lognormal_u64(n, 34)
     vals = inputs.index_payload(n)
     opts = dict(merge_ways=merge_ways, splitters=splitters)
