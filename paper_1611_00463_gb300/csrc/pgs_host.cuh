@@ -57,7 +57,7 @@ struct Options {
   float* model_out = nullptr;
   int tile_variant = 0;       // merge tile shape (see kMergeShapes)
   int merge_ways = 0;         // lists merged per pass: 4 (two tree levels), 2 (one level), 0 = by size
-  int copy_back = PGS_COPY_BACK_GROUPS;   // pgs_sort_host: bucket groups after a host wait, or all at the end
+  int copy_back = PGS_COPY_BACK_AUTO;     // pgs_sort_host: by size, bucket groups after a host wait, or all at the end
   int graph_cache = PGS_GRAPH_CACHE_AUTO; // pgs_sort / pgs_sort_copy: replay repeated calls from a CUDA graph
   uint64_t spin_limit = 0;    // ns of %globaltimer a device-side wait may take; 0 = kWaitLimitNs
   int fault_inject = 0;       // testing only: PGS_FAULT_WAIT_TIMEOUT
@@ -95,7 +95,9 @@ inline int read_options(const pgs_config* cfg, Options* o) {
   if (o->splitter_mode < 0 || o->splitter_mode > 1) return PGS_ERR_INVALID;
   if (o->tile_variant < 0 || o->tile_variant >= PGS_TILE_VARIANTS) return PGS_ERR_INVALID;
   if (o->merge_ways != 0 && o->merge_ways != 2 && o->merge_ways != 4) return PGS_ERR_INVALID;
-  if (o->copy_back != PGS_COPY_BACK_GROUPS && o->copy_back != PGS_COPY_BACK_AT_END) return PGS_ERR_INVALID;
+  if (o->copy_back != PGS_COPY_BACK_AUTO && o->copy_back != PGS_COPY_BACK_GROUPS &&
+      o->copy_back != PGS_COPY_BACK_AT_END)
+    return PGS_ERR_INVALID;
   if (o->graph_cache != PGS_GRAPH_CACHE_AUTO && o->graph_cache != PGS_GRAPH_CACHE_OFF) return PGS_ERR_INVALID;
   if (o->fault_inject != 0 && o->fault_inject != PGS_FAULT_WAIT_TIMEOUT) return PGS_ERR_INVALID;
   return PGS_OK;
@@ -702,6 +704,17 @@ inline uint64_t host_run_start(uint64_t r, uint64_t n, uint64_t P) { return (r *
 // (their bounds read back once step 4 has fixed them), and group g's keys are
 // copied to the host while group g + 1 merges.
 constexpr uint32_t kHostGroups = 8;
+// With copy_back AUTO, below this many keys a host-buffer sort copies in and
+// out in one piece and never waits on the host: the groups' extra copies,
+// events and the host's read of the bucket bounds cost more than the overlap
+// they buy.  Measured (two calls in flight / one call, Gkeys/s): 2^22 u32
+// keys 9.35 / 5.42 in one piece against 5.25 / 4.08 in groups, 2^24 u32
+// 11.15 / 6.97 against 8.16 / 6.26, 2^26 u32 12.45 / 7.27 against 12.91 /
+// 8.90 (u64 alike).
+#ifndef PGS_HOST_GROUP_MIN_LOG2
+#define PGS_HOST_GROUP_MIN_LOG2 25
+#endif
+constexpr uint64_t kHostGroupMinKeys = 1ull << PGS_HOST_GROUP_MIN_LOG2;
 struct HostGroups {
   uint32_t groups = 0;                 // 0: the input is already on the device
   uint32_t r0[kHostGroups + 1] = {};   // runs [r0[g], r0[g+1]) form group g
@@ -1206,11 +1219,12 @@ int run_sort_host(const Shape& sh, const Options& o, const K* hk, const uint32_t
   HostCopies hc;
   PGS_TRY(host_copies_for(o.workspace, &hc));
   HostGroups hg;
-  hg.groups = std::min<uint32_t>(kHostGroups, R);
+  const bool whole = o.copy_back == PGS_COPY_BACK_AUTO && n < kHostGroupMinKeys;
+  hg.groups = whole ? 1 : std::min<uint32_t>(kHostGroups, R);
   for (uint32_t g = 0; g <= hg.groups; ++g) hg.r0[g] = (uint32_t)(((uint64_t)g * R) / hg.groups);
   // Bucket groups copied back during step 6 (P = 1 has no step 6; AT_END
   // copies everything after it and never waits on the host).
-  hg.out_groups = (R > 1 && o.copy_back == PGS_COPY_BACK_GROUPS) ? std::min<uint32_t>(kHostGroups, R) : 0;
+  hg.out_groups = (!whole && R > 1 && o.copy_back != PGS_COPY_BACK_AT_END) ? std::min<uint32_t>(kHostGroups, R) : 0;
   for (uint32_t g = 0; g < kHostGroups; ++g) {
     hg.ev[g] = hc.ev[g];
     hg.ev_out[g] = hc.ev_out[g];

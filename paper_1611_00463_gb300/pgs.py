@@ -20,7 +20,7 @@ PGS_OK, PGS_ERR_INVALID, PGS_ERR_WORKSPACE, PGS_ERR_CUDA, PGS_ERR_TIMEOUT, PGS_E
 INVESTIGATOR = {"rank": 0, "equal": 1, "off": 2, "local": 3}
 EXCHANGE = {"auto": 0, "scatter": 1, "fused": 2}
 SPLITTERS = {"sampled": 0, "learned": 1}
-COPY_BACK = {"groups": 0, "end": 1}
+COPY_BACK = {"auto": 0, "end": 1, "groups": 2}
 GRAPH_CACHE = {"auto": 0, "off": 1}
 FAULT_INJECT = {"off": 0, "wait_timeout": 1}     # testing only (pgs_config.fault_inject)
 DTYPES = {"u32": PGS_U32, "u64": PGS_U64, "f32": PGS_F32}
@@ -255,7 +255,7 @@ def make_config(dtype: str = "u32", samples_per_run: int = 0, eps: float = 0.0, 
                 cuts: torch.Tensor | None = None, splitters_out: torch.Tensor | None = None,
                 stats: torch.Tensor | None = None, timer: Timer | None = None,
                 model: torch.Tensor | None = None, model_out: torch.Tensor | None = None,
-                tile_variant: int = 0, merge_ways: int = 0, copy_back: str = "groups",
+                tile_variant: int = 0, merge_ways: int = 0, copy_back: str = "auto",
                 graph_cache: str = "auto", spin_limit: int = 0, fault_inject: str = "off") -> pgs_config:
     """The options of a call.  The struct holds raw device addresses, so it
     also keeps a reference to every tensor (and the timer) it points to: they

@@ -176,7 +176,7 @@ def test_copy_back_option_is_validated():
     good = pgs.make_config(dtype="u64", copy_back="end")
     assert pgs.pgs_host_workspace_bytes(1 << 20, 16, good) > 0
     bad = pgs.make_config(dtype="u64")
-    bad.copy_back = 2
+    bad.copy_back = 3
     assert pgs.pgs_host_workspace_bytes(1 << 20, 16, bad) == 0
 
 

@@ -3,7 +3,9 @@
 The sorted keys and payloads must equal the oracle's stable sort bit for bit
 and the bucket vector must equal the oracle's step 1-4 computation, for run
 groups of every shape (fewer runs than copy groups, ragged groups, one run),
-pinned and pageable host memory, keys only and with payloads.
+the default copies (one piece each way below 2^25 keys, groups above) and the
+explicit GROUPS and AT_END forms, pinned and pageable host memory, keys only
+and with payloads.
 """
 import numpy as np
 import pytest
@@ -48,7 +50,9 @@ def check(keys, vals, P, dtype, **kw):
 
 
 @pytest.mark.parametrize("dtype,n,P", [("u64", 300_007, 128), ("u32", 3 * TILE + 77, 3), ("f32", 200_003, 16),
-                                       ("u32", 50_000, 1), ("u64", 7, 64), ("u32", 1, 5), ("f32", 123_457, 11)])
+                                       ("u32", 50_000, 1), ("u64", 7, 64), ("u32", 1, 5), ("f32", 123_457, 11),
+                                       # from 2^25 keys the default copies go in groups of runs and of buckets
+                                       ("u32", (1 << 25) + 12_345, 24)])
 def test_host_sort_matches_oracle(dtype, n, P):
     gen = {"u32": inputs.exponential_u32, "u64": inputs.normal_lognormal_u64, "f32": inputs.zipf_dup_f32}[dtype]
     keys = gen(n, n % 89 + 1)
@@ -97,12 +101,13 @@ def test_host_sort_rejects_device_buffers_and_small_workspace():
     assert pgs.pgs_host_workspace_bytes(n, P, cfg0) > pgs.pgs_workspace_bytes(n, P, cfg0)
 
 
-@pytest.mark.parametrize("copy_back", ["groups", "end"])
+@pytest.mark.parametrize("copy_back", ["groups", "end", "auto"])
 def test_host_sorts_in_flight_on_two_streams(copy_back):
     """Consecutive calls on two streams with their own workspaces overlap on the
     GPU (one call's copy in during the other's merges); each result is exact.
     With copy_back = "end" no call waits, so all six are queued at once and a
-    lane's next call must wait for its previous one on the device."""
+    lane's next call must wait for its previous one on the device, and so
+    with "auto" at this size (one copy each way)."""
     import torch
     from paper_1611_00463_gb300 import pgs
     n, P = 600_011, 32
@@ -137,11 +142,12 @@ def test_host_sorts_in_flight_on_two_streams(copy_back):
 def test_host_sort_bucket_groups_with_every_option(opts, P):
     """Step 6 in bucket groups under four-way rounds, the scatter exchange,
     learned splitters and every P shape (bucket rounds after the first: none,
-    odd, even)."""
+    odd, even), with the copies in groups (copy_back GROUPS unless the case
+    says AT_END)."""
     n = 4 * TILE * 9 + 123
     keys = inputs.zipf_dup_f32(n, P)
     vals = inputs.index_payload(n)
-    got_k, got_v, e, _, _ = run_host(keys, vals, P, "f32", **opts)
+    got_k, got_v, e, _, _ = run_host(keys, vals, P, "f32", **{"copy_back": "groups", **opts})
     if opts.get("investigator") == "local":
         ref = O.sample_sort(keys, vals, P, "f32", variant=O.INVESTIGATOR_LOCAL)
         assert np.array_equal(got_k, ref["keys"]) and np.array_equal(got_v, ref["vals"])
