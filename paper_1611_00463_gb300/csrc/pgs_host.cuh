@@ -183,7 +183,7 @@ inline void finish_shape(Shape& sh) {
   if (sh.run_rounds > 1) sh.max_quads = std::max<uint64_t>(sh.max_quads, (uint64_t)sh.R * ceil_div(sh.maxlen, 4ull * kTile));
   if (sh.four) sh.max_pairs = std::max<uint64_t>(sh.max_pairs, 2 * sh.max_quads);   // the index-sample merges
   sh.max_tiles = ceil_div(std::max<uint64_t>(sh.n, 1), kMergeMinTile) + sh.max_pairs + 1;
-  sh.max_tiles4 = ceil_div(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) + sh.max_quads, kMerge4Q) +
+  sh.max_tiles4 = ceil_div(ceil_div(std::max<uint64_t>(sh.n, 1), kIdxStride) + sh.max_quads, kMerge4MinQ) +
                   sh.max_quads + 1;
   sh.scan_len = std::max<uint64_t>(std::max<uint64_t>(sh.max_pairs, sh.Q), sh.max_quads);
   // Step 6 planned by the offsets kernel: one instance, pairwise rounds, the
@@ -514,9 +514,11 @@ inline int set_smem_attrs() {
   PGS_TRY((set_merge_attr<K, V, kMergeShapes[1].nt, kMergeShapes[1].vt>()));
   PGS_TRY((set_merge_attr<K, V, kMergeShapes[2].nt, kMergeShapes[2].vt>()));
   PGS_TRY((set_merge_attr<K, V, kMergeShapes[3].nt, kMergeShapes[3].vt>()));
-  PGS_CUDA(cudaFuncSetAttribute(k_merge4<K, V, kMerge4NT, kMerge4VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes));
-  static_assert(merge4_max_tile(kMerge4Q) <= (uint32_t)(kMerge4NT * kMerge4VT), "four-way tiles fit the CTA");
+  constexpr int NT4 = merge4_nt<K>(), VT4 = merge4_vt<K>();
+  PGS_CUDA(cudaFuncSetAttribute(k_merge4<K, V, NT4, VT4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Merge4Layout<K, V, NT4, VT4>::bytes));
+  static_assert(merge4_max_tile(merge4_q<K>()) <= (uint32_t)(merge4_nt<K>() * merge4_vt<K>()),
+                "four-way tiles fit the CTA");
   PGS_CUDA(cudaFuncSetAttribute(k_scatter<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)sizeof(ScatterSmem<K>)));
   PGS_CUDA(cudaFuncSetAttribute(k_mlp_grad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -623,16 +625,17 @@ inline int merge4_round(Ctx& c, const K* ks, const uint32_t* vs, K* kd, uint32_t
   PGS_TRY((merge_round<K, false>(c, GenNone{}, idx_in, nullptr, xs, nullptr, 2 * nquads, samples, b, 0, step,
                                  nullptr, nullptr, 2 * nq_live)));
   PGS_TRY(scan_u64(c, b.tcount4, b.tbegin4, nquads, b.scan_sums, b.scan_sums2, step));
-  const uint64_t tiles_ub = ceil_div(samples, kMerge4Q) + nq_live + 1;   // <= sh.max_tiles4
+  const uint64_t tiles_ub = ceil_div(samples, merge4_q<K>()) + nq_live + 1;   // <= sh.max_tiles4
   if (tiles_ub > b.max_tiles4) return PGS_ERR_CUDA;                        // plan bug: never expected
   PGS_TRY(launch(c, PGS_KERNEL_PARTITION, step, 48 * tiles_ub, [&] {
     klaunch(c.st, c.pdl, k_corank4<K>, grid_for(tiles_ub, 256), 256, 0, ks, idx_in, xs, b.quads, b.tbegin4, nquads, b.splits4,
-                                                            tiles_ub, kMerge4Q, b.err);
+                                                            tiles_ub, merge4_q<K>(), b.err);
   }));
   const uint64_t bytes = 2 * len * (sizeof(K) + (V ? 4 : 0));
-  constexpr size_t smem = Merge4Layout<K, V, kMerge4NT, kMerge4VT>::bytes;
+  constexpr int NT4 = merge4_nt<K>(), VT4 = merge4_vt<K>();
+  constexpr size_t smem = Merge4Layout<K, V, NT4, VT4>::bytes;
   return launch(c, PGS_KERNEL_MERGE4, step, bytes, [&] {
-    klaunch(c.st, c.pdl, k_merge4<K, V, kMerge4NT, kMerge4VT>, (unsigned)tiles_ub, kMerge4NT, smem, 
+    klaunch(c.st, c.pdl, k_merge4<K, V, NT4, VT4>, (unsigned)tiles_ub, NT4, smem, 
         ks, vs, kd, vd, b.splits4, b.quads, b.tbegin4 + nquads, tiles_ub, f32_out, b.err, idx_out, c.wait_ns, inject);
   });
 }
@@ -862,7 +865,7 @@ struct Pipeline {
         const uint64_t nq = cmax * Rg;
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 1, 112 * nq, [&] {
           klaunch(st, c.pdl, k_quads4_runs, grid_for(nq, 256), 256, 0, b.quads, b.tcount4, b.pairs, b.tcount, ro, Rg, w, cmax,
-                                                           kMerge4Q, mtile);
+                                                           merge4_q<K>(), mtile);
         }));
         PGS_TRY(quad_round(nq, len, 1));
         w *= 4;
@@ -1010,7 +1013,7 @@ struct Pipeline {
       if (sh.four && levels >= 2) {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 112 * Qg, [&] {
           klaunch(st, c.pdl, k_quads4_buckets, grid_for(Qg, 256), 256, 0, b.quads, b.tcount4, b.pairs, b.tcount, g, b.off, q0,
-                                                              Qg, step, kMerge4Q, mtile);
+                                                              Qg, step, merge4_q<K>(), mtile);
         }));
         PGS_TRY(quad_round(Qg, len, 6, bucket_live_pairs(Qg, 2 * step)));
         step *= 4;

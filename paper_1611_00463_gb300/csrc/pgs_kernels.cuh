@@ -17,20 +17,29 @@ constexpr int kNT = 256;             // threads per CTA of the sort and merge ke
 constexpr int kVT = 17;              // items per thread; odd, so blocked smem access is conflict free
 constexpr int kTile = kNT * kVT;     // 4352 keys per block-sort tile and per merge tile
 constexpr int kMergeMinTile = 64 * 17;            // smallest merge tile of the tunable shapes
-// Four-way rounds: threads per CTA, outputs per thread at most (odd, so the
-// blocked staging is free of bank conflicts), and CTAs per SM to compile for.
-#ifndef PGS_MERGE4_NT
-#define PGS_MERGE4_NT 128
+// Four-way rounds, per key width: threads per CTA, outputs per thread at most
+// (odd, so the blocked staging is free of bank conflicts) and CTAs per SM to
+// compile for.  Measured per pass (ms; 2^27 u64 keys, 2^28 u32 keys):
+// 8-byte keys 128 x 17 0.752, 128 x 25 0.761, 256 x 17 0.779, 128 x 21 0.796,
+// 128 x 33 0.823; 4-byte keys 256 x 17 1.136, 128 x 21 1.168, 128 x 17 1.188,
+// 128 x 25 1.188, 128 x 33 1.257.  (PGS_MERGE4_NT / _VT / _MIN_BLOCKS set
+// one shape for both widths, for such sweeps.)
+template <int W> struct Merge4Shape;
+#ifdef PGS_MERGE4_NT
+template <int W> struct Merge4Shape {
+  static constexpr int NT = PGS_MERGE4_NT, VT = PGS_MERGE4_VT, MIN_BLOCKS = PGS_MERGE4_MIN_BLOCKS;
+};
+#else
+template <> struct Merge4Shape<8> { static constexpr int NT = 128, VT = 17, MIN_BLOCKS = 7; };
+template <> struct Merge4Shape<4> { static constexpr int NT = 256, VT = 17, MIN_BLOCKS = 3; };
 #endif
-#ifndef PGS_MERGE4_VT
-#define PGS_MERGE4_VT 17
-#endif
-#ifndef PGS_MERGE4_MIN_BLOCKS
-#define PGS_MERGE4_MIN_BLOCKS 7
-#endif
-constexpr int kMerge4NT = PGS_MERGE4_NT;
-constexpr int kMerge4VT = PGS_MERGE4_VT;          // a tile holds <= NT x VT outputs (2176)
-constexpr uint32_t kMerge4Q = (kMerge4NT * kMerge4VT - 4 * 63) / 64;   // index samples per tile (30)
+template <typename K> constexpr int merge4_nt() { return Merge4Shape<(int)sizeof(K)>::NT; }
+template <typename K> constexpr int merge4_vt() { return Merge4Shape<(int)sizeof(K)>::VT; }
+// Index samples per tile: tiles hold at most 64 Q + 4 x 63 <= NT x VT outputs.
+template <typename K> constexpr uint32_t merge4_q() { return (merge4_nt<K>() * merge4_vt<K>() - 4 * 63) / 64; }
+// The smallest Q of any key width (workspace bounds that hold for all of them).
+constexpr uint32_t kMerge4MinQ = merge4_q<uint64_t>() < merge4_q<uint32_t>() ? merge4_q<uint64_t>()
+                                                                              : merge4_q<uint32_t>();
 constexpr int kScanNT = 1024;
 constexpr int kScanVT = 8;
 constexpr int kScanChunk = kScanNT * kScanVT;
@@ -1173,9 +1182,9 @@ struct Merge4Layout {
 // level-1 outputs straddle the end of X switches from the (A, B) merge to the
 // (C, D) merge in mid-loop.
 // CTAs per SM the four-way tile is compiled for: with 8-byte keys and
-// payloads the compiler's 93 registers would hold it to 5.
+// payloads the compiler's 93 registers would hold 128 x 17 to 5.
 template <typename K, bool VALS>
-constexpr int merge4_min_blocks() { return PGS_MERGE4_MIN_BLOCKS; }
+constexpr int merge4_min_blocks() { return Merge4Shape<(int)sizeof(K)>::MIN_BLOCKS; }
 
 template <typename K, bool VALS, int NT, int VT>
 __global__ void __launch_bounds__(NT, (merge4_min_blocks<K, VALS>()))

@@ -274,7 +274,7 @@ int run_merge_lists(const Shape& sh, const Options& o, const K* kin, const uint3
       if (sh.four && levels >= 2) {
         PGS_TRY(launch(c, PGS_KERNEL_PAIRS, 6, 112ull * k, [&] {
           klaunch(st, c.pdl, k_quads4_buckets, grid_for(k, 256), 256, 0, b.quads, b.tcount4, b.pairs, b.tcount, g, b.off, 0, k,
-                                                             step, kMerge4Q, mtile);
+                                                             step, merge4_q<K>(), mtile);
         }));
         PGS_TRY((merge4_round<K, V>(c, src, vsrc, kd, vd, k, n, b, last ? f32 : 0, 6, kidx, io,
                                     ceil_div(k, 4ull * step) + 1)));

@@ -11,8 +11,9 @@ stable four-way merge (key, list, position) written out from its definition,
 for small S so that every alignment, tie pattern and list end is reached:
 each boundary's co-ranks are exactly the elements before its sample; the
 boundaries rise; every tile holds S Q +- 3 (S - 1) outputs and the first and
-last at most S Q + 4 (S - 1), so with S = 64 and Q = 30 a tile never exceeds
-the 2176 outputs a CTA holds."""
+last at most S Q + 4 (S - 1), so with S = 64 a tile never exceeds the outputs
+a CTA holds: Q = 30 and 2176 (128 x 17) for 8-byte keys, Q = 64 and 4352
+(256 x 17) for 4-byte keys."""
 import math
 
 import numpy as np
@@ -152,11 +153,13 @@ def test_boundaries_are_exact_and_tiles_bounded(S, Q):
         check_quad(src, s, n, S, Q)
 
 
-def test_kernel_stride_and_tile():
-    """S = 64, Q = 30 (2176-output tiles) on lists of thousands of keys, with
-    heavy ties, one-sided lists and empty lists."""
-    S, Q = 64, 30
-    assert S * Q + 4 * (S - 1) <= 128 * 17
+@pytest.mark.parametrize("Q,tile", [(30, 128 * 17), (64, 256 * 17)])
+def test_kernel_stride_and_tile(Q, tile):
+    """S = 64 and the kernel's Q for each key width (2176- and 4352-output
+    tiles) on lists of thousands of keys, with heavy ties, one-sided lists and
+    empty lists."""
+    S = 64
+    assert S * Q + 4 * (S - 1) <= tile
     g = np.random.default_rng(64)
     for vmax, lens in [(2, (3000, 2500, 0, 4100)), (7, (5000, 10, 3000, 3000)), (1 << 40, (4096, 4096, 4096, 4096)),
                        (1 << 40, (1, 0, 0, 9000)), (50, (2000, 2000, 2000, 2000))]:
@@ -167,4 +170,4 @@ def test_kernel_stride_and_tile():
         for i in range(4):
             src[s[i]:s[i] + n[i]] = sorted(src[s[i]:s[i] + n[i]])
         sizes = check_quad(src, s, n, S, Q)
-        assert max(sizes) <= 2176
+        assert max(sizes) <= tile
