@@ -108,14 +108,14 @@ typedef enum { PGS_GRAPH_CACHE_AUTO = 0, PGS_GRAPH_CACHE_OFF = 1 } pgs_graph_cac
 typedef enum {
   PGS_KERNEL_BLOCK_SORT = 0,   /* step 1: shared-memory block sort of one tile */
   PGS_KERNEL_MERGE = 1,        /* steps 1, 3, 6: pairwise merge-path merge of one round */
-  PGS_KERNEL_PARTITION = 2,    /* merge-path splits of one round */
+  PGS_KERNEL_PARTITION = 2,    /* one round's plan: merge-path splits, a small round's tile jobs, four-way co-ranks */
   PGS_KERNEL_PAIRS = 3,        /* pair descriptors of one round */
   PGS_KERNEL_SCAN = 4,         /* device-wide exclusive scan */
   PGS_KERNEL_SAMPLE = 5,       /* step 2: regular samples */
-  PGS_KERNEL_SPLITTERS = 6,    /* step 3: splitter pick */
-  PGS_KERNEL_CUT_SEARCH = 7,   /* step 4: binary searches */
+  PGS_KERNEL_SPLITTERS = 6,    /* step 3: splitter pick (a sort's pick runs inside the cut search), learned model */
+  PGS_KERNEL_CUT_SEARCH = 7,   /* steps 3-4: splitter pick, binary searches, fixed cuts */
   PGS_KERNEL_INVESTIGATOR = 8, /* step 4: investigator cuts */
-  PGS_KERNEL_OFFSETS = 9,      /* step 5 set-up: segment sizes and receive offsets */
+  PGS_KERNEL_OFFSETS = 9,      /* step 5 set-up: segment sizes, receive offsets (and small sorts' bucket round plans) */
   PGS_KERNEL_SCATTER = 10,     /* step 5: the exchange */
   PGS_KERNEL_STATS = 11,       /* load statistics */
   PGS_KERNEL_MERGE4 = 12,      /* steps 1, 6: four-way merge of one pass (two tree levels) */
