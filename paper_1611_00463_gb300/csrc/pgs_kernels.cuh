@@ -20,17 +20,19 @@ constexpr int kMergeMinTile = 64 * 17;            // smallest merge tile of the 
 // Four-way rounds, per key width: threads per CTA, outputs per thread at most
 // (odd, so the blocked staging is free of bank conflicts) and CTAs per SM to
 // compile for.  Measured per pass (ms; 2^27 u64 keys, 2^28 u32 keys):
-// 8-byte keys 128 x 17 0.752, 128 x 25 0.761, 256 x 17 0.779, 128 x 21 0.796,
-// 128 x 33 0.823; 4-byte keys 256 x 17 1.136, 128 x 21 1.168, 128 x 17 1.188,
-// 128 x 25 1.188, 128 x 33 1.257.  (PGS_MERGE4_NT / _VT / _MIN_BLOCKS set
-// one shape for both widths, for such sweeps.)
+// 8-byte keys 128 x 19 0.748, 128 x 17 0.752, 128 x 25 0.761, 256 x 17 0.779,
+// 128 x 21 0.796, 128 x 33 0.823 (the whole 2^28-key u64 sort 17.79 ms with
+// 128 x 19 against 17.86 with 128 x 17); 4-byte keys 256 x 17 1.136,
+// 128 x 21 1.168, 128 x 17 1.188, 128 x 25 1.188, 128 x 33 1.257.
+// (PGS_MERGE4_NT / _VT / _MIN_BLOCKS set one shape for both widths, for such
+// sweeps.)
 template <int W> struct Merge4Shape;
 #ifdef PGS_MERGE4_NT
 template <int W> struct Merge4Shape {
   static constexpr int NT = PGS_MERGE4_NT, VT = PGS_MERGE4_VT, MIN_BLOCKS = PGS_MERGE4_MIN_BLOCKS;
 };
 #else
-template <> struct Merge4Shape<8> { static constexpr int NT = 128, VT = 17, MIN_BLOCKS = 7; };
+template <> struct Merge4Shape<8> { static constexpr int NT = 128, VT = 19, MIN_BLOCKS = 6; };
 template <> struct Merge4Shape<4> { static constexpr int NT = 256, VT = 17, MIN_BLOCKS = 3; };
 #endif
 template <typename K> constexpr int merge4_nt() { return Merge4Shape<(int)sizeof(K)>::NT; }
@@ -1181,8 +1183,8 @@ struct Merge4Layout {
 // staged once more in place and leaves with 16-byte stores.  A thread whose
 // level-1 outputs straddle the end of X switches from the (A, B) merge to the
 // (C, D) merge in mid-loop.
-// CTAs per SM the four-way tile is compiled for: with 8-byte keys and
-// payloads the compiler's 93 registers would hold 128 x 17 to 5.
+// CTAs per SM the four-way tile is compiled for (with 8-byte keys and
+// payloads the compiler's own choice of registers would hold 128 x 17 to 5).
 template <typename K, bool VALS>
 constexpr int merge4_min_blocks() { return Merge4Shape<(int)sizeof(K)>::MIN_BLOCKS; }
 

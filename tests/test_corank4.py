@@ -12,7 +12,7 @@ for small S so that every alignment, tie pattern and list end is reached:
 each boundary's co-ranks are exactly the elements before its sample; the
 boundaries rise; every tile holds S Q +- 3 (S - 1) outputs and the first and
 last at most S Q + 4 (S - 1), so with S = 64 a tile never exceeds the outputs
-a CTA holds: Q = 30 and 2176 (128 x 17) for 8-byte keys, Q = 64 and 4352
+a CTA holds: Q = 34 and 2432 (128 x 19) for 8-byte keys, Q = 64 and 4352
 (256 x 17) for 4-byte keys."""
 import math
 
@@ -153,7 +153,7 @@ def test_boundaries_are_exact_and_tiles_bounded(S, Q):
         check_quad(src, s, n, S, Q)
 
 
-@pytest.mark.parametrize("Q,tile", [(30, 128 * 17), (64, 256 * 17)])
+@pytest.mark.parametrize("Q,tile", [(30, 128 * 17), (34, 128 * 19), (64, 256 * 17)])
 def test_kernel_stride_and_tile(Q, tile):
     """S = 64 and the kernel's Q for each key width (2176- and 4352-output
     tiles) on lists of thousands of keys, with heavy ties, one-sided lists and
