@@ -22,8 +22,9 @@ constexpr int kMergeMinTile = 64 * 17;            // smallest merge tile of the 
 // compile for.  Measured per pass (ms; 2^27 u64 keys, 2^28 u32 keys):
 // 8-byte keys 128 x 19 0.748, 128 x 17 0.752, 128 x 25 0.761, 256 x 17 0.779,
 // 128 x 21 0.796, 128 x 33 0.823 (the whole 2^28-key u64 sort 17.79 ms with
-// 128 x 19 against 17.86 with 128 x 17); 4-byte keys 256 x 17 1.136,
-// 128 x 21 1.168, 128 x 17 1.188, 128 x 25 1.188, 128 x 33 1.257.
+// 128 x 19 against 17.86 with 128 x 17); 4-byte keys 256 x 17 1.133-1.136,
+// 128 x 21 1.168, 256 x 15 1.182, 128 x 17 1.188, 128 x 25 1.188,
+// 256 x 21 1.246, 256 x 13 1.248, 128 x 33 1.257, 256 x 19 1.283.
 // (PGS_MERGE4_NT / _VT / _MIN_BLOCKS set one shape for both widths, for such
 // sweeps.)
 template <int W> struct Merge4Shape;
