@@ -14,7 +14,10 @@
 namespace pgs {
 
 constexpr int kNT = 256;             // threads per CTA of the sort and merge kernels
-constexpr int kVT = 17;              // items per thread; odd, so blocked smem access is conflict free
+#ifndef PGS_BLOCK_VT
+#define PGS_BLOCK_VT 17
+#endif
+constexpr int kVT = PGS_BLOCK_VT;    // items per thread; odd, so blocked smem access is conflict free
 constexpr int kTile = kNT * kVT;     // 4352 keys per block-sort tile and per merge tile
 constexpr int kMergeMinTile = 64 * 17;            // smallest merge tile of the tunable shapes
 // Four-way rounds, per key width: threads per CTA, outputs per thread at most
