@@ -234,3 +234,20 @@ def test_static_limits_match_header_and_every_option_fits(lib):
                 assert 0 < b <= pgs.STATIC_SCRATCH_BYTES, (dt, spl, mw, ex, g, s, eps, n, P, b)
                 worst = max(worst, b)
     assert worst > pgs.STATIC_SCRATCH_BYTES // 2        # the grid reaches the expensive combinations
+
+
+@pytest.mark.parametrize("P", [2, 16, 63])
+@pytest.mark.parametrize("dtype", ["u32", "u64"])
+def test_bucket_rounds_planned_ahead_only_within_their_limit(P, dtype):
+    """A single sort with pairwise rounds whose every bucket round is small
+    (ceil(n / 1088) + P^2 <= 4096 tiles) has its bucket rounds planned by the
+    offsets kernel, in job tables of its own: its workspace holds them up to
+    that n and not one key past it, and never with four-way rounds."""
+    from paper_1611_00463_gb300 import pgs
+    limit = (4096 - P * P) * 1088
+    cfg = pgs.make_config(dtype=dtype, merge_ways=2)
+    rounds = (P - 1).bit_length()
+    tables = rounds * ((limit + 1087) // 1088 + P * P) * 48     # at least the job tables
+    assert pgs.pgs_workspace_bytes(limit, P, cfg) - pgs.pgs_workspace_bytes(limit + 1, P, cfg) >= tables
+    four = pgs.make_config(dtype=dtype, merge_ways=4)
+    assert pgs.pgs_workspace_bytes(limit, P, four) - pgs.pgs_workspace_bytes(limit + 1, P, four) <= 0
