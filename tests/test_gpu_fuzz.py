@@ -88,3 +88,38 @@ def test_random_batch(seed):
         a, b = int(offsets[i]), int(offsets[i + 1])
         wk, wv = O.stable_sort(keys[a:b], vals[a:b], dtype)
         assert np.array_equal(got_k[a:b], wk) and np.array_equal(got_v[a:b], wv), f"instance {i}"
+
+
+def random_case_larger(seed):
+    """Sizes up to 3M keys, every merge-width choice (0 = by size) and every
+    merge tile shape: the rounds that plan themselves, by one CTA or by the
+    partition kernel, and the bucket rounds planned by the offsets kernel."""
+    g = np.random.default_rng(seed)
+    dtype = ["u32", "u64", "f32"][int(g.integers(0, 3))]
+    n = int(g.choice([int(g.integers(1, 5000)), int(g.integers(5000, 300000)), int(g.integers(300000, 3000000))]))
+    P = int(g.choice([1, 2, int(g.integers(3, 70)), int(g.integers(70, 400))]))
+    gen = GENS[dtype][int(g.integers(0, len(GENS[dtype])))]
+    opts = {"investigator": ["rank", "equal", "off"][int(g.integers(0, 3))],
+            "exchange": ["auto", "scatter"][int(g.integers(0, 2))],
+            "merge_ways": [0, 2, 4][int(g.integers(0, 3))],
+            "tile_variant": int(g.integers(0, 4))}
+    s = int(g.integers(1, 300)) if g.random() < 0.3 else None
+    return dtype, n, P, gen, opts, s, int(g.integers(0, 1 << 30))
+
+
+@pytest.mark.parametrize("seed", range(10000, 10040))
+def test_random_larger_configuration(seed):
+    from tests.gpu_helpers import gpu_sort
+    dtype, n, P, gen, opts, s, kseed = random_case_larger(seed)
+    keys = gen(n, kseed)
+    vals = inputs.index_payload(n)
+    kw = dict(opts)
+    if s is not None:
+        kw["samples_per_run"] = s
+    got = gpu_sort(keys, vals, P, dtype, **kw)
+    want_k, want_v = O.stable_sort(keys, vals, dtype)
+    assert np.array_equal(got["keys"], want_k) and np.array_equal(got["vals"], want_v)
+    variant = {"rank": O.INVESTIGATOR_RANK, "equal": O.INVESTIGATOR_EQUAL, "off": O.INVESTIGATOR_OFF}[opts["investigator"]]
+    ref = O.buckets(keys, P, dtype, samples_per_run=s, variant=variant)
+    assert np.array_equal(got["e"], ref["e"])
+    assert np.array_equal(got["cut"], ref["cut"])
